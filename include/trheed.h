@@ -1,0 +1,166 @@
+/*
+ * trheed.h - C ABI of the GB300 RHEED/TRHEPD rocking-curve library (libtrheed.so).
+ *
+ * The library computes the forward model of reflection high-energy electron diffraction (RHEED)
+ * and total-reflection high-energy positron diffraction (TRHEPD) by the matrix-ODE multi-slice
+ * method of Kudo, Yamamoto & Hoshi, "A fast and accurate computation method for reflective
+ * diffraction simulations" (arXiv 2306.00271):
+ *
+ *   - the problem (Section 2.1, Eqs. sch1-sch3, vtau, vrho, bd0, bd1): a 2D-periodic surface slab
+ *     z_e <= z <= 0 with lattice a1, a2; beams k_j = m1 b1 + m2 b2 (k_1 = 0); the n-beam system
+ *     c'' = -(U(z) + Gamma^2) c with U_jk = u_{g_j - g_k}(z) and
+ *     Gamma = diag(sqrt(gamma^2 - |b0 + k_j|^2)); incident tau(0) = e_1, no wave from below
+ *     (rho(z_e) = 0);
+ *   - the method (Section 3, Algorithm 1): the economical state Z = [Q; P] (2n x n, Eq. mateq2)
+ *     integrated from z_e to 0 by a splitting integrator (Section 3.4), with the right-hand-side
+ *     transformation Z <- Z Q^{-1} whenever the Gershgorin-based bound xi on cond(Q) exceeds a
+ *     threshold (Section 3.2), and rho(0) = (Gamma + i P Q^{-1})(Gamma - i P Q^{-1})^{-1} e_1
+ *     (Eq. vrhocomp);
+ *   - the output (Section 2.1, below Eq. bd1): rho(0) per beam and the intensity
+ *     eta_i = |rho_i|^2 sin(theta0) Gamma_1 / Gamma_i for propagating beams (0 for evanescent ones).
+ *
+ * Every step of that path runs in CUDA kernels for sm_103a. There is no CPU fallback: on a
+ * machine without a usable GPU every compute call returns TRH_ECUDA.
+ *
+ * Conventions
+ *   - All functions return 0 (TRH_OK) or a negative TRH_E* code; no C++ exception crosses the
+ *     ABI. trh_strerror() names a code; trh_last_error() gives a message for the last failing
+ *     call on this thread.
+ *   - Lengths in Angstrom, energies in eV, angles in degrees.
+ *   - complex128 = two consecutive doubles (re, im).
+ *   - Pointers marked "host or device" may point to host memory or to device memory of the
+ *     current device; the library detects which (cudaPointerGetAttributes). Host outputs are
+ *     written before the call returns; device outputs are written in stream order on `stream`.
+ *   - The caller owns every buffer it passes; the library never frees or retains caller memory
+ *     beyond the call (trh_create copies what it needs). The library owns its context and all
+ *     device scratch, allocated in trh_create / trh_set_structure and freed in trh_destroy.
+ *   - A context may be used by one thread at a time.
+ */
+#ifndef TRHEED_H
+#define TRHEED_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define TRH_OK            0
+#define TRH_EINVAL       -1  /* bad argument: shape, k_1 != 0, h <= 0, z_e >= 0, N too large...  */
+#define TRH_EGRAZING     -2  /* some Gamma_j = 0 (beam exactly on the Ewald circle)              */
+#define TRH_ESINGULAR    -3  /* zero or non-finite pivot in the RHST or in the final solve       */
+#define TRH_ETIMEOUT     -4  /* a device-side bounded wait expired                               */
+#define TRH_ENOMEM       -5  /* device or host allocation failed                                 */
+#define TRH_ECUDA        -6  /* CUDA runtime error (including: no device)                        */
+#define TRH_EUNSUPPORTED -7  /* valid request this build does not implement                      */
+
+/* ---- method selection --------------------------------------------------------------------- */
+enum trh_integrator {
+  TRH_SP4 = 0, /* BAB splitting, SRKN_6^b coefficients (Section 3.4; 6 kicks per step with FSAL) */
+  TRH_SP6 = 1, /* BAB splitting, SRKN_11^b coefficients (11 kicks per step with FSAL)            */
+  TRH_RK4 = 2  /* classical Runge-Kutta (Section 3.4)                                           */
+};
+
+enum trh_precision {
+  TRH_FP64  = 0, /* every product, update and solve in IEEE binary64                            */
+  TRH_MIXED = 1  /* U*Q products on the BF16 tensor cores as a 3-term split with FP32
+                    accumulation; state, RHST and final solve in higher precision (see
+                    trh_rocking_curve)                                                           */
+};
+
+/* ---- problem description ------------------------------------------------------------------ */
+typedef struct trh_problem {
+  int particle;          /* +1 electron (RHEED), -1 positron (TRHEPD)                            */
+  double energy_ev;      /* kinetic energy E (eV), > 0                                           */
+  double absorption;     /* absorptive potential as a fraction of the real one (e.g. 0.1), >= 0  */
+  double a1[2], a2[2];   /* surface lattice vectors (A)                                           */
+  int n_beams;           /* N >= 1                                                                */
+  const int* beams;      /* [N][2] (m1, m2) host; beams[0] must be (0, 0); entries distinct       */
+  int n_atoms;           /* atoms per parameter set, >= 1                                         */
+  const double* atoms;   /* [n_atoms][3] x, y, z (A), z <= 0; host. Default structure.           */
+  const double* dw;      /* [n_atoms] Debye-Waller B (A^2), >= 0; host                            */
+  const int* species;    /* [n_atoms] species index in [0, n_species); host                      */
+  int n_species;         /* >= 1                                                                  */
+  const double* sf;      /* [n_species][8] scattering factor a_1..a_4 (A), b_1..b_4 (A^2), host.
+                            Electron scattering factor f(s) = sum_i a_i exp(-b_i s^2),
+                            s = |q| / (4 pi).                                                     */
+  double z_e;            /* slab bottom (A), < 0                                                  */
+  int n_steps;           /* L >= 1; step h = -z_e / L                                              */
+  int integrator;        /* enum trh_integrator                                                    */
+  double rhst_threshold; /* RHST threshold on xi; <= 0 selects 1000 (Algorithm 1)                 */
+  int precision;         /* enum trh_precision                                                     */
+} trh_problem;
+
+typedef struct trh_ctx trh_ctx;
+
+/* Counters of the last trh_rocking_curve call. */
+typedef struct trh_stats {
+  int n_sets;             /* parameter sets in the context                                        */
+  int n_angles;           /* angles in the last call                                               */
+  int n_beams;            /* N                                                                     */
+  int n_nodes;            /* potential evaluation nodes per set (kick positions)                  */
+  long long rhst_total;   /* RHST transforms summed over all (set, angle) of the last call         */
+  int rhst_max;           /* largest RHST count of one (set, angle)                                */
+  int n_bad;              /* (set, angle) pairs with a nonzero status                              */
+  int first_bad_set;      /* -1 if none                                                            */
+  int first_bad_angle;    /* -1 if none                                                            */
+  int first_bad_status;   /* TRH_E* code of that pair                                              */
+  int kernels_launched;   /* kernels launched by the last call                                     */
+  double ms_last;         /* wall time of the last call (host clock, includes synchronisation)   */
+  double ms_potential;    /* device time of the potential-table kernels of the last call (CUDA
+                             events on the call's stream; 0 if the tables were current)          */
+  double ms_integrate;    /* device time of the integration kernel of the last call              */
+} trh_stats;
+
+/* Create a context for one beam set and method. Validates and copies `p` (the caller may free
+ * its arrays afterwards), allocates device tables for one parameter set (the default structure
+ * p->atoms, p->dw) and builds the host-side geometry (reciprocal rods, difference map U_jk ->
+ * u_{g_j - g_k}, kick positions of the integrator).
+ * Errors: TRH_EINVAL (see field comments; N > 64 on the FP64 path and N > 64 on the mixed path
+ * are TRH_EUNSUPPORTED in this build), TRH_ENOMEM, TRH_ECUDA. On error *out is NULL. */
+int trh_create(trh_ctx** out, const trh_problem* p);
+
+/* Replace the context's parameter sets: n_sets structures sharing the beam set, species table
+ * and slab. `atoms` is [n_sets][n_atoms][3] and `dw` is [n_sets][n_atoms], host or device
+ * memory (both on the same side); `dw` may be NULL (every set uses the problem's dw). Host
+ * inputs are validated (z <= 0, dw >= 0); device inputs are copied as given (stream order on
+ * the legacy default stream, synchronised before return). Builds nothing yet: the potential
+ * tables are rebuilt by the next trh_rocking_curve (Section 3.4: one U(z) serves every angle
+ * of a set), so calling this with unchanged data forces a rebuild.
+ * Errors: TRH_EINVAL (n_sets < 1, z > 0, dw < 0), TRH_ENOMEM, TRH_ECUDA. */
+int trh_set_structure(trh_ctx* ctx, int n_sets, const double* atoms, const double* dw);
+
+/* Rocking curves of every parameter set at n_angles incident directions (Section 2.1: eta as a
+ * function of theta0 and theta1).
+ *   theta0, theta1 : [n_angles] glancing angle and azimuth (from a1), degrees; host or device.
+ *   rho_out        : [n_sets][n_angles][N] complex128 rho(0); host or device; may be NULL.
+ *   eta_out        : [n_sets][n_angles][N] float64 intensities; host or device; may be NULL.
+ *   stream         : cudaStream_t (NULL = legacy default stream).
+ * Steps per set: potential table at every kick position (one kernel), then one kernel that
+ * integrates every (set, angle) pair from z_e to 0 with the RHST and assembles rho and eta.
+ * TRH_FP64 computes everything in binary64. TRH_MIXED computes U*Q on the tensor cores
+ * (BF16 3-term split, FP32 accumulation), keeps Q, P and the RHST elimination in double-float
+ * (pairs of FP32, about 48 significant bits) and assembles rho in binary64 with one step of
+ * iterative refinement.
+ * Errors: TRH_EINVAL (n_angles < 1, theta0 outside (0, 90)), TRH_EGRAZING, TRH_ESINGULAR (the
+ * outputs of the failing pairs are NaN; trh_query names the first one), TRH_ETIMEOUT,
+ * TRH_ECUDA. */
+int trh_rocking_curve(trh_ctx* ctx, int n_angles, const double* theta0, const double* theta1,
+                      void* rho_out, double* eta_out, void* stream);
+
+/* Counters of the last call (see trh_stats). Errors: TRH_EINVAL (NULL arguments). */
+int trh_query(const trh_ctx* ctx, trh_stats* out);
+
+/* Static string naming a status code; never NULL. */
+const char* trh_strerror(int status);
+
+/* Message of the last failing call on the calling thread ("" if none); valid until the next
+ * call on this thread. */
+const char* trh_last_error(void);
+
+/* Free the context and its device memory. NULL is accepted. Synchronises the device. */
+void trh_destroy(trh_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRHEED_H */

@@ -53,9 +53,7 @@ def _worker(args):
     return rocking_curve(wl, method, threshold, [a], n_steps, pot)
 
 
-def _init_worker():
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[v] = "1"
+_BLAS_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
 def rocking_curve_parallel(wl, method: str = "sp4", threshold: float = 1000.0, angles=None,
@@ -65,8 +63,21 @@ def rocking_curve_parallel(wl, method: str = "sp4", threshold: float = 1000.0, a
     idx = list(range(len(wl.theta0))) if angles is None else list(angles)
     procs = processes or len(os.sched_getaffinity(0))
     ctx = mpc.get_context("spawn")
-    with ctx.Pool(min(procs, len(idx)), initializer=_init_worker) as pool:
-        parts = pool.map(_worker, [(wl, a, method, threshold, n_steps) for a in idx])
+    # children read the BLAS thread count when they import NumPy, i.e. from the environment
+    # they inherit at spawn time
+    saved = {v: os.environ.get(v) for v in _BLAS_VARS}
+    for v in _BLAS_VARS:
+        os.environ[v] = "1"
+    try:
+        with ctx.Pool(min(procs, len(idx))) as pool:
+            parts = pool.map(_worker, [(wl, a, method, threshold, n_steps) for a in idx],
+                             chunksize=1)
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
     return tuple(np.concatenate([p[k] for p in parts]) for k in range(4))
 
 

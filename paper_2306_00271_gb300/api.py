@@ -1,0 +1,208 @@
+"""Python binding of libtrheed (include/trheed.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels. PyTorch provides device memory
+(tensors' data pointers) and the current CUDA stream. Loading fails loudly when the library is
+missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtrheed.so")
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "trheed.h")
+
+TRH_OK, TRH_EINVAL, TRH_EGRAZING, TRH_ESINGULAR = 0, -1, -2, -3
+TRH_ETIMEOUT, TRH_ENOMEM, TRH_ECUDA, TRH_EUNSUPPORTED = -4, -5, -6, -7
+INTEGRATORS = {"sp4": 0, "sp6": 1, "rk4": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class TrhProblem(C.Structure):
+    _fields_ = [
+        ("particle", C.c_int), ("energy_ev", C.c_double), ("absorption", C.c_double),
+        ("a1", C.c_double * 2), ("a2", C.c_double * 2),
+        ("n_beams", C.c_int), ("beams", C.POINTER(C.c_int)),
+        ("n_atoms", C.c_int), ("atoms", C.POINTER(C.c_double)), ("dw", C.POINTER(C.c_double)),
+        ("species", C.POINTER(C.c_int)), ("n_species", C.c_int), ("sf", C.POINTER(C.c_double)),
+        ("z_e", C.c_double), ("n_steps", C.c_int), ("integrator", C.c_int),
+        ("rhst_threshold", C.c_double), ("precision", C.c_int),
+    ]
+
+
+class TrhStats(C.Structure):
+    _fields_ = [
+        ("n_sets", C.c_int), ("n_angles", C.c_int), ("n_beams", C.c_int), ("n_nodes", C.c_int),
+        ("rhst_total", C.c_longlong), ("rhst_max", C.c_int), ("n_bad", C.c_int),
+        ("first_bad_set", C.c_int), ("first_bad_angle", C.c_int), ("first_bad_status", C.c_int),
+        ("kernels_launched", C.c_int), ("ms_last", C.c_double),
+        ("ms_potential", C.c_double), ("ms_integrate", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TrhError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"trheed error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions include/trheed.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(trh_[a-z_]+)\s*\(", txt)))
+
+
+def load():
+    """Load libtrheed.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2306_00271_gb300.build` (no CPU fallback exists)")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    lib.trh_create.argtypes = [C.POINTER(vp), C.POINTER(TrhProblem)]
+    lib.trh_set_structure.argtypes = [vp, C.c_int, vp, vp]
+    lib.trh_rocking_curve.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+    lib.trh_query.argtypes = [vp, C.POINTER(TrhStats)]
+    lib.trh_strerror.argtypes = [C.c_int]
+    lib.trh_strerror.restype = C.c_char_p
+    lib.trh_last_error.restype = C.c_char_p
+    lib.trh_destroy.argtypes = [vp]
+    lib.trh_destroy.restype = None
+    for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != TRH_OK:
+        lib = load()
+        raise TrhError(code, lib.trh_last_error().decode())
+
+
+def _ptr(a) -> C.c_void_p:
+    if a is None:
+        return C.c_void_p(0)
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+class Engine:
+    """One context of libtrheed: a beam set, slab, integrator and precision, and one or more
+    parameter sets (structures)."""
+
+    def __init__(self, wl, precision: str = "fp64", integrator: str = "sp4",
+                 threshold: float = 1000.0):
+        self.lib = load()
+        self.wl = wl
+        self.N = int(wl.beams.shape[0])
+        self._keep = dict(
+            beams=np.ascontiguousarray(wl.beams, dtype=np.int32),
+            atoms=np.ascontiguousarray(wl.atoms, dtype=np.float64),
+            dw=np.ascontiguousarray(wl.dw, dtype=np.float64),
+            species=np.ascontiguousarray(wl.species, dtype=np.int32),
+            sf=np.ascontiguousarray(wl.sf, dtype=np.float64))
+        k = self._keep
+        p = TrhProblem()
+        p.particle = int(wl.particle)
+        p.energy_ev = float(wl.energy_ev)
+        p.absorption = float(wl.absorption)
+        p.a1[0], p.a1[1] = float(wl.a1[0]), float(wl.a1[1])
+        p.a2[0], p.a2[1] = float(wl.a2[0]), float(wl.a2[1])
+        p.n_beams = self.N
+        p.beams = k["beams"].ctypes.data_as(C.POINTER(C.c_int))
+        p.n_atoms = int(k["atoms"].shape[0])
+        p.atoms = k["atoms"].ctypes.data_as(C.POINTER(C.c_double))
+        p.dw = k["dw"].ctypes.data_as(C.POINTER(C.c_double))
+        p.species = k["species"].ctypes.data_as(C.POINTER(C.c_int))
+        p.n_species = int(k["sf"].shape[0])
+        p.sf = k["sf"].ctypes.data_as(C.POINTER(C.c_double))
+        p.z_e = float(wl.z_e)
+        p.n_steps = int(wl.n_steps)
+        p.integrator = INTEGRATORS[integrator]
+        p.rhst_threshold = float(threshold)
+        p.precision = PRECISIONS[precision]
+        self.n_atoms = p.n_atoms
+        self.n_sets = 1
+        self.ctx = C.c_void_p()
+        _check(self.lib.trh_create(C.byref(self.ctx), C.byref(p)))
+
+    def set_structures(self, atoms, dw=None):
+        """atoms (n_sets, n_atoms, 3) and dw (n_sets, n_atoms): numpy arrays, or CUDA float64
+        tensors (copied on the device; no host round trip)."""
+        if hasattr(atoms, "is_cuda") and atoms.is_cuda:
+            a = atoms.contiguous()
+            d = None if dw is None else dw.contiguous()
+            n_sets = a.numel() // (3 * self.n_atoms)
+            _check(self.lib.trh_set_structure(self.ctx, n_sets, _ptr(a), _ptr(d)))
+            self.n_sets = n_sets
+            return
+        atoms = np.ascontiguousarray(atoms, dtype=np.float64).reshape(-1, self.n_atoms, 3)
+        dwp = None if dw is None else np.ascontiguousarray(dw, dtype=np.float64).reshape(
+            atoms.shape[0], self.n_atoms)
+        _check(self.lib.trh_set_structure(self.ctx, atoms.shape[0], _ptr(atoms), _ptr(dwp)))
+        self.n_sets = atoms.shape[0]
+
+    def rocking_curve(self, theta0, theta1=None, rho=None, eta=None, stream=None):
+        """Device path: theta0/theta1 torch float64 tensors (any device) or arrays; returns
+        (rho, eta) as torch tensors on the current CUDA device, shape (n_sets, A, N)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t0 = torch.as_tensor(theta0, dtype=torch.float64).to(dev).contiguous()
+        t1 = (torch.full_like(t0, float(self.wl.theta1[0])) if theta1 is None
+              else torch.as_tensor(theta1, dtype=torch.float64).to(dev).contiguous())
+        A = t0.numel()
+        if rho is None:
+            rho = torch.empty((self.n_sets, A, self.N), dtype=torch.complex128, device=dev)
+        if eta is None:
+            eta = torch.empty((self.n_sets, A, self.N), dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.trh_rocking_curve(self.ctx, A, _ptr(t0), _ptr(t1), _ptr(rho), _ptr(eta),
+                                          C.c_void_p(st)))
+        return rho, eta
+
+    def rocking_curve_host(self, theta0, theta1=None, rho=None, eta=None, stream=None):
+        """Host path: numpy (or pinned torch) inputs and outputs; the library copies."""
+        t0 = np.ascontiguousarray(np.atleast_1d(theta0), dtype=np.float64)
+        t1 = (np.full_like(t0, float(self.wl.theta1[0])) if theta1 is None
+              else np.ascontiguousarray(np.atleast_1d(theta1), dtype=np.float64))
+        A = t0.size
+        if rho is None:
+            rho = np.empty((self.n_sets, A, self.N), dtype=np.complex128)
+        if eta is None:
+            eta = np.empty((self.n_sets, A, self.N), dtype=np.float64)
+        _check(self.lib.trh_rocking_curve(self.ctx, A, _ptr(t0), _ptr(t1), _ptr(rho), _ptr(eta),
+                                          C.c_void_p(0 if stream is None else stream)))
+        return rho, eta
+
+    def stats(self) -> dict:
+        s = TrhStats()
+        _check(self.lib.trh_query(self.ctx, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.ctx:
+            self.lib.trh_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,548 @@
+// C ABI of libtrheed (declared in include/trheed.h): validation, problem geometry, device
+// buffers and kernel launches. The arithmetic of the method runs in the kernels; this file only
+// prepares the inputs they need (reciprocal rods, the difference map of Eq. sch2, the kick
+// positions of the integrator) and moves data.
+#include "trheed.h"
+#include "internal.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? TRH_ENOMEM : TRH_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define TRH_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kHbarC = 1973.269804;   // eV * Angstrom
+constexpr double kMc2 = 510998.95;       // electron rest energy, eV
+
+// SRKN_6^b and SRKN_11^b (Blanes & Moan 2002), the coefficients of the paper's sp4 / sp6.
+void bab_scheme(int integrator, trh::Scheme* s) {
+  std::vector<double> a, b;
+  if (integrator == TRH_SP4) {
+    const double a1 = 0.209515106613362, a2 = -0.143851773179818, a3 = 0.5 - a1 - a2;
+    const double b1 = 0.0792036964311957, b2 = 0.353172906049774, b3 = -0.0420650803577195;
+    const double b4 = 1.0 - 2.0 * (b1 + b2 + b3);
+    a = {a1, a2, a3, a3, a2, a1};
+    b = {b1, b2, b3, b4, b3, b2, b1};
+  } else {
+    const double aa[5] = {0.123229775946271, 0.290553797799558, -0.127049212625417,
+                          -0.246331761062075, 0.357208872795928};
+    const double bb[5] = {0.0414649985182624, 0.198128671918067, -0.0400061921041533,
+                          0.0752539843015807, -0.0115113874206879};
+    double sa = 0, sb = 0;
+    for (int i = 0; i < 5; ++i) { sa += aa[i]; sb += bb[i]; }
+    for (int i = 0; i < 5; ++i) a.push_back(aa[i]);
+    a.push_back(1.0 - 2.0 * sa);
+    for (int i = 4; i >= 0; --i) a.push_back(aa[i]);
+    for (int i = 0; i < 5; ++i) b.push_back(bb[i]);
+    b.push_back(0.5 - sb);
+    b.push_back(0.5 - sb);
+    for (int i = 4; i >= 0; --i) b.push_back(bb[i]);
+  }
+  s->s = (int)a.size();
+  for (int i = 0; i < s->s; ++i) s->a[i] = a[i];
+  for (int i = 0; i <= s->s; ++i) s->b[i] = b[i];
+}
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t count) {
+    if (count <= n) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct trh_ctx {
+  // problem (host copies)
+  int particle = 0, N = 0, M = 0, n_atoms = 0, n_species = 0, L = 0, integrator = 0, precision = 0;
+  double energy = 0, absorption = 0, z_e = 0, h = 0, threshold = 1000.0;
+  double a1[2] = {0, 0}, a2[2] = {0, 0};
+  std::vector<int> species;
+  std::vector<double> sf;
+  // geometry
+  std::vector<double> kvec;     // [N][2]
+  std::vector<double> gdiff;    // [M][2]
+  std::vector<int> lmap;        // [N][N]
+  std::vector<double> node_z;   // [n_nodes]
+  trh::Scheme scheme{};
+  int n_nodes = 0;
+  double gamma = 0, phi_a1 = 0, area = 0;
+  // parameter sets
+  int n_sets = 0;
+  std::vector<double> atoms, dw;  // [n_sets][n_atoms][3], [n_sets][n_atoms]
+  bool tables_dirty = true;
+  // device
+  DevBuf<double2> d_kvec, d_g, d_u, d_F, d_rho;
+  DevBuf<double> d_atoms, d_dw, d_sf, d_nodes, d_theta, d_eta;
+  DevBuf<int> d_species, d_lmap, d_status;
+  DevBuf<unsigned char> d_img;
+  std::vector<int> h_status;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  trh_stats stats{};
+};
+
+extern "C" {
+
+const char* trh_strerror(int status) {
+  switch (status) {
+    case TRH_OK: return "ok";
+    case TRH_EINVAL: return "invalid argument";
+    case TRH_EGRAZING: return "beam at grazing emergence (Gamma_j = 0)";
+    case TRH_ESINGULAR: return "singular or non-finite pivot";
+    case TRH_ETIMEOUT: return "device wait timed out";
+    case TRH_ENOMEM: return "out of memory";
+    case TRH_ECUDA: return "CUDA error";
+    case TRH_EUNSUPPORTED: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+const char* trh_last_error(void) { return g_last_error.c_str(); }
+
+static int upload_sets(trh_ctx* c) {
+  TRH_CUDA(c->d_atoms.ensure((size_t)c->n_sets * c->n_atoms * 3));
+  TRH_CUDA(c->d_dw.ensure((size_t)c->n_sets * c->n_atoms));
+  TRH_CUDA(cudaMemcpy(c->d_atoms.p, c->atoms.data(), c->atoms.size() * sizeof(double),
+                      cudaMemcpyHostToDevice));
+  TRH_CUDA(cudaMemcpy(c->d_dw.p, c->dw.data(), c->dw.size() * sizeof(double),
+                      cudaMemcpyHostToDevice));
+  TRH_CUDA(c->d_u.ensure((size_t)c->n_sets * c->n_nodes * c->M));
+  TRH_CUDA(c->d_F.ensure((size_t)c->n_sets * c->M * 4 * c->n_atoms));
+  c->tables_dirty = true;
+  return TRH_OK;
+}
+
+int trh_create(trh_ctx** out, const trh_problem* p) {
+  if (!out) return fail(TRH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(TRH_EINVAL, "problem is NULL");
+  if (p->particle != 1 && p->particle != -1) return fail(TRH_EINVAL, "particle must be +1 or -1");
+  if (!(p->energy_ev > 0)) return fail(TRH_EINVAL, "energy must be positive");
+  if (!(p->absorption >= 0)) return fail(TRH_EINVAL, "absorption must be >= 0");
+  if (p->n_beams < 1 || !p->beams) return fail(TRH_EINVAL, "need at least one beam");
+  if (p->beams[0] != 0 || p->beams[1] != 0) return fail(TRH_EINVAL, "beams[0] must be (0,0)");
+  if (p->n_atoms < 1 || !p->atoms || !p->dw || !p->species)
+    return fail(TRH_EINVAL, "atoms, dw and species are required");
+  if (p->n_species < 1 || !p->sf) return fail(TRH_EINVAL, "scattering factors are required");
+  if (!(p->z_e < 0)) return fail(TRH_EINVAL, "z_e must be negative");
+  if (p->n_steps < 1) return fail(TRH_EINVAL, "n_steps must be >= 1");
+  if (p->integrator != TRH_SP4 && p->integrator != TRH_SP6 && p->integrator != TRH_RK4)
+    return fail(TRH_EINVAL, "unknown integrator");
+  if (p->precision != TRH_FP64 && p->precision != TRH_MIXED)
+    return fail(TRH_EINVAL, "unknown precision");
+  if (p->integrator == TRH_RK4) return fail(TRH_EUNSUPPORTED, "RK4 is not implemented on the GPU");
+  if (p->precision == TRH_MIXED && !trh::mixed_available())
+    return fail(TRH_EUNSUPPORTED, "mixed path is not built in this library");
+  if (p->precision == TRH_FP64 && p->n_beams > trh::kMaxBeamsFp64)
+    return fail(TRH_EUNSUPPORTED, "FP64 path supports N <= %d", trh::kMaxBeamsFp64);
+  if (p->precision == TRH_MIXED && p->n_beams > trh::kMaxBeamsMixed)
+    return fail(TRH_EUNSUPPORTED, "mixed path supports N <= %d", trh::kMaxBeamsMixed);
+  const double det = p->a1[0] * p->a2[1] - p->a1[1] * p->a2[0];
+  if (!(std::fabs(det) > 0)) return fail(TRH_EINVAL, "lattice vectors are parallel");
+  for (int a = 0; a < p->n_atoms; ++a) {
+    if (p->species[a] < 0 || p->species[a] >= p->n_species)
+      return fail(TRH_EINVAL, "species[%d] out of range", a);
+    if (!(p->atoms[3 * a + 2] <= 0)) return fail(TRH_EINVAL, "atom %d above the surface", a);
+    if (!(p->dw[a] >= 0)) return fail(TRH_EINVAL, "dw[%d] < 0", a);
+  }
+  for (int s = 0; s < p->n_species; ++s)
+    for (int i = 0; i < 4; ++i)
+      if (!(p->sf[8 * s + 4 + i] > 0)) return fail(TRH_EINVAL, "scattering b must be > 0");
+
+  trh_ctx* c = new trh_ctx();
+  c->particle = p->particle;
+  c->energy = p->energy_ev;
+  c->absorption = p->absorption;
+  c->N = p->n_beams;
+  c->n_atoms = p->n_atoms;
+  c->n_species = p->n_species;
+  c->z_e = p->z_e;
+  c->L = p->n_steps;
+  c->h = -p->z_e / p->n_steps;
+  c->integrator = p->integrator;
+  c->precision = p->precision;
+  c->threshold = p->rhst_threshold > 0 ? p->rhst_threshold : 1000.0;
+  for (int i = 0; i < 2; ++i) { c->a1[i] = p->a1[i]; c->a2[i] = p->a2[i]; }
+  c->species.assign(p->species, p->species + p->n_atoms);
+  c->sf.assign(p->sf, p->sf + 8 * p->n_species);
+
+  // reciprocal basis b_i . a_j = 2 pi delta_ij and rods k_j
+  const double b1x = 2 * kPi * p->a2[1] / det, b1y = -2 * kPi * p->a2[0] / det;
+  const double b2x = -2 * kPi * p->a1[1] / det, b2y = 2 * kPi * p->a1[0] / det;
+  c->kvec.resize(2 * c->N);
+  std::map<std::pair<int, int>, int> seen;
+  for (int j = 0; j < c->N; ++j) {
+    const int m1 = p->beams[2 * j], m2 = p->beams[2 * j + 1];
+    if (!seen.emplace(std::make_pair(m1, m2), j).second) {
+      delete c;
+      return fail(TRH_EINVAL, "beam %d duplicates another", j);
+    }
+    c->kvec[2 * j] = m1 * b1x + m2 * b2x;
+    c->kvec[2 * j + 1] = m1 * b1y + m2 * b2y;
+  }
+  // distinct differences g_j - g_k and the index map l(j, k) of Eq. sch2
+  std::map<std::pair<int, int>, int> diffs;
+  c->lmap.resize((size_t)c->N * c->N);
+  for (int j = 0; j < c->N; ++j)
+    for (int k = 0; k < c->N; ++k) {
+      const auto key = std::make_pair(p->beams[2 * j] - p->beams[2 * k],
+                                      p->beams[2 * j + 1] - p->beams[2 * k + 1]);
+      auto it = diffs.find(key);
+      int id;
+      if (it == diffs.end()) {
+        id = (int)diffs.size();
+        diffs.emplace(key, id);
+      } else {
+        id = it->second;
+      }
+      c->lmap[(size_t)j * c->N + k] = id;
+    }
+  c->M = (int)diffs.size();
+  c->gdiff.resize(2 * c->M);
+  for (const auto& kv : diffs) {
+    c->gdiff[2 * kv.second] = kv.first.first * b1x + kv.first.second * b2x;
+    c->gdiff[2 * kv.second + 1] = kv.first.first * b1y + kv.first.second * b2y;
+  }
+  // kick positions: node s*i + r at z_i + c_r h (c_r = a_0 + ... + a_{r-1}), last node at 0
+  bab_scheme(c->integrator, &c->scheme);
+  const int s = c->scheme.s;
+  c->n_nodes = s * c->L + 1;
+  c->node_z.resize(c->n_nodes);
+  std::vector<double> cr(s, 0.0);
+  for (int r = 1; r < s; ++r) cr[r] = cr[r - 1] + c->scheme.a[r - 1];
+  for (int i = 0; i < c->L; ++i)
+    for (int r = 0; r < s; ++r) c->node_z[(size_t)s * i + r] = c->z_e + i * c->h + cr[r] * c->h;
+  c->node_z[(size_t)s * c->L] = c->z_e + c->L * c->h;
+
+  const double E = c->energy;
+  c->gamma = std::sqrt(E * E + 2.0 * E * kMc2) / kHbarC;
+  c->phi_a1 = std::atan2(p->a1[1], p->a1[0]);
+  c->area = std::fabs(det);
+
+  c->n_sets = 1;
+  c->atoms.assign(p->atoms, p->atoms + 3 * p->n_atoms);
+  c->dw.assign(p->dw, p->dw + p->n_atoms);
+
+  int dev_count = 0;
+  cudaError_t e = cudaGetDeviceCount(&dev_count);
+  if (e != cudaSuccess || dev_count < 1) {
+    cudaGetLastError();
+    delete c;
+    return fail(TRH_ECUDA, "no CUDA device available");
+  }
+  int rc = TRH_OK;
+#define TRY(call)                          \
+  do {                                     \
+    cudaError_t e_ = (call);               \
+    if (e_ != cudaSuccess) {               \
+      rc = cuda_fail(e_, #call);           \
+      goto failed;                         \
+    }                                      \
+  } while (0)
+  TRY(c->d_kvec.ensure(c->N));
+  TRY(c->d_g.ensure(c->M));
+  TRY(c->d_lmap.ensure((size_t)c->N * c->N));
+  TRY(c->d_nodes.ensure(c->n_nodes));
+  TRY(c->d_sf.ensure(c->sf.size()));
+  TRY(c->d_species.ensure(c->n_atoms));
+  TRY(cudaMemcpy(c->d_kvec.p, c->kvec.data(), c->kvec.size() * 8, cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(c->d_g.p, c->gdiff.data(), c->gdiff.size() * 8, cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(c->d_lmap.p, c->lmap.data(), c->lmap.size() * 4, cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(c->d_nodes.p, c->node_z.data(), c->node_z.size() * 8, cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(c->d_sf.p, c->sf.data(), c->sf.size() * 8, cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(c->d_species.p, c->species.data(), c->species.size() * 4,
+                 cudaMemcpyHostToDevice));
+#undef TRY
+  rc = upload_sets(c);
+  if (rc != TRH_OK) goto failed;
+  c->stats.n_beams = c->N;
+  c->stats.n_nodes = c->n_nodes;
+  c->stats.n_sets = c->n_sets;
+  c->stats.first_bad_set = c->stats.first_bad_angle = -1;
+  *out = c;
+  return TRH_OK;
+failed:
+  trh_destroy(c);
+  return rc;
+}
+
+int trh_set_structure(trh_ctx* c, int n_sets, const double* atoms, const double* dw) {
+  if (!c || !atoms || n_sets < 1) return fail(TRH_EINVAL, "bad arguments");
+  const size_t na = (size_t)n_sets * c->n_atoms;
+  if (is_device_ptr(atoms)) {
+    if (dw && !is_device_ptr(dw)) return fail(TRH_EINVAL, "atoms and dw must be on one side");
+    TRH_CUDA(c->d_atoms.ensure(na * 3));
+    TRH_CUDA(c->d_dw.ensure(na));
+    TRH_CUDA(cudaMemcpy(c->d_atoms.p, atoms, na * 3 * sizeof(double), cudaMemcpyDeviceToDevice));
+    if (dw) {
+      TRH_CUDA(cudaMemcpy(c->d_dw.p, dw, na * sizeof(double), cudaMemcpyDeviceToDevice));
+    } else {
+      std::vector<double> dwv(na);
+      for (size_t a = 0; a < na; ++a) dwv[a] = c->dw[a % c->n_atoms];
+      TRH_CUDA(cudaMemcpy(c->d_dw.p, dwv.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    c->n_sets = n_sets;
+    c->stats.n_sets = n_sets;
+    TRH_CUDA(c->d_u.ensure((size_t)n_sets * c->n_nodes * c->M));
+    TRH_CUDA(c->d_F.ensure((size_t)n_sets * c->M * 4 * c->n_atoms));
+    c->tables_dirty = true;
+    return TRH_OK;
+  }
+  for (size_t a = 0; a < na; ++a) {
+    if (!(atoms[3 * a + 2] <= 0)) return fail(TRH_EINVAL, "atom %zu above the surface", a);
+    if (dw && !(dw[a] >= 0)) return fail(TRH_EINVAL, "dw[%zu] < 0", a);
+  }
+  std::vector<double> dwv(na);
+  for (size_t a = 0; a < na; ++a) dwv[a] = dw ? dw[a] : c->dw[a % c->n_atoms];
+  c->atoms.assign(atoms, atoms + 3 * na);
+  c->dw.swap(dwv);
+  c->n_sets = n_sets;
+  c->stats.n_sets = n_sets;
+  return upload_sets(c);
+}
+
+int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
+                      void* rho_out, double* eta_out, void* stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!c || n_angles < 1 || !theta0 || !theta1) return fail(TRH_EINVAL, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  int launched = 0;
+  const bool dev_t0 = is_device_ptr(theta0), dev_t1 = is_device_ptr(theta1);
+  if (!dev_t0) {
+    for (int a = 0; a < n_angles; ++a)
+      if (!(theta0[a] > 0 && theta0[a] < 90))
+        return fail(TRH_EINVAL, "theta0[%d] = %g outside (0, 90)", a, theta0[a]);
+  }
+  const size_t pairs = (size_t)c->n_sets * n_angles;
+  TRH_CUDA(c->d_theta.ensure(2 * (size_t)n_angles));
+  TRH_CUDA(cudaMemcpyAsync(c->d_theta.p, theta0, n_angles * 8,
+                           dev_t0 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  TRH_CUDA(cudaMemcpyAsync(c->d_theta.p + n_angles, theta1, n_angles * 8,
+                           dev_t1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  if (!c->ev[0])
+    for (int i = 0; i < 4; ++i) TRH_CUDA(cudaEventCreate(&c->ev[i]));
+  const bool rebuilt = c->tables_dirty;
+  if (c->tables_dirty) {
+    TRH_CUDA(cudaEventRecord(c->ev[0], st));
+    trh::PotentialParams pp{};
+    pp.g = c->d_g.p;
+    pp.atoms = c->d_atoms.p;
+    pp.dw = c->d_dw.p;
+    pp.species = c->d_species.p;
+    pp.sf = c->d_sf.p;
+    pp.node_z = c->d_nodes.p;
+    const double gl = 1.0 + c->energy / kMc2;
+    const double scale = 4.0 * kPi * gl / c->area;
+    pp.pref = make_double2(c->particle * scale, -c->absorption * scale);
+    pp.M = c->M;
+    pp.n_atoms = c->n_atoms;
+    pp.n_nodes = c->n_nodes;
+    pp.n_sets = c->n_sets;
+    pp.F = c->d_F.p;
+    pp.u = c->d_u.p;
+    pp.u32 = nullptr;
+    TRH_CUDA(trh::launch_potential(pp, st, &launched));
+    if (c->precision == TRH_MIXED) {
+      TRH_CUDA(c->d_img.ensure((size_t)c->n_sets * c->n_nodes * trh::mixed_image_bytes_per_node()));
+      trh::MixedImageParams mp{};
+      mp.u = c->d_u.p;
+      mp.lmap = c->d_lmap.p;
+      mp.img = c->d_img.p;
+      mp.N = c->N;
+      mp.M = c->M;
+      mp.n_nodes = c->n_nodes;
+      mp.n_sets = c->n_sets;
+      TRH_CUDA(trh::launch_umma_images(mp, st, &launched));
+    }
+    TRH_CUDA(cudaEventRecord(c->ev[1], st));
+    c->tables_dirty = false;
+  }
+  const bool dev_rho = is_device_ptr(rho_out), dev_eta = is_device_ptr(eta_out);
+  double2* rho = dev_rho ? (double2*)rho_out : nullptr;
+  double* eta = dev_eta ? eta_out : nullptr;
+  if (!rho) {
+    TRH_CUDA(c->d_rho.ensure(pairs * c->N));
+    rho = c->d_rho.p;
+  }
+  if (!eta) {
+    TRH_CUDA(c->d_eta.ensure(pairs * c->N));
+    eta = c->d_eta.p;
+  }
+  TRH_CUDA(c->d_status.ensure(2 * pairs));
+  trh::IntegrateParams ip{};
+  ip.sch = c->scheme;
+  ip.ang.theta0 = c->d_theta.p;
+  ip.ang.theta1 = c->d_theta.p + n_angles;
+  ip.ang.kvec = c->d_kvec.p;
+  ip.ang.gamma = c->gamma;
+  ip.ang.phi_a1 = c->phi_a1;
+  ip.ang.n_angles = n_angles;
+  ip.out.rho = rho;
+  ip.out.eta = eta;
+  ip.out.status = c->d_status.p;
+  ip.out.n_rhst = c->d_status.p + pairs;
+  ip.u = c->d_u.p;
+  ip.lmap = c->d_lmap.p;
+  ip.N = c->N;
+  ip.M = c->M;
+  ip.n_nodes = c->n_nodes;
+  ip.n_sets = c->n_sets;
+  ip.L = c->L;
+  ip.h = c->h;
+  ip.threshold = c->threshold;
+  TRH_CUDA(cudaEventRecord(c->ev[2], st));
+  if (c->precision == TRH_MIXED) {
+    trh::MixedParams mp{};
+    mp.sch = ip.sch;
+    mp.ang = ip.ang;
+    mp.out = ip.out;
+    mp.img = c->d_img.p;
+    mp.N = c->N;
+    mp.n_nodes = c->n_nodes;
+    mp.n_sets = c->n_sets;
+    mp.L = c->L;
+    mp.n_mma = (c->N + 15) / 16 * 16;
+    mp.k_slices = (2 * c->N + 15) / 16;
+    mp.h = c->h;
+    mp.threshold = c->threshold;
+    const int sc = c->scheme.s;
+    auto split = [](double v, float* hi, float* lo) {
+      *hi = (float)v;
+      *lo = (float)(v - (double)*hi);
+    };
+    split(c->h * c->scheme.b[0], &mp.kick_hi[0], &mp.kick_lo[0]);
+    for (int r = 1; r < sc; ++r) split(c->h * c->scheme.b[r], &mp.kick_hi[r], &mp.kick_lo[r]);
+    split(c->h * (c->scheme.b[sc] + c->scheme.b[0]), &mp.kick_hi[sc], &mp.kick_lo[sc]);
+    split(c->h * c->scheme.b[sc], &mp.kick_hi[sc + 1], &mp.kick_lo[sc + 1]);
+    for (int r = 0; r < sc; ++r) split(c->h * c->scheme.a[r], &mp.drift_hi[r], &mp.drift_lo[r]);
+    TRH_CUDA(trh::launch_integrate_mixed(mp, st, &launched));
+  } else {
+    TRH_CUDA(trh::launch_integrate_fp64(ip, st, &launched));
+  }
+  TRH_CUDA(cudaEventRecord(c->ev[3], st));
+  if (rho_out && !dev_rho)
+    TRH_CUDA(cudaMemcpyAsync(rho_out, rho, pairs * c->N * sizeof(double2),
+                             cudaMemcpyDeviceToHost, st));
+  if (eta_out && !dev_eta)
+    TRH_CUDA(cudaMemcpyAsync(eta_out, eta, pairs * c->N * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+  c->h_status.resize(2 * pairs);
+  TRH_CUDA(cudaMemcpyAsync(c->h_status.data(), c->d_status.p, 2 * pairs * sizeof(int),
+                           cudaMemcpyDeviceToHost, st));
+  TRH_CUDA(cudaStreamSynchronize(st));
+  trh_stats& S = c->stats;
+  S.n_angles = n_angles;
+  S.rhst_total = 0;
+  S.rhst_max = 0;
+  S.n_bad = 0;
+  S.first_bad_set = S.first_bad_angle = -1;
+  S.first_bad_status = TRH_OK;
+  for (size_t q = 0; q < pairs; ++q) {
+    const int stq = c->h_status[q], nr = c->h_status[pairs + q];
+    S.rhst_total += nr;
+    if (nr > S.rhst_max) S.rhst_max = nr;
+    if (stq != 0) {
+      if (S.n_bad == 0) {
+        S.first_bad_set = (int)(q / n_angles);
+        S.first_bad_angle = (int)(q % n_angles);
+        S.first_bad_status = stq;
+      }
+      S.n_bad++;
+    }
+  }
+  S.kernels_launched = launched;
+  float ms = 0.f;
+  S.ms_potential = 0.0;
+  if (rebuilt && cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) S.ms_potential = ms;
+  S.ms_integrate = (cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]) == cudaSuccess) ? ms : 0.0;
+  S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
+                  .count();
+  if (S.n_bad)
+    return fail(S.first_bad_status, "%d (set, angle) pairs failed; first: set %d angle %d (%s)",
+                S.n_bad, S.first_bad_set, S.first_bad_angle, trh_strerror(S.first_bad_status));
+  return TRH_OK;
+}
+
+int trh_query(const trh_ctx* c, trh_stats* out) {
+  if (!c || !out) return fail(TRH_EINVAL, "bad arguments");
+  *out = c->stats;
+  return TRH_OK;
+}
+
+void trh_destroy(trh_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (int i = 0; i < 4; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  c->d_kvec.release();
+  c->d_g.release();
+  c->d_u.release();
+  c->d_F.release();
+  c->d_rho.release();
+  c->d_atoms.release();
+  c->d_dw.release();
+  c->d_sf.release();
+  c->d_nodes.release();
+  c->d_theta.release();
+  c->d_eta.release();
+  c->d_species.release();
+  c->d_lmap.release();
+  c->d_status.release();
+  c->d_img.release();
+  delete c;
+}
+
+}  // extern "C"

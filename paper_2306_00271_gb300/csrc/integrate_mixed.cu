@@ -1,0 +1,739 @@
+// Mixed-precision path: one CTA integrates one (parameter set, angle) pair (Algorithm 1) with the
+// kick products U(tau) Q on the 5th-generation tensor cores, accumulated exactly.
+//
+// Real-ified complex product. Rows and columns interleave real and imaginary parts: real row
+// 2j+p is part p of beam j, so
+//   A[2j+p][2k+q] = [[Re U_jk, -Im U_jk], [Im U_jk, Re U_jk]][p][q]     (M = K = 128, N <= 64)
+//   B[2k+q][c]    = part q of Q_kc                                       (K = 128, n columns)
+//   D = A B       = real-ified W = U Q, with D[2j+p][c] = part p of W_jc
+// so TMEM lane 2j+p holds part p of row j and a lane pair (2j, 2j+1) holds whole complex numbers.
+//
+// Exact tensor-core accumulation. The FP32 accumulation of the tensor cores truncates the addends
+// it aligns, which biases every product towards zero; accumulated over thousands of kicks this
+// bias dominates the error. So the operands are written as fixed-point digits: each row i of A
+// has a power-of-two scale alpha_i >= max_k |A_ik| and each column c of B a power-of-two scale
+// gamma_c >= max_k |B_kc|, and the scaled entries are cut into four signed 8-bit digits
+// x / scale = (d0 + d1 / 2^8 + d2 / 2^16 + d3 / 2^24) / 2^7 with |d| <= 128 (exact in BF16).
+// Every digit product is an integer below 2^14 in magnitude; the products of each order
+// o = a + b <= 3 (digit a of A times digit b of B) are summed over K = 128 in their own TMEM
+// accumulator D_o, which stays below 2^24, so the tensor cores add them without any rounding.
+// The epilogue forms
+//   W_ic = alpha_i gamma_c 2^-14 (D_0 + 2^-8 (D_1 + 2^-8 (D_2 + 2^-8 D_3)))
+// with round-to-nearest FP32 arithmetic. The fourth digit matters: with three, entries two or
+// three orders of magnitude below their row or column maximum keep too few bits, and the rocking
+// curves drift by ~1e-6; with four the error is at the FP32 level (unbiased).
+//
+// State: Q and P as double-float pairs (hi, lo FP32; about 48 significant bits) in registers; the
+// kick P <- P - hb W - (hb Gamma^2) Q and the drift Q <- Q + ha P are exact to that precision.
+//
+// Per kick: every thread waits for the bulk copy of U(tau)'s digit image (128 KB + row scales, TMA
+// engine); thread 0 issues 10 x 8 tcgen05.mma (128 x n x 16) into the four accumulators and
+// commits to an mbarrier; the next image is fetched as soon as the MMAs are done, overlapping the
+// epilogue. The epilogue (16 warps; warp w reads TMEM lanes 32(w%4).. and columns 16(w/4)..)
+// applies the kick and the drift, takes the exact column maxima of the new Q (warp reductions,
+// then shared memory) and writes its digits as the next B operand.
+//
+// Per step: the Varah bound xi of Q (FP32); if xi > threshold the RHST Z <- Z T with T = Q^{-1}
+// computed by FP32 Gauss-Jordan elimination (any invertible T leaves rho unchanged, Section 3.2,
+// so an approximate inverse is as valid as the exact one) and Z T applied in double-float
+// arithmetic, with TMEM as the row-gather workspace. At the end rho is assembled in FP64 with one
+// step of iterative refinement.
+#include "dense_fp64.cuh"
+#include "internal.h"
+#include "umma.cuh"
+
+namespace trh {
+
+namespace {
+
+using namespace umma;
+
+constexpr int NT = 512;
+constexpr int CPT = 16;                      // columns per thread
+constexpr int MT = 128;
+constexpr int KT = 128;
+constexpr int NC = 64;
+constexpr int A_LBO = 128, A_SBO = 16 * 128;
+constexpr int NDIG = 4;                      // fixed-point digits per operand
+constexpr int A_TERM = MT * KT * 2;          // one digit plane of A
+constexpr int A_DIGITS = NDIG * A_TERM;      // 128 KB
+constexpr int A_SCALES = MT * 4;             // row scales
+constexpr int IMG_BYTES = A_DIGITS + A_SCALES;
+constexpr int B_LBO = 144, B_SBO = 16 * 144;  // padded K-block stride: conflict-free stores
+constexpr int B_TERM = (NC / 8) * B_SBO;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TM_D0 = 0, TM_D1 = 64, TM_D2 = 128, TM_D3 = 192;
+constexpr uint32_t TM_QH = 256, TM_QL = 320, TM_PH = 384, TM_PL = 448;
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+constexpr double kPi = 3.14159265358979323846;
+constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23: x + M - M rounds x to an integer
+
+struct __align__(128) Smem {
+  unsigned char A[A_DIGITS];    // U(tau) digit planes; FP64 LU workspace at the end
+  unsigned char B[NDIG * B_TERM];  // digit planes of Q; FP32 T = Q^{-1} during the RHST
+  float alpha[2][MT];           // row scales of A, double-buffered with the image
+  float gamma[NC];              // column scales of the current B
+  uint32_t colmax[4][NC];       // per-quadrant column maxima (float bits of |Q|)
+  uint64_t bar_tma, bar_mma;
+  uint32_t tmem_base;
+  int status, flag, n_rhst;
+  int piv[NC];
+  float rowsum[4][NC], diag[NC];
+  float redf[4];
+  double gam2[NC], Gr[NC], Gi[NC];
+  float2 frow[NC], fcol[NC];
+  double2 xv[NC], rv[NC];
+  double psum[4][MT];
+};
+
+// Error-free transformations. The explicit _rn intrinsics are never contracted into FMAs: a
+// contraction would make the rounded sum differ from the one the error term assumes.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ float rint_magic(float x) {  // |x| < 2^22, round to nearest even
+  return __fsub_rn(__fadd_rn(x, kMagic), kMagic);
+}
+
+// Smallest power of two >= x (x > 0 finite); 1 for x == 0.
+__device__ __forceinline__ float pow2_ceil(float x) {
+  if (!(x > 0.0f)) return 1.0f;
+  const uint32_t b = __float_as_uint(x);
+  uint32_t e = b & 0x7F800000u;
+  if (b & 0x007FFFFFu) e += 0x00800000u;
+  return __uint_as_float(e);
+}
+
+// Fixed-point digits of v = x / scale (|v| <= 1): BF16 bit patterns of d0..d3. The remainders
+// are exact in FP32 (power-of-two scalings and differences of nearby values).
+__device__ __forceinline__ void digits4(float x, float inv_scale, uint16_t (&b)[NDIG]) {
+  float v = __fmul_rn(__fmul_rn(x, inv_scale), 128.0f);
+#pragma unroll
+  for (int i = 0; i < NDIG; ++i) {
+    const float d = rint_magic(v);
+    // integers of magnitude <= 256 have zero low halves: the BF16 pattern is the top 16 bits
+    b[i] = (uint16_t)(__float_as_uint(d) >> 16);
+    v = __fmul_rn(__fsub_rn(v, d), 256.0f);
+  }
+}
+
+// Column maxima of |Qh| over the 128 real-ified rows -> power-of-two scales, then the digit
+// planes of B. One block barrier inside; all threads call it.
+__device__ __forceinline__ void write_b_digits(Smem& S, const float (&qh)[CPT], int m, int c0,
+                                               int qd, int lane) {
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const uint32_t mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(qh[i])));
+    if (lane == i) S.colmax[qd][c0 + i] = mx;
+  }
+  __syncthreads();
+  float inv[CPT];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const uint32_t a = max(max(S.colmax[0][c0 + i], S.colmax[1][c0 + i]),
+                           max(S.colmax[2][c0 + i], S.colmax[3][c0 + i]));
+    const float g = pow2_ceil(__uint_as_float(a));
+    inv[i] = 1.0f / g;  // exact: g is a power of two
+    if (qd == 0 && lane == i) S.gamma[c0 + i] = g;
+  }
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = c0 + i;
+    uint16_t b[NDIG];
+    digits4(qh[i], inv[i], b);
+    const int off = (c >> 3) * B_SBO + (m >> 3) * B_LBO + (c & 7) * 16 + (m & 7) * 2;
+#pragma unroll
+    for (int t = 0; t < NDIG; ++t) *reinterpret_cast<uint16_t*>(S.B + t * B_TERM + off) = b[t];
+  }
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// In-place inverse of the n x n complex FP32 matrix T (row stride NC) by Gauss-Jordan elimination
+// with row pivoting; the row interchanges are undone on the columns in reverse order at the end.
+__device__ void gj_invert(Smem& S, float2* T, int n) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      float best = -1.0f;
+      int bi = k;
+      for (int r = k + lane; r < n; r += 32) {
+        const float2 a = T[r * NC + k];
+        const float m2 = a.x * a.x + a.y * a.y;
+        if (m2 > best) {
+          best = m2;
+          bi = r;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > best || (v2 == best && i2 < bi)) {
+          best = v2;
+          bi = i2;
+        }
+      }
+      if (lane == 0) {
+        S.piv[k] = bi;
+        if (!(best > 0.0f) || !isfinite(best)) S.status = kSingular;
+      }
+    }
+    __syncthreads();
+    if (S.status != kOk) return;
+    const int pr = S.piv[k];
+    if (pr != k) {
+      for (int c = tid; c < n; c += NT) {
+        const float2 t = T[k * NC + c];
+        T[k * NC + c] = T[pr * NC + c];
+        T[pr * NC + c] = t;
+      }
+      __syncthreads();
+    }
+    {
+      const float2 a = T[k * NC + k];
+      const float d = a.x * a.x + a.y * a.y;
+      const float2 inv = make_float2(a.x / d, -a.y / d);
+      for (int c = tid; c < n; c += NT) {
+        const float2 t = T[k * NC + c];
+        S.frow[c] = (c == k) ? inv
+                             : make_float2(t.x * inv.x - t.y * inv.y, t.x * inv.y + t.y * inv.x);
+        S.fcol[c] = (c == k) ? make_float2(0.f, 0.f) : T[c * NC + k];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += NT) {
+      const int r = e / n, c = e - r * n;
+      const float2 fr = S.frow[c];
+      if (r == k) {
+        T[r * NC + c] = fr;
+      } else {
+        const float2 fc = S.fcol[r];
+        float2 t = (c == k) ? make_float2(0.f, 0.f) : T[r * NC + c];
+        t.x -= fc.x * fr.x - fc.y * fr.y;
+        t.y -= fc.x * fr.y + fc.y * fr.x;
+        T[r * NC + c] = t;
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int pr = S.piv[k];
+    if (pr != k) {
+      for (int r = tid; r < n; r += NT) {
+        const float2 t = T[r * NC + k];
+        T[r * NC + k] = T[r * NC + pr];
+        T[r * NC + pr] = t;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// out = Z T for this thread's part of row j and its CPT columns, Z read from TMEM (hi at col_h,
+// lo at col_l) in double-float, T (FP32) from shared memory; products are exact (FMA residual)
+// and summed with error-free additions.
+__device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32_t col_h,
+                                        uint32_t col_l, int part, int c0, int n,
+                                        float (&oh)[CPT], float (&ol)[CPT]) {
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) oh[i] = ol[i] = 0.0f;
+  for (int kc = 0; kc < n; kc += 8) {
+    float zh[8], zl[8], ph[8], pl[8];
+    tmem_ld8(t_lane + col_h + kc, zh);
+    tmem_ld8(t_lane + col_l + kc, zl);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      ph[kk] = __shfl_xor_sync(0xffffffffu, zh[kk], 1);
+      pl[kk] = __shfl_xor_sync(0xffffffffu, zl[kk], 1);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      if (kc + kk >= n) break;
+      // part 0: Re = zr tr - zi ti ; part 1: Im = zr ti + zi tr
+      const float zrh = part ? ph[kk] : zh[kk], zrl = part ? pl[kk] : zl[kk];
+      const float zih = part ? zh[kk] : ph[kk], zil = part ? zl[kk] : pl[kk];
+      const float x2h = part ? zih : -zih, x2l = part ? zil : -zil;
+      const float2* Trow = T + (kc + kk) * NC + c0;
+#pragma unroll
+      for (int i = 0; i < CPT; ++i) {
+        const float2 t = Trow[i];
+        const float y1 = part ? t.y : t.x;
+        const float y2 = part ? t.x : t.y;
+        const float p1 = __fmul_rn(zrh, y1);
+        float e1 = fmaf(zrh, y1, -p1);
+        e1 = fmaf(zrl, y1, e1);
+        const float p2 = __fmul_rn(x2h, y2);
+        float e2 = fmaf(x2h, y2, -p2);
+        e2 = fmaf(x2l, y2, e2);
+        float s, e, s2, e3;
+        two_sum(oh[i], p1, s, e);
+        two_sum(s, p2, s2, e3);
+        oh[i] = s2;
+        ol[i] = __fadd_rn(ol[i], __fadd_rn(__fadd_rn(e, e3), __fadd_rn(e1, e2)));
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    float s, e;
+    quick_two_sum(oh[i], ol[i], s, e);
+    const bool live = (c0 + i) < n;
+    oh[i] = live ? s : 0.0f;
+    ol[i] = live ? e : 0.0f;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int qd = warp & 3, cq = warp >> 2;
+  const int m = 32 * qd + lane;  // real-ified row = TMEM lane
+  const int j = m >> 1, part = m & 1;
+  const int c0 = CPT * cq;
+  const int angle = blockIdx.x, set = blockIdx.y;
+  const int N = p.N;
+  const size_t pair = (size_t)set * p.ang.n_angles + angle;
+  const unsigned char* img_set = p.img + (size_t)set * p.n_nodes * IMG_BYTES;
+
+  if (tid == 0) {
+    S.status = kOk;
+    S.n_rhst = 0;
+    mbar_init(&S.bar_tma, 1);
+    mbar_init(&S.bar_mma, 1);
+    mbar_fence_init();
+  }
+  // Row A1: Gamma for this angle (binary64)
+  const double t0 = p.ang.theta0[angle] * (kPi / 180.0);
+  const double phi = p.ang.phi_a1 + p.ang.theta1[angle] * (kPi / 180.0);
+  const double sin_t0 = sin(t0);
+  const double bmag = p.ang.gamma * cos(t0);
+  const double b0x = bmag * cos(phi), b0y = bmag * sin(phi);
+  if (tid < NC) {
+    double g2 = 0.0, gr = 0.0, gi = 0.0;
+    if (tid < N) {
+      const double qx = b0x + p.ang.kvec[tid].x, qy = b0y + p.ang.kvec[tid].y;
+      g2 = p.ang.gamma * p.ang.gamma - (qx * qx + qy * qy);
+      if (g2 >= 0.0) gr = sqrt(g2);
+      else gi = -sqrt(-g2);
+      if (fabs(g2) < 1e-12 * p.ang.gamma * p.ang.gamma) S.status = kGrazing;
+    }
+    S.gam2[tid] = g2;
+    S.Gr[tid] = gr;
+    S.Gi[tid] = gi;
+  }
+  if (warp == 0) tmem_alloc(&S.tmem_base, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+  const uint32_t t_lane = tmem + ((uint32_t)(32 * qd) << 16);
+  const double g2d = (j < N) ? S.gam2[j] : 0.0;
+  const float g2h = (float)g2d, g2l = (float)(g2d - (double)g2h);
+
+  // initial value [I; i Gamma]
+  float Qh[CPT], Ql[CPT], Ph[CPT], Pl[CPT];
+  {
+    const double pv = (j < N) ? (part ? S.Gr[j] : -S.Gi[j]) : 0.0;
+    const float pvh = (float)pv, pvl = (float)(pv - (double)pvh);
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+      const bool dg = (j < N) && (c0 + i == j);
+      Qh[i] = (dg && part == 0) ? 1.0f : 0.0f;
+      Ql[i] = 0.0f;
+      Ph[i] = dg ? pvh : 0.0f;
+      Pl[i] = dg ? pvl : 0.0f;
+    }
+  }
+  write_b_digits(S, Qh, m, c0, qd, lane);
+  fence_proxy_async_smem();
+  bool tma_pending = false;
+  if (tid == 0 && S.status == kOk) {
+    mbar_arrive_expect_tx(&S.bar_tma, IMG_BYTES);
+    bulk_g2s(S.A, img_set, A_DIGITS, &S.bar_tma);
+    bulk_g2s(S.alpha[0], img_set + A_DIGITS, A_SCALES, &S.bar_tma);
+    tma_pending = true;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  uint32_t ph_tma = 0, ph_mma = 0;
+  const int s = p.sch.s;
+  const uint32_t idesc = idesc_bf16_f32(MT, p.n_mma);
+  const uint32_t a_base = smem_u32(S.A), b_base = smem_u32(S.B);
+  int abort = (S.status != kOk);
+  int kick_no = 0;
+
+  for (int i = 0; i <= p.L && !abort; ++i) {
+    const bool last = (i == p.L);
+    const int nk = last ? 1 : s;
+    for (int r = 0; r < nk; ++r, ++kick_no) {
+      const int kidx = last ? s + 1 : (r > 0 ? r : (i == 0 ? 0 : s));
+      const int next = last ? -1 : s * i + r + 1;
+      int to = 0;
+      // every thread waits for this node's image (it reads the row scale below)
+      if (mbar_wait(&S.bar_tma, ph_tma, kWaitCycles)) {
+        ph_tma ^= 1;
+        if (tid == 0) tma_pending = false;
+      } else {
+        to = 1;  // the copy stays pending; it is drained before exit
+      }
+      const float alpha_m = S.alpha[kick_no & 1][m];
+      if (tid == 0) {
+        if (!to) {
+          tc_fence_after();
+          // orders 0..3 of the digit products, each in its own accumulator
+          const int ta[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+          const int tb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+          const uint32_t dcol[10] = {TM_D0, TM_D1, TM_D1, TM_D2, TM_D2,
+                                     TM_D2, TM_D3, TM_D3, TM_D3, TM_D3};
+          const bool first[10] = {true, true, false, true, false, false, true, false, false, false};
+          for (int t = 0; t < 10; ++t)
+            for (int ks = 0; ks < p.k_slices; ++ks) {
+              const uint64_t ad = smem_desc(a_base + ta[t] * A_TERM + ks * 2 * A_LBO, A_LBO, A_SBO);
+              const uint64_t bd = smem_desc(b_base + tb[t] * B_TERM + ks * 2 * B_LBO, B_LBO, B_SBO);
+              mma_bf16(tmem + dcol[t], ad, bd, idesc, !(first[t] && ks == 0));
+            }
+        }
+        mma_commit(&S.bar_mma);
+      }
+      if (!mbar_wait(&S.bar_mma, ph_mma, kWaitCycles)) to = 1;
+      ph_mma ^= 1;
+      tc_fence_after();
+      if (tid == 0 && next >= 0 && !to) {
+        const unsigned char* img = img_set + (size_t)next * IMG_BYTES;
+        mbar_arrive_expect_tx(&S.bar_tma, IMG_BYTES);
+        bulk_g2s(S.A, img, A_DIGITS, &S.bar_tma);
+        bulk_g2s(S.alpha[(kick_no + 1) & 1], img + A_DIGITS, A_SCALES, &S.bar_tma);
+        tma_pending = true;
+      }
+      // epilogue: W from the three exact accumulators, kick P -= hb W + (hb Gamma_j^2) Q with
+      // the Gamma^2 term in double-float, drift Q += ha P (double-float)
+      // acc = D_0 + 2^-8 (D_1 + 2^-8 (D_2 + 2^-8 D_3)), folded as the accumulators arrive
+      constexpr float kQ = 0.00390625f;  // 2^-8
+      float acc[CPT], dt[CPT];
+      tmem_ld16(t_lane + TM_D3 + c0, acc);
+#pragma unroll
+      for (int o = 2; o >= 0; --o) {
+        tmem_ld16(t_lane + (o == 2 ? TM_D2 : (o == 1 ? TM_D1 : TM_D0)) + c0, dt);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
+      }
+      const float hbh = p.kick_hi[kidx], hbl = p.kick_lo[kidx];
+      float cgh, cgl;  // hb * Gamma_j^2 as a float pair
+      {
+        const float pp = __fmul_rn(hbh, g2h);
+        float pe = fmaf(hbh, g2h, -pp);
+        pe = fmaf(hbh, g2l, pe);
+        pe = fmaf(hbl, g2h, pe);
+        quick_two_sum(pp, pe, cgh, cgl);
+      }
+      const float hah = last ? 0.0f : p.drift_hi[r], hal = last ? 0.0f : p.drift_lo[r];
+      const float wscale = alpha_m * (1.0f / 16384.0f);
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        if (c0 + c >= N) continue;  // padding columns stay zero (TMEM there is never written)
+        const float w = __fmul_rn(__fmul_rn(acc[c], S.gamma[c0 + c]), wscale);
+        const float t1 = __fmul_rn(hbh, w);
+        const float p2 = __fmul_rn(cgh, Qh[c]);
+        float e2 = fmaf(cgh, Qh[c], -p2);
+        e2 = fmaf(cgh, Ql[c], e2);
+        e2 = fmaf(cgl, Qh[c], e2);
+        float s1, r1, s2, r2;
+        two_sum(Ph[c], -p2, s1, r1);
+        two_sum(s1, -t1, s2, r2);
+        quick_two_sum(s2, __fadd_rn(Pl[c], __fsub_rn(__fadd_rn(r1, r2), e2)), Ph[c], Pl[c]);
+        if (!last) {
+          const float pp = __fmul_rn(hah, Ph[c]);
+          float pe = fmaf(hah, Ph[c], -pp);
+          pe = fmaf(hah, Pl[c], pe);
+          pe = fmaf(hal, Ph[c], pe);
+          float qs, qe;
+          two_sum(Qh[c], pp, qs, qe);
+          quick_two_sum(qs, __fadd_rn(Ql[c], __fadd_rn(qe, pe)), Qh[c], Ql[c]);
+        }
+      }
+      if (!last) write_b_digits(S, Qh, m, c0, qd, lane);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      abort = __syncthreads_or(to);
+      tc_fence_after();
+      if (abort) break;
+    }
+    if (abort || last) break;
+
+    // badness xi of Q (FP32 Varah bound) after the step
+    {
+      float sum = 0.0f, dg = 0.0f;
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const float o = __shfl_xor_sync(0xffffffffu, Qh[c], 1);
+        const float a = sqrtf(Qh[c] * Qh[c] + o * o);
+        if (c0 + c < N) sum += a;
+        if (c0 + c == j) dg = a;
+      }
+      if (part == 0 && j < N) {
+        S.rowsum[cq][j] = sum;
+        if (j >= c0 && j < c0 + CPT) S.diag[j] = dg;
+      }
+      __syncthreads();
+      if (warp < 2) {
+        float rs = 0.0f, mg = INFINITY;
+        if (tid < N) {
+          rs = (S.rowsum[0][tid] + S.rowsum[1][tid]) + (S.rowsum[2][tid] + S.rowsum[3][tid]);
+          mg = S.diag[tid] - (rs - S.diag[tid]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          rs = fmaxf(rs, __shfl_xor_sync(0xffffffffu, rs, o));
+          mg = fminf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+        }
+        if (lane == 0) {
+          S.redf[2 * warp] = rs;
+          S.redf[2 * warp + 1] = mg;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const float rs = fmaxf(S.redf[0], S.redf[2]);
+        const float mg = fminf(S.redf[1], S.redf[3]);
+        const float xi = (mg > 0.0f) ? rs / mg : INFINITY;
+        S.flag = !(xi <= (float)p.threshold);
+      }
+      __syncthreads();
+    }
+    if (S.flag) {
+      // RHST: T = Q^{-1} (FP32 Gauss-Jordan), Z <- Z T (double-float)
+      float2* T = reinterpret_cast<float2*>(S.B);
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (j < N && c0 + c < N) reinterpret_cast<float*>(&T[j * NC + c0 + c])[part] = Qh[c];
+      __syncthreads();
+      gj_invert(S, T, N);
+      if (S.status != kOk) {
+        abort = 1;
+        break;
+      }
+      tmem_st16(t_lane + TM_QH + c0, Qh);
+      tmem_st16(t_lane + TM_QL + c0, Ql);
+      tmem_st16(t_lane + TM_PH + c0, Ph);
+      tmem_st16(t_lane + TM_PL + c0, Pl);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      apply_t(T, t_lane, TM_QH, TM_QL, part, c0, N, Qh, Ql);
+      apply_t(T, t_lane, TM_PH, TM_PL, part, c0, N, Ph, Pl);
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      write_b_digits(S, Qh, m, c0, qd, lane);
+      fence_proxy_async_smem();
+      if (tid == 0) S.n_rhst++;
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    }
+  }
+
+  // drain: a bulk copy issued but never waited for must land before the CTA exits
+  if (tid == 0 && tma_pending) {
+    if (!mbar_wait(&S.bar_tma, ph_tma, kWaitCycles)) S.status = kTimeout;
+  }
+  if (abort && tid == 0 && S.status == kOk) S.status = kTimeout;
+  __syncthreads();
+
+  if (S.status == kOk) {
+    // ---- assembly in FP64: A0 = Gamma Q - i P, x = A0^{-1} e_1 (+1 refinement), rho = B0 x
+    const double gr = (j < N) ? S.Gr[j] : 0.0, gi = (j < N) ? S.Gi[j] : 0.0;
+    double2* LU = reinterpret_cast<double2*>(S.A);
+    // sign = -1: A0 = Gamma Q - i P ; sign = +1: B0 = Gamma Q + i P (complex entry of (j, c0+c))
+    auto entry = [&](int c, double sign) {
+      const double qv = (double)Qh[c] + (double)Ql[c];
+      const double pv = (double)Ph[c] + (double)Pl[c];
+      const double qo = __shfl_xor_sync(0xffffffffu, qv, 1);
+      const double po = __shfl_xor_sync(0xffffffffu, pv, 1);
+      const double qr = part ? qo : qv, qi = part ? qv : qo;
+      const double pr = part ? po : pv, pi = part ? pv : po;
+      return make_double2(gr * qr - gi * qi - sign * pi, gr * qi + gi * qr + sign * pr);
+    };
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const double2 a = entry(c, -1.0);
+      if (j < N && c0 + c < N)
+        reinterpret_cast<double*>(&LU[j * NC + c0 + c])[part] = part ? a.y : a.x;
+    }
+    __syncthreads();
+    dense::lu_factor(LU, NC, N, S.piv, &S.status, nullptr, nullptr);
+    if (S.status == kOk) {
+      if (warp == 0) {
+        for (int k = lane; k < N; k += 32) S.xv[k] = make_double2(k == 0 ? 1.0 : 0.0, 0.0);
+        __syncwarp();
+        dense::lu_solve_warp(LU, NC, N, S.piv, S.xv);
+      }
+      __syncthreads();
+      // pass 0: residual r = e_1 - A0 x and one correction; pass 1: rho = B0 x
+      for (int pass = 0; pass < 2; ++pass) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const double2 a = entry(c, pass == 0 ? -1.0 : 1.0);
+          if (c0 + c < N) {
+            const double2 x = S.xv[c0 + c];
+            acc += part ? (a.x * x.y + a.y * x.x) : (a.x * x.x - a.y * x.y);
+          }
+        }
+        S.psum[cq][m] = acc;
+        __syncthreads();
+        if (pass == 0) {
+          if (tid < N) {
+            const double re = (S.psum[0][2 * tid] + S.psum[1][2 * tid]) +
+                              (S.psum[2][2 * tid] + S.psum[3][2 * tid]);
+            const double im = (S.psum[0][2 * tid + 1] + S.psum[1][2 * tid + 1]) +
+                              (S.psum[2][2 * tid + 1] + S.psum[3][2 * tid + 1]);
+            S.rv[tid] = make_double2((tid == 0 ? 1.0 : 0.0) - re, -im);
+          }
+          __syncthreads();
+          if (warp == 0) {
+            dense::lu_solve_warp(LU, NC, N, S.piv, S.rv);
+            for (int k = lane; k < N; k += 32)
+              S.xv[k] = make_double2(S.xv[k].x + S.rv[k].x, S.xv[k].y + S.rv[k].y);
+          }
+          __syncthreads();
+        } else if (tid < N) {
+          const double re = (S.psum[0][2 * tid] + S.psum[1][2 * tid]) +
+                            (S.psum[2][2 * tid] + S.psum[3][2 * tid]);
+          const double im = (S.psum[0][2 * tid + 1] + S.psum[1][2 * tid + 1]) +
+                            (S.psum[2][2 * tid + 1] + S.psum[3][2 * tid + 1]);
+          p.out.rho[pair * N + tid] = make_double2(re, im);
+          const double g2 = S.gam2[tid];
+          p.out.eta[pair * N + tid] =
+              (g2 > 0.0) ? (re * re + im * im) * sin_t0 * sqrt(S.gam2[0]) / sqrt(g2) : 0.0;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (S.status != kOk) {
+    for (int k = tid; k < N; k += NT) {
+      p.out.rho[pair * N + k] = make_double2(NAN, NAN);
+      p.out.eta[pair * N + k] = NAN;
+    }
+  }
+  if (tid == 0) {
+    p.out.status[pair] = S.status;
+    p.out.n_rhst[pair] = S.n_rhst;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Fixed-point digit images of the real-ified U(tau), one CTA per node: row scales
+// alpha_i = 2^ceil(log2 max_k |A_ik|) and four BF16 digit planes of 128 x 128 in the canonical
+// K-major no-swizzle layout (8-row x 16-byte core matrices, K-blocks 128 B apart, 8-row groups
+// 2048 B apart), then the 128 row scales.
+__global__ void __launch_bounds__(256) k_umma_images(MixedImageParams p) {
+  __shared__ float s_alpha[MT];
+  __shared__ float s_inv[MT];
+  const size_t node_all = blockIdx.x;  // set * n_nodes + node
+  const double2* u = p.u + node_all * p.M;
+  const int tid = threadIdx.x;
+  const int N = p.N;
+  // row maxima: 4 threads per beam row j, each over a quarter of the columns
+  {
+    const int jr = tid >> 2, qtr = tid & 3;
+    float mx = 0.0f;
+    if (jr < N)
+      for (int k = qtr; k < N; k += 4) {
+        const double2 uv = u[p.lmap[jr * N + k]];
+        mx = fmaxf(mx, fmaxf(fabsf((float)uv.x), fabsf((float)uv.y)));
+      }
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    if (qtr == 0 && jr < 64) {
+      const float a = pow2_ceil(mx);
+      s_alpha[2 * jr] = s_alpha[2 * jr + 1] = a;
+      s_inv[2 * jr] = s_inv[2 * jr + 1] = 1.0f / a;
+    }
+  }
+  __syncthreads();
+  unsigned char* img = p.img + node_all * IMG_BYTES;
+  for (int t = tid; t < MT * KT / 8; t += blockDim.x) {
+    const int mg = t >> 7, kb = (t >> 3) & 15, mr = t & 7;
+    const int m = 8 * mg + mr;
+    const int j = m >> 1, pp = m & 1;
+    uint16_t v[NDIG][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kk = 8 * kb + e;
+      const int k = kk >> 1, q = kk & 1;
+      float x = 0.0f;
+      if (j < N && k < N) {
+        const double2 uv = u[p.lmap[j * N + k]];
+        x = (float)((pp == q) ? uv.x : (pp == 0 ? -uv.y : uv.y));
+      }
+      uint16_t b[NDIG];
+      digits4(x, s_inv[m], b);
+#pragma unroll
+      for (int t = 0; t < NDIG; ++t) v[t][e] = b[t];
+    }
+    unsigned char* dst = img + (size_t)mg * A_SBO + kb * A_LBO + mr * 16;
+#pragma unroll
+    for (int term = 0; term < NDIG; ++term) {
+      uint4 w;
+      w.x = v[term][0] | ((uint32_t)v[term][1] << 16);
+      w.y = v[term][2] | ((uint32_t)v[term][3] << 16);
+      w.z = v[term][4] | ((uint32_t)v[term][5] << 16);
+      w.w = v[term][6] | ((uint32_t)v[term][7] << 16);
+      *reinterpret_cast<uint4*>(dst + term * A_TERM) = w;
+    }
+  }
+  if (tid < MT) reinterpret_cast<float*>(img + A_DIGITS)[tid] = s_alpha[tid];
+}
+
+}  // namespace
+
+bool mixed_available() { return true; }
+size_t mixed_image_bytes_per_node() { return IMG_BYTES; }
+
+cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* n_launched) {
+  const unsigned blocks = (unsigned)((size_t)p.n_sets * p.n_nodes);
+  k_umma_images<<<blocks, 256, 0, st>>>(p);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_mixed(const MixedParams& p, cudaStream_t st, int* n_launched) {
+  const size_t smem = sizeof(Smem) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_integrate_mixed,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(p.ang.n_angles, p.n_sets);
+  k_integrate_mixed<<<grid, NT, smem, st>>>(p);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace trh

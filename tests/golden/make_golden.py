@@ -1,0 +1,32 @@
+"""Write the oracle's expected outputs for the full-size parity tests.
+
+Calls only ``oracle/`` (Algorithm 1, sp4, threshold 1000, FP64) on the seeded workloads of
+``paper_2306_00271_gb300.workloads``; nothing here comes from the CUDA path.
+
+    python tests/golden/make_golden.py            # writes tests/golden/trhepd_n61_sp4.npz
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle.curve import rocking_curve_parallel  # noqa: E402
+from paper_2306_00271_gb300 import workloads as W  # noqa: E402
+
+
+def main():
+    wl = W.trhepd_n61()
+    t = time.time()
+    rho, eta, flux, n_rhst = rocking_curve_parallel(wl, "sp4", 1000.0)
+    out = os.path.join(HERE, "trhepd_n61_sp4.npz")
+    np.savez_compressed(out, theta0=wl.theta0, theta1=wl.theta1, rho=rho, eta=eta,
+                        n_rhst=n_rhst, n_steps=wl.n_steps, z_e=wl.z_e)
+    print(f"wrote {out} in {time.time() - t:.1f}s; rhst per angle {n_rhst.min()}..{n_rhst.max()}")
+
+
+if __name__ == "__main__":
+    main()
