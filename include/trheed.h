@@ -160,6 +160,32 @@ const char* trh_last_error(void);
 /* Free the context and its device memory. NULL is accepted. Synchronises the device. */
 void trh_destroy(trh_ctx* ctx);
 
+/* Rocking curve of one structure on the binary64 path without any device allocation.
+ *
+ * The paper has no counterpart: this entry exists for callers that cannot call cudaMalloc when
+ * they need a curve, e.g. code running inside a CUDA stream capture (allocations there are not
+ * capturable), code with a fixed device-memory budget, or host applications that own all device
+ * memory. The caller passes device buffers for the angles and the outputs; the potential table,
+ * scattering factors, geometry tables and status words live in one fixed-size device array of
+ * 16 MiB inside this library, which every GPU that loads the library keeps until process exit.
+ *   p              : problem as for trh_create (host memory); precision must be TRH_FP64,
+ *                    integrator TRH_SP4 or TRH_SP6, N <= 64, at most 256 atoms.
+ *   theta0, theta1 : [n_angles] degrees, DEVICE memory.
+ *   rho_out        : [n_angles][N] complex128, DEVICE memory.
+ *   eta_out        : [n_angles][N] float64, DEVICE memory.
+ *   stream         : cudaStream_t (NULL = legacy default stream); the work is enqueued on it and
+ *                    the call returns without synchronising.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture on the device. No call allocates or frees device
+ * memory. All calls share the array and it keeps the last call's contents (nothing in it needs
+ * to start at zero), so calls whose work overlaps on the GPU race: serialise them on one stream.
+ * Results equal those of trh_rocking_curve with TRH_FP64 for the same problem and angles; a
+ * (set, angle) whose RHST or final solve hits a singular pivot yields NaN outputs.
+ * Errors: TRH_EINVAL (bad arguments, or a problem whose tables exceed the 16 MiB array: the
+ * message from trh_last_error() states the bytes needed), TRH_ECUDA. */
+int trh_rocking_curve_noalloc(const trh_problem* p, int n_angles, const double* theta0,
+                              const double* theta1, void* rho_out, double* eta_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

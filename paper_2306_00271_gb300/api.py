@@ -83,6 +83,8 @@ def load():
     lib.trh_last_error.restype = C.c_char_p
     lib.trh_destroy.argtypes = [vp]
     lib.trh_destroy.restype = None
+    lib.trh_rocking_curve_noalloc.argtypes = [C.POINTER(TrhProblem), C.c_int, vp, vp, vp, vp, vp]
+    lib.trh_rocking_curve_noalloc.restype = C.c_int
     for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
@@ -101,6 +103,53 @@ def _ptr(a) -> C.c_void_p:
     if hasattr(a, "data_ptr"):
         return C.c_void_p(a.data_ptr())
     return C.c_void_p(a.ctypes.data)
+
+
+def make_problem(wl, precision: str = "fp64", integrator: str = "sp4",
+                 threshold: float = 1000.0):
+    """(TrhProblem, arrays it points into) for a workload; keep the arrays alive with it."""
+    keep = dict(
+        beams=np.ascontiguousarray(wl.beams, dtype=np.int32),
+        atoms=np.ascontiguousarray(wl.atoms, dtype=np.float64),
+        dw=np.ascontiguousarray(wl.dw, dtype=np.float64),
+        species=np.ascontiguousarray(wl.species, dtype=np.int32),
+        sf=np.ascontiguousarray(wl.sf, dtype=np.float64))
+    p = TrhProblem()
+    p.particle = int(wl.particle)
+    p.energy_ev = float(wl.energy_ev)
+    p.absorption = float(wl.absorption)
+    p.a1[0], p.a1[1] = float(wl.a1[0]), float(wl.a1[1])
+    p.a2[0], p.a2[1] = float(wl.a2[0]), float(wl.a2[1])
+    p.n_beams = int(keep["beams"].shape[0])
+    p.beams = keep["beams"].ctypes.data_as(C.POINTER(C.c_int))
+    p.n_atoms = int(keep["atoms"].shape[0])
+    p.atoms = keep["atoms"].ctypes.data_as(C.POINTER(C.c_double))
+    p.dw = keep["dw"].ctypes.data_as(C.POINTER(C.c_double))
+    p.species = keep["species"].ctypes.data_as(C.POINTER(C.c_int))
+    p.n_species = int(keep["sf"].shape[0])
+    p.sf = keep["sf"].ctypes.data_as(C.POINTER(C.c_double))
+    p.z_e = float(wl.z_e)
+    p.n_steps = int(wl.n_steps)
+    p.integrator = INTEGRATORS[integrator]
+    p.rhst_threshold = float(threshold)
+    p.precision = PRECISIONS[precision]
+    return p, keep
+
+
+def rocking_curve_noalloc(wl, theta0, theta1, rho, eta, integrator: str = "sp4",
+                          threshold: float = 1000.0, stream=None):
+    """trh_rocking_curve_noalloc: binary64 curve of one structure using only the library's fixed
+    device array (no device allocation). theta0/theta1 (A,) float64, rho (A, N) complex128 and
+    eta (A, N) float64 must be CUDA tensors; the work is enqueued on `stream` (default: torch's
+    current stream) and not synchronised."""
+    lib = load()
+    p, keep = make_problem(wl, "fp64", integrator, threshold)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.trh_rocking_curve_noalloc(C.byref(p), int(theta0.numel()), _ptr(theta0),
+                                         _ptr(theta1), _ptr(rho), _ptr(eta), C.c_void_p(stream)))
+    return rho, eta
 
 
 class Engine:

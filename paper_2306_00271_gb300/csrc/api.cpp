@@ -105,6 +105,10 @@ bool is_device_ptr(const void* ptr) {
 
 }  // namespace
 
+namespace trh {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace trh
+
 struct trh_ctx {
   // problem (host copies)
   int particle = 0, N = 0, M = 0, n_atoms = 0, n_species = 0, L = 0, integrator = 0, precision = 0;

@@ -94,6 +94,8 @@ cudaError_t launch_potential(const PotentialParams& p, cudaStream_t st, int* n_l
 cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* n_launched);
 cudaError_t launch_integrate_mixed(const MixedParams& p, cudaStream_t st, int* n_launched);
 size_t mixed_image_bytes_per_node();
+// Records the message trh_last_error() returns on this thread.
+void set_last_error(const char* msg);
 cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int* n_launched);
 size_t integrate_fp64_smem_bytes();
 bool mixed_available();
