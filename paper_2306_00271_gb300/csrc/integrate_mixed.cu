@@ -81,7 +81,7 @@ struct __align__(128) Smem {
   float rowsum[4][NC], diag[NC];
   float redf[4];
   double gam2[NC], Gr[NC], Gi[NC];
-  float2 frow[NC], fcol[NC];
+  float2 frow[NC], fcol[NC], oldk[NC];
   double2 xv[NC], rv[NC];
   double psum[4][MT];
 };
@@ -169,8 +169,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 
 // In-place inverse of the n x n complex FP32 matrix T (row stride NC) by Gauss-Jordan elimination
 // with row pivoting; the row interchanges are undone on the columns in reverse order at the end.
+// Thread t owns column t % 64 and rows t / 64, t / 64 + 8, ... (no index division in the update).
 __device__ void gj_invert(Smem& S, float2* T, int n) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int col = tid & 63, rg = tid >> 6;  // 8 row groups
   for (int k = 0; k < n; ++k) {
     if (warp == 0) {
       float best = -1.0f;
@@ -200,37 +202,33 @@ __device__ void gj_invert(Smem& S, float2* T, int n) {
     __syncthreads();
     if (S.status != kOk) return;
     const int pr = S.piv[k];
-    if (pr != k) {
-      for (int c = tid; c < n; c += NT) {
-        const float2 t = T[k * NC + c];
-        T[k * NC + c] = T[pr * NC + c];
-        T[pr * NC + c] = t;
-      }
-      __syncthreads();
-    }
-    {
-      const float2 a = T[k * NC + k];
+    // pivot row (after the interchange) scaled by 1/pivot, and column k (before the update)
+    if (tid < n) {
+      const float2 a = T[pr * NC + k];
       const float d = a.x * a.x + a.y * a.y;
       const float2 inv = make_float2(a.x / d, -a.y / d);
-      for (int c = tid; c < n; c += NT) {
-        const float2 t = T[k * NC + c];
-        S.frow[c] = (c == k) ? inv
-                             : make_float2(t.x * inv.x - t.y * inv.y, t.x * inv.y + t.y * inv.x);
-        S.fcol[c] = (c == k) ? make_float2(0.f, 0.f) : T[c * NC + k];
-      }
+      const float2 t = T[pr * NC + tid];
+      S.frow[tid] = (tid == k) ? inv
+                               : make_float2(t.x * inv.x - t.y * inv.y, t.x * inv.y + t.y * inv.x);
+      // row r's multiplier: rows k and pr trade places
+      const int src = (tid == k) ? pr : (tid == pr ? k : tid);
+      S.fcol[tid] = (tid == k) ? make_float2(0.f, 0.f) : T[src * NC + k];
+      S.oldk[tid] = T[k * NC + tid];  // old row k, overwritten by the pivot row below
     }
     __syncthreads();
-    for (int e = tid; e < n * n; e += NT) {
-      const int r = e / n, c = e - r * n;
-      const float2 fr = S.frow[c];
-      if (r == k) {
-        T[r * NC + c] = fr;
-      } else {
-        const float2 fc = S.fcol[r];
-        float2 t = (c == k) ? make_float2(0.f, 0.f) : T[r * NC + c];
-        t.x -= fc.x * fr.x - fc.y * fr.y;
-        t.y -= fc.x * fr.y + fc.y * fr.x;
-        T[r * NC + c] = t;
+    if (col < n) {
+      const float2 fr = S.frow[col];
+      // the interchange: old row k moves to pr, old row pr becomes the new pivot row k
+      for (int r = rg; r < n; r += 8) {
+        if (r == k) {
+          T[k * NC + col] = fr;
+        } else {
+          const float2 fc = S.fcol[r];
+          float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? S.oldk[col] : T[r * NC + col]);
+          t.x -= fc.x * fr.x - fc.y * fr.y;
+          t.y -= fc.x * fr.y + fc.y * fr.x;
+          T[r * NC + col] = t;
+        }
       }
     }
     __syncthreads();
@@ -302,6 +300,9 @@ __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32
   }
 }
 
+// KS = number of 16-wide K slices (ceil(2N / 16)), a template parameter so the MMA issue loop of
+// the single issuing thread is fully unrolled with constant descriptor offsets.
+template <int KS>
 __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
@@ -402,18 +403,26 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
       if (tid == 0) {
         if (!to) {
           tc_fence_after();
-          // orders 0..3 of the digit products, each in its own accumulator
-          const int ta[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-          const int tb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-          const uint32_t dcol[10] = {TM_D0, TM_D1, TM_D1, TM_D2, TM_D2,
-                                     TM_D2, TM_D3, TM_D3, TM_D3, TM_D3};
-          const bool first[10] = {true, true, false, true, false, false, true, false, false, false};
-          for (int t = 0; t < 10; ++t)
-            for (int ks = 0; ks < p.k_slices; ++ks) {
-              const uint64_t ad = smem_desc(a_base + ta[t] * A_TERM + ks * 2 * A_LBO, A_LBO, A_SBO);
-              const uint64_t bd = smem_desc(b_base + tb[t] * B_TERM + ks * 2 * B_LBO, B_LBO, B_SBO);
-              mma_bf16(tmem + dcol[t], ad, bd, idesc, !(first[t] && ks == 0));
-            }
+          // orders 0..3 of the digit products, each in its own accumulator. Descriptors are built
+          // once; the 14-bit start-address field (bits 0-13, in 16-byte units) is advanced
+          // directly (shared addresses stay below 256 KB, so it never carries).
+          constexpr int kTa[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+          constexpr int kTb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+          constexpr int kOrd[10] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+          constexpr bool kFirst[10] = {true, true, false, true, false, false,
+                                       true, false, false, false};
+          const uint64_t a0 = smem_desc(a_base, A_LBO, A_SBO);
+          const uint64_t b0 = smem_desc(b_base, B_LBO, B_SBO);
+#pragma unroll
+          for (int t = 0; t < 10; ++t) {
+            const uint64_t at = a0 + (uint64_t)((kTa[t] * A_TERM) >> 4);
+            const uint64_t bt = b0 + (uint64_t)((kTb[t] * B_TERM) >> 4);
+            const uint32_t dt = tmem + TM_D0 + 64u * kOrd[t];
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks)
+              mma_bf16(dt, at + (uint64_t)(ks * ((2 * A_LBO) >> 4)),
+                       bt + (uint64_t)(ks * ((2 * B_LBO) >> 4)), idesc, !(kFirst[t] && ks == 0));
+          }
         }
         mma_commit(&S.bar_mma);
       }
@@ -725,15 +734,32 @@ cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_integrate_mixed(const MixedParams& p, cudaStream_t st, int* n_launched) {
+template <int KS>
+static cudaError_t launch_ks(const MixedParams& p, cudaStream_t st) {
   const size_t smem = sizeof(Smem) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_integrate_mixed,
+  cudaError_t e = cudaFuncSetAttribute(k_integrate_mixed<KS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(p.ang.n_angles, p.n_sets);
-  k_integrate_mixed<<<grid, NT, smem, st>>>(p);
-  if (n_launched) *n_launched += 1;
+  k_integrate_mixed<KS><<<grid, NT, smem, st>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_mixed(const MixedParams& p, cudaStream_t st, int* n_launched) {
+  cudaError_t e;
+  switch (p.k_slices) {
+    case 1: e = launch_ks<1>(p, st); break;
+    case 2: e = launch_ks<2>(p, st); break;
+    case 3: e = launch_ks<3>(p, st); break;
+    case 4: e = launch_ks<4>(p, st); break;
+    case 5: e = launch_ks<5>(p, st); break;
+    case 6: e = launch_ks<6>(p, st); break;
+    case 7: e = launch_ks<7>(p, st); break;
+    case 8: e = launch_ks<8>(p, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (n_launched) *n_launched += 1;
+  return e;
 }
 
 }  // namespace trh
