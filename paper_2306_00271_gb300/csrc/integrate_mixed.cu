@@ -72,8 +72,9 @@ struct __align__(128) Smem {
   unsigned char A[A_DIGITS];    // U(tau) digit planes; FP64 LU workspace at the end
   unsigned char B[NDIG * B_TERM];  // digit planes of Q; FP32 T = Q^{-1} during the RHST
   float alpha[2][MT];           // row scales of A, double-buffered with the image
-  float gamma[NC];              // column scales of the current B
-  uint32_t colmax[4][NC];       // per-quadrant column maxima (float bits of |Q|)
+  float gamma[2][NC];           // column scales of B, by kick parity
+  uint4 colmax[2][NC];          // per-quadrant column maxima of Q (float bits of |Q|), by parity
+  int ovf;                      // a digit outgrew its scale (set before the end-of-kick barrier)
   uint64_t bar_tma, bar_mma;
   uint32_t tmem_base;
   int status, flag, n_rhst;
@@ -110,6 +111,10 @@ __device__ __forceinline__ float pow2_ceil(float x) {
   if (b & 0x007FFFFFu) e += 0x00800000u;
   return __uint_as_float(e);
 }
+// 1 / g for a normal power of two g, from its exponent bits.
+__device__ __forceinline__ float pow2_inv(float g) {
+  return __uint_as_float((254u << 23) - (__float_as_uint(g) & 0x7F800000u));
+}
 
 // Fixed-point digits of v = x / scale (|v| <= 1): BF16 bit patterns of d0..d3. The remainders
 // are exact in FP32 (power-of-two scalings and differences of nearby values).
@@ -124,34 +129,45 @@ __device__ __forceinline__ void digits4(float x, float inv_scale, uint16_t (&b)[
   }
 }
 
-// Column maxima of |Qh| over the 128 real-ified rows -> power-of-two scales, then the digit
-// planes of B. One block barrier inside; all threads call it.
-__device__ __forceinline__ void write_b_digits(Smem& S, const float (&qh)[CPT], int m, int c0,
-                                               int qd, int lane) {
+// Column maxima of this warp's 32 rows of |Qh|, one lane per column, into colmax[par][c][qd].
+__device__ __forceinline__ void column_maxima(Smem& S, const float (&qh)[CPT], int c0, int qd,
+                                              int lane, int par) {
 #pragma unroll
   for (int i = 0; i < CPT; ++i) {
     const uint32_t mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(qh[i])));
-    if (lane == i) S.colmax[qd][c0 + i] = mx;
+    if (lane == i) reinterpret_cast<uint32_t*>(&S.colmax[par][c0 + i])[qd] = mx;
   }
-  __syncthreads();
-  float inv[CPT];
-#pragma unroll
-  for (int i = 0; i < CPT; ++i) {
-    const uint32_t a = max(max(S.colmax[0][c0 + i], S.colmax[1][c0 + i]),
-                           max(S.colmax[2][c0 + i], S.colmax[3][c0 + i]));
-    const float g = pow2_ceil(__uint_as_float(a));
-    inv[i] = 1.0f / g;  // exact: g is a power of two
-    if (qd == 0 && lane == i) S.gamma[c0 + i] = g;
-  }
+}
+
+// Digits of B from qh with the column scales taken from colmax[spar]; the scales are published
+// in gamma[gpar] for the epilogue that reads the product. Returns true if some |x| / scale > 2
+// (the fixed-point format tolerates |d0| <= 256: every accumulator stays below 2^24).
+__device__ __forceinline__ bool digits_b(Smem& S, const float (&qh)[CPT], int m, int c0, int qd,
+                                         int lane, int spar, int gpar) {
+  bool ovf = false;
 #pragma unroll
   for (int i = 0; i < CPT; ++i) {
     const int c = c0 + i;
+    const uint4 q4 = S.colmax[spar][c];
+    const float g = pow2_ceil(__uint_as_float(max(max(q4.x, q4.y), max(q4.z, q4.w))));
+    if (qd == 0 && lane == i) S.gamma[gpar][c] = g;
+    const float inv = pow2_inv(g);
+    ovf |= fabsf(qh[i]) * inv > 2.0f;
     uint16_t b[NDIG];
-    digits4(qh[i], inv[i], b);
+    digits4(qh[i], inv, b);
     const int off = (c >> 3) * B_SBO + (m >> 3) * B_LBO + (c & 7) * 16 + (m & 7) * 2;
 #pragma unroll
     for (int t = 0; t < NDIG; ++t) *reinterpret_cast<uint16_t*>(S.B + t * B_TERM + off) = b[t];
   }
+  return ovf;
+}
+
+// Exact variant: maxima of qh itself (one block barrier), digits, scales into gamma[par].
+__device__ __forceinline__ void write_b_exact(Smem& S, const float (&qh)[CPT], int m, int c0,
+                                              int qd, int lane, int par) {
+  column_maxima(S, qh, c0, qd, lane, par);
+  __syncthreads();
+  digits_b(S, qh, m, c0, qd, lane, par, par);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
@@ -365,7 +381,8 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
       Pl[i] = dg ? pvl : 0.0f;
     }
   }
-  write_b_digits(S, Qh, m, c0, qd, lane);
+  if (tid == 0) S.ovf = 0;
+  write_b_exact(S, Qh, m, c0, qd, lane, 0);
   fence_proxy_async_smem();
   bool tma_pending = false;
   if (tid == 0 && S.status == kOk) {
@@ -462,7 +479,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         if (c0 + c >= N) continue;  // padding columns stay zero (TMEM there is never written)
-        const float w = __fmul_rn(__fmul_rn(acc[c], S.gamma[c0 + c]), wscale);
+        const float w = __fmul_rn(__fmul_rn(acc[c], S.gamma[kick_no & 1][c0 + c]), wscale);
         const float t1 = __fmul_rn(hbh, w);
         const float p2 = __fmul_rn(cgh, Qh[c]);
         float e2 = fmaf(cgh, Qh[c], -p2);
@@ -482,12 +499,25 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
           quick_two_sum(qs, __fadd_rn(Ql[c], __fadd_rn(qe, pe)), Qh[c], Ql[c]);
         }
       }
-      if (!last) write_b_digits(S, Qh, m, c0, qd, lane);
+      // B for the next kick: digits of the new Q with the scales of this kick's Q (its column
+      // maxima are complete since the previous barrier); the new maxima go to the other parity
+      const int pc = kick_no & 1, pn = pc ^ 1;
+      if (!last) {
+        column_maxima(S, Qh, c0, qd, lane, pn);
+        if (digits_b(S, Qh, m, c0, qd, lane, pc, pn)) S.ovf = 1;
+      }
       fence_proxy_async_smem();
       tc_fence_before();
       abort = __syncthreads_or(to);
       tc_fence_after();
       if (abort) break;
+      if (S.ovf) {  // a column grew more than twofold: redo with the exact maxima of the new Q
+        digits_b(S, Qh, m, c0, qd, lane, pn, pn);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) S.ovf = 0;
+        __syncthreads();
+      }
     }
     if (abort || last) break;
 
@@ -556,7 +586,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      write_b_digits(S, Qh, m, c0, qd, lane);
+      write_b_exact(S, Qh, m, c0, qd, lane, kick_no & 1);
       fence_proxy_async_smem();
       if (tid == 0) S.n_rhst++;
       tc_fence_before();
