@@ -120,6 +120,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2306_00271_gb300 import api
     wl = W.trhepd_n61()
+    if args.slices:
+        wl = wl.with_steps(args.slices)
     A = len(wl.theta0)
     dev = torch.device("cuda", local)
     engines = {}
@@ -199,6 +201,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="auto", choices=["auto", "mixed", "fp64"])
     ap.add_argument("--cpu-angles", type=int, default=0)
+    ap.add_argument("--slices", type=int, default=0,
+                    help="override the slice count (small cases for profiling; not a bench line)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     args = ap.parse_args()
     ws, rank, _ = _dist()
     wl = W.trhepd_n61()
@@ -233,6 +238,9 @@ def main():
     wl, res, ws, rank = run_ours(args)
     if rank != 0:
         return
+    if args.slices:
+        cfg["n_steps"] = wl.n_steps
+        cfg["workload"] = cfg["workload"].replace("L=2000", f"L={wl.n_steps}") + " (profiling case)"
     head = res[paths[0]]
     peaks = _peaks() or {}
     N, L, A = 61, wl.n_steps, len(wl.theta0)
@@ -267,7 +275,7 @@ def main():
     if "mixed" in res and "fp64" in res:
         from oracle.curve import curve_error
         out["mixed_vs_fp64_curve_error"] = curve_error(res["mixed"]["eta"], res["fp64"]["eta"])
-    if ws == 1:
+    if ws == 1 and not args.no_cpu:
         n = args.cpu_angles or min(60, max(8, len(os.sched_getaffinity(0))))
         try:
             out["cpu_baseline"] = cpu_baseline(wl, n)
