@@ -193,6 +193,40 @@ def run_ours(args):
     return wl, results, ws, rank
 
 
+def run_gradient(local: int, warmup: int = 1):
+    """One R-factor gradient at the differentiation workload (N = 61, 2000 slices, 60 angles,
+    12 free z + 6 Debye-Waller classes, checkpoints every 64 steps), FP64 reverse sweep. The
+    target curve is this library's own FP64 curve at the hidden true structure."""
+    import torch
+    from paper_2306_00271_gb300 import api
+    fp = W.rfactor_fit()
+    wl = fp.workload
+    eng = api.Engine(wl, "fp64", "sp4")
+    truth = W.fit_structure(fp, fp.z_true, fp.b_true)
+    eng.set_structures(truth.atoms[None], truth.dw[None])
+    _, eta_t = eng.rocking_curve(wl.theta0, wl.theta1)
+    target = eta_t[0, :, 0].contiguous()
+    eng.set_structures(wl.atoms[None], wl.dw[None])
+    eng.set_fit(fp.free_atoms, fp.dw_class, ckpt_every=64)
+    for _ in range(warmup):
+        eng.rfactor_grad(wl.theta0, wl.theta1, target)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    R, gz, gb = eng.rfactor_grad(wl.theta0, wl.theta1, target)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = eng.stats()
+    eng.close()
+    return {"metric": "R-factor gradients/s (N=61, L=2000, 60 angles, 18 parameters, FP64 "
+                      "reverse sweep, checkpoints every 64 steps)",
+            "value": 1000.0 / ms, "unit": "gradients/s", "ms_per_gradient": ms,
+            "ms_forward": st["ms_integrate"], "ms_reverse": st["ms_gradient"],
+            "kernels_launched": st["kernels_launched"], "R": float(R[0])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,6 +238,7 @@ def main():
     ap.add_argument("--slices", type=int, default=0,
                     help="override the slice count (small cases for profiling; not a bench line)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     args = ap.parse_args()
     ws, rank, _ = _dist()
     wl = W.trhepd_n61()
@@ -275,6 +310,8 @@ def main():
     if "mixed" in res and "fp64" in res:
         from oracle.curve import curve_error
         out["mixed_vs_fp64_curve_error"] = curve_error(res["mixed"]["eta"], res["fp64"]["eta"])
+    if not args.no_grad and not args.slices:
+        out["gradient"] = run_gradient(int(os.environ.get("LOCAL_RANK", "0")))
     if ws == 1 and not args.no_cpu:
         n = args.cpu_angles or min(60, max(8, len(os.sched_getaffinity(0))))
         try:

@@ -109,6 +109,8 @@ typedef struct trh_stats {
   double ms_potential;    /* device time of the potential-table kernels of the last call (CUDA
                              events on the call's stream; 0 if the tables were current)          */
   double ms_integrate;    /* device time of the integration kernel of the last call              */
+  double ms_gradient;     /* device time of the reverse sweep of the last trh_curve_jacobian /
+                             trh_rfactor_grad call (0 after trh_rocking_curve)                   */
 } trh_stats;
 
 /* Create a context for one beam set and method. Validates and copies `p` (the caller may free
@@ -146,6 +148,52 @@ int trh_set_structure(trh_ctx* ctx, int n_sets, const double* atoms, const doubl
  * TRH_ECUDA. */
 int trh_rocking_curve(trh_ctx* ctx, int n_angles, const double* theta0, const double* theta1,
                       void* rho_out, double* eta_out, void* stream);
+
+/* ---- reverse analysis ---------------------------------------------------------------------
+ * The paper's motivation (Section 1) is the reverse analysis of measured curves: a structure
+ * x* = argmin_x |d - F(x)|^2 over structural parameters x. The calls below give the gradient of
+ * that objective with respect to atomic z coordinates and Debye-Waller factors, by the adjoint
+ * (reverse sweep) of Algorithm 1 on the binary64 path, so that gradient-based searches can use
+ * it. The objective (the paper prints none) is the R-factor of the specular curve:
+ *   eta~(theta) = eta_1(theta) / sum_theta' eta_1(theta'),   R = sum_theta (eta~ - t~)^2,
+ * with t~ the target curve normalised the same way. The RHST matrices are constants of the
+ * reverse map (rho is invariant under Z -> Z T, Section 3.2). Memory is bounded by
+ * checkpoints: the forward pass stores [Q; P] every `ckpt_every` steps and the reverse sweep
+ * recomputes one segment at a time. Device scratch per (set, angle) pair, in bytes:
+ *   16 N^2 (2 (L / C + 1) + 2 (s C + 1) + 2 C + 2) + 4 C,   C = ckpt_every, s = kicks per step,
+ * about 53 MB at N = 61, L = 2000, C = 64 (sp4).
+ * Both calls always integrate on the binary64 path (the kernels of TRH_FP64), whatever the
+ * context's precision. */
+
+/* Declare the fit parameters: the z coordinates of atoms free_atoms[0..n_free-1] (distinct
+ * indices into the context's atoms) and n_classes Debye-Waller classes, dw_class[a] in
+ * [0, n_classes) for an atom whose B is the class's parameter, -1 for a fixed B (dw_class is
+ * [n_atoms], host; may be NULL when n_classes = 0). Every class needs at least one atom; at most
+ * 64 atoms may carry a parameter. ckpt_every <= 0 selects 64 steps per checkpoint.
+ * Errors: TRH_EINVAL, TRH_EUNSUPPORTED (more than 64 atoms), TRH_ENOMEM, TRH_ECUDA. */
+int trh_set_fit(trh_ctx* ctx, int n_free, const int* free_atoms, int n_classes,
+                const int* dw_class, int ckpt_every);
+
+/* Jacobian of the specular intensity eta_1 with respect to the fit parameters, for every
+ * parameter set and angle.
+ *   theta0, theta1 : [n_angles] degrees; host or device.
+ *   eta_out        : [n_sets][n_angles][N] float64 intensities; host or device; may be NULL.
+ *   jac_out        : [n_sets][n_angles][n_free + n_classes] float64: d eta_1 / d z of each free
+ *                    atom (1/A), then d eta_1 / d B of each class (1/A^2); host or device.
+ *   stream         : cudaStream_t (NULL = legacy default stream); synchronised before return.
+ * Errors: as trh_rocking_curve, and TRH_EINVAL before trh_set_fit. */
+int trh_curve_jacobian(trh_ctx* ctx, int n_angles, const double* theta0, const double* theta1,
+                       double* eta_out, double* jac_out, void* stream);
+
+/* R-factor of each parameter set's specular curve against `target` ([n_angles] float64, >= 0,
+ * not all zero; host or device; shared by all sets) and its gradient.
+ *   R_out  : [n_sets]; host or device; may be NULL.
+ *   dR_dz  : [n_sets][n_free] dR/dz of the free atoms (1/A); host or device.
+ *   dR_dB  : [n_sets][n_classes] dR/dB of the classes (1/A^2); host or device.
+ * Errors: as trh_curve_jacobian, and TRH_EINVAL for a negative or all-zero host target. */
+int trh_rfactor_grad(trh_ctx* ctx, int n_angles, const double* theta0, const double* theta1,
+                     const double* target, double* R_out, double* dR_dz, double* dR_dB,
+                     void* stream);
 
 /* Counters of the last call (see trh_stats). Errors: TRH_EINVAL (NULL arguments). */
 int trh_query(const trh_ctx* ctx, trh_stats* out);

@@ -42,6 +42,7 @@ class TrhStats(C.Structure):
         ("first_bad_set", C.c_int), ("first_bad_angle", C.c_int), ("first_bad_status", C.c_int),
         ("kernels_launched", C.c_int), ("ms_last", C.c_double),
         ("ms_potential", C.c_double), ("ms_integrate", C.c_double),
+        ("ms_gradient", C.c_double),
     ]
 
     def as_dict(self):
@@ -85,7 +86,11 @@ def load():
     lib.trh_destroy.restype = None
     lib.trh_rocking_curve_noalloc.argtypes = [C.POINTER(TrhProblem), C.c_int, vp, vp, vp, vp, vp]
     lib.trh_rocking_curve_noalloc.restype = C.c_int
-    for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query"):
+    lib.trh_set_fit.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.c_int]
+    lib.trh_curve_jacobian.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+    lib.trh_rfactor_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+    for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query", "trh_set_fit",
+              "trh_curve_jacobian", "trh_rfactor_grad"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -240,6 +245,56 @@ class Engine:
                                           C.c_void_p(0 if stream is None else stream)))
         return rho, eta
 
+    def set_fit(self, free_atoms, dw_class=None, ckpt_every: int = 64):
+        """Fit parameters for curve_jacobian / rfactor_grad: z of the atoms ``free_atoms`` and
+        one B per Debye-Waller class (``dw_class[a]`` = class of atom a, -1 = fixed B)."""
+        fa = np.ascontiguousarray(free_atoms, dtype=np.int32).reshape(-1)
+        if dw_class is None:
+            cls, n_classes = None, 0
+        else:
+            cls = np.ascontiguousarray(dw_class, dtype=np.int32).reshape(-1)
+            n_classes = int(cls.max()) + 1 if cls.size and cls.max() >= 0 else 0
+        self._fit = (fa, cls)
+        _check(self.lib.trh_set_fit(self.ctx, int(fa.size), _ptr(fa), n_classes, _ptr(cls),
+                                    int(ckpt_every)))
+        self.n_free, self.n_classes = int(fa.size), n_classes
+
+    def _angles(self, theta0, theta1, dev):
+        import torch
+        t0 = torch.as_tensor(theta0, dtype=torch.float64).to(dev).contiguous()
+        t1 = (torch.full_like(t0, float(self.wl.theta1[0])) if theta1 is None
+              else torch.as_tensor(theta1, dtype=torch.float64).to(dev).contiguous())
+        return t0, t1
+
+    def curve_jacobian(self, theta0, theta1=None, stream=None):
+        """(eta (n_sets, A, N), jac (n_sets, A, n_free + n_classes)) as CUDA tensors:
+        d eta_1 / d z of the free atoms, then d eta_1 / d B of the classes (reverse sweep)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t0, t1 = self._angles(theta0, theta1, dev)
+        A = t0.numel()
+        eta = torch.empty((self.n_sets, A, self.N), dtype=torch.float64, device=dev)
+        jac = torch.empty((self.n_sets, A, self.n_free + self.n_classes), dtype=torch.float64,
+                          device=dev)
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.trh_curve_jacobian(self.ctx, A, _ptr(t0), _ptr(t1), _ptr(eta), _ptr(jac),
+                                           C.c_void_p(st)))
+        return eta, jac
+
+    def rfactor_grad(self, theta0, theta1, target, stream=None):
+        """(R (n_sets,), dR/dz (n_sets, n_free), dR/dB (n_sets, n_classes)) as CUDA tensors."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t0, t1 = self._angles(theta0, theta1, dev)
+        tg = torch.as_tensor(target, dtype=torch.float64).to(dev).contiguous()
+        R = torch.empty(self.n_sets, dtype=torch.float64, device=dev)
+        gz = torch.empty((self.n_sets, self.n_free), dtype=torch.float64, device=dev)
+        gb = torch.empty((self.n_sets, self.n_classes), dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.trh_rfactor_grad(self.ctx, t0.numel(), _ptr(t0), _ptr(t1), _ptr(tg),
+                                         _ptr(R), _ptr(gz), _ptr(gb), C.c_void_p(st)))
+        return R, gz, gb
+
     def stats(self) -> dict:
         s = TrhStats()
         _check(self.lib.trh_query(self.ctx, C.byref(s)))
@@ -255,3 +310,60 @@ class Engine:
             self.close()
         except Exception:
             pass
+
+
+def _rfactor_function():
+    import torch
+
+    class RFactorFunction(torch.autograd.Function):
+        """R(z, B) of a fit with its gradient from the library's reverse sweep."""
+
+        @staticmethod
+        def forward(ctx, z, b, fit):
+            R, gz, gb = fit._evaluate(z, b)
+            ctx.save_for_backward(gz, gb)
+            return R
+
+        @staticmethod
+        def backward(ctx, gR):
+            gz, gb = ctx.saved_tensors
+            return gR[:, None] * gz, gR[:, None] * gb, None
+
+    return RFactorFunction
+
+
+class RFactor:
+    """The reverse-analysis objective (Section 1: argmin over structures of the misfit between
+    measured and computed curves) as a differentiable torch function.
+
+    ``fit(z, b)`` takes z (n_sets, n_free) coordinates of the free atoms and b (n_sets,
+    n_classes) Debye-Waller factors of the classes (CUDA float64 tensors), writes them into the
+    structure, and returns R (n_sets,) whose backward pass uses the adjoint gradients computed
+    in the same library call (no extra forward run)."""
+
+    def __init__(self, engine: "Engine", free_atoms, dw_class, theta0, theta1, target,
+                 ckpt_every: int = 64):
+        import torch
+        self.engine = engine
+        engine.set_fit(free_atoms, dw_class, ckpt_every)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.free = torch.as_tensor(np.asarray(free_atoms, dtype=np.int64), device=dev)
+        cls = np.asarray(dw_class, dtype=np.int64)
+        self.members = torch.as_tensor(np.nonzero(cls >= 0)[0], device=dev)
+        self.member_class = torch.as_tensor(cls[cls >= 0], device=dev)
+        self.atoms0 = torch.as_tensor(np.asarray(engine.wl.atoms, dtype=np.float64), device=dev)
+        self.dw0 = torch.as_tensor(np.asarray(engine.wl.dw, dtype=np.float64), device=dev)
+        self.theta0, self.theta1, self.target = theta0, theta1, target
+        self._fn = _rfactor_function()
+
+    def _evaluate(self, z, b):
+        n_sets = z.shape[0]
+        atoms = self.atoms0.expand(n_sets, -1, -1).clone()
+        atoms[:, self.free, 2] = z.detach()
+        dw = self.dw0.expand(n_sets, -1).clone()
+        dw[:, self.members] = b.detach()[:, self.member_class]
+        self.engine.set_structures(atoms.contiguous(), dw.contiguous())
+        return self.engine.rfactor_grad(self.theta0, self.theta1, self.target)
+
+    def __call__(self, z, b):
+        return self._fn.apply(z, b, self)

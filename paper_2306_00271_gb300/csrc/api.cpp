@@ -134,8 +134,15 @@ struct trh_ctx {
   DevBuf<int> d_species, d_lmap, d_status;
   DevBuf<unsigned char> d_img;
   std::vector<int> h_status;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   trh_stats stats{};
+  // fit parameters (trh_set_fit): free z coordinates, Debye-Waller classes, and the atoms whose
+  // derivatives the reverse sweep accumulates (union of both)
+  int n_free = 0, n_classes = 0, ckpt_every = 64;
+  std::vector<int> free_atoms, dw_class, active, free_active, class_of_active;
+  DevBuf<int> d_active, d_free_active, d_class_active, d_rflag;
+  DevBuf<double2> d_ckpt, d_segQ, d_segPb, d_segR, d_adjZ;
+  DevBuf<double> d_jacA, d_target, d_jac, d_R, d_gz, d_gb;
 };
 
 extern "C" {
@@ -358,74 +365,72 @@ int trh_set_structure(trh_ctx* c, int n_sets, const double* atoms, const double*
   return upload_sets(c);
 }
 
-int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
-                      void* rho_out, double* eta_out, void* stream) {
-  const auto t_start = std::chrono::steady_clock::now();
-  if (!c || n_angles < 1 || !theta0 || !theta1) return fail(TRH_EINVAL, "bad arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  int launched = 0;
+static int upload_angles(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
+                         cudaStream_t st) {
+  if (n_angles < 1 || !theta0 || !theta1) return fail(TRH_EINVAL, "bad arguments");
   const bool dev_t0 = is_device_ptr(theta0), dev_t1 = is_device_ptr(theta1);
   if (!dev_t0) {
     for (int a = 0; a < n_angles; ++a)
       if (!(theta0[a] > 0 && theta0[a] < 90))
         return fail(TRH_EINVAL, "theta0[%d] = %g outside (0, 90)", a, theta0[a]);
   }
-  const size_t pairs = (size_t)c->n_sets * n_angles;
   TRH_CUDA(c->d_theta.ensure(2 * (size_t)n_angles));
   TRH_CUDA(cudaMemcpyAsync(c->d_theta.p, theta0, n_angles * 8,
                            dev_t0 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   TRH_CUDA(cudaMemcpyAsync(c->d_theta.p + n_angles, theta1, n_angles * 8,
                            dev_t1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   if (!c->ev[0])
-    for (int i = 0; i < 4; ++i) TRH_CUDA(cudaEventCreate(&c->ev[i]));
-  const bool rebuilt = c->tables_dirty;
-  if (c->tables_dirty) {
-    TRH_CUDA(cudaEventRecord(c->ev[0], st));
-    trh::PotentialParams pp{};
-    pp.g = c->d_g.p;
-    pp.atoms = c->d_atoms.p;
-    pp.dw = c->d_dw.p;
-    pp.species = c->d_species.p;
-    pp.sf = c->d_sf.p;
-    pp.node_z = c->d_nodes.p;
-    const double gl = 1.0 + c->energy / kMc2;
-    const double scale = 4.0 * kPi * gl / c->area;
-    pp.pref = make_double2(c->particle * scale, -c->absorption * scale);
-    pp.M = c->M;
-    pp.n_atoms = c->n_atoms;
-    pp.n_nodes = c->n_nodes;
-    pp.n_sets = c->n_sets;
-    pp.F = c->d_F.p;
-    pp.u = c->d_u.p;
-    pp.u32 = nullptr;
-    TRH_CUDA(trh::launch_potential(pp, st, &launched));
-    if (c->precision == TRH_MIXED) {
-      TRH_CUDA(c->d_img.ensure((size_t)c->n_sets * c->n_nodes * trh::mixed_image_bytes_per_node()));
-      trh::MixedImageParams mp{};
-      mp.u = c->d_u.p;
-      mp.lmap = c->d_lmap.p;
-      mp.img = c->d_img.p;
-      mp.N = c->N;
-      mp.M = c->M;
-      mp.n_nodes = c->n_nodes;
-      mp.n_sets = c->n_sets;
-      TRH_CUDA(trh::launch_umma_images(mp, st, &launched));
-    }
-    TRH_CUDA(cudaEventRecord(c->ev[1], st));
-    c->tables_dirty = false;
+    for (int i = 0; i < 6; ++i) TRH_CUDA(cudaEventCreate(&c->ev[i]));
+  return TRH_OK;
+}
+
+static double2 potential_prefactor(const trh_ctx* c) {
+  const double gl = 1.0 + c->energy / kMc2;
+  const double scale = 4.0 * kPi * gl / c->area;
+  return make_double2(c->particle * scale, -c->absorption * scale);
+}
+
+// Potential tables (and, on the mixed path, the tensor-core images) if the structure changed;
+// events ev[0], ev[1] bracket them. Sets *rebuilt.
+static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuilt) {
+  *rebuilt = c->tables_dirty;
+  if (!c->tables_dirty) return TRH_OK;
+  TRH_CUDA(cudaEventRecord(c->ev[0], st));
+  trh::PotentialParams pp{};
+  pp.g = c->d_g.p;
+  pp.atoms = c->d_atoms.p;
+  pp.dw = c->d_dw.p;
+  pp.species = c->d_species.p;
+  pp.sf = c->d_sf.p;
+  pp.node_z = c->d_nodes.p;
+  pp.pref = potential_prefactor(c);
+  pp.M = c->M;
+  pp.n_atoms = c->n_atoms;
+  pp.n_nodes = c->n_nodes;
+  pp.n_sets = c->n_sets;
+  pp.F = c->d_F.p;
+  pp.u = c->d_u.p;
+  pp.u32 = nullptr;
+  TRH_CUDA(trh::launch_potential(pp, st, launched));
+  if (c->precision == TRH_MIXED) {
+    TRH_CUDA(c->d_img.ensure((size_t)c->n_sets * c->n_nodes * trh::mixed_image_bytes_per_node()));
+    trh::MixedImageParams mp{};
+    mp.u = c->d_u.p;
+    mp.lmap = c->d_lmap.p;
+    mp.img = c->d_img.p;
+    mp.N = c->N;
+    mp.M = c->M;
+    mp.n_nodes = c->n_nodes;
+    mp.n_sets = c->n_sets;
+    TRH_CUDA(trh::launch_umma_images(mp, st, launched));
   }
-  const bool dev_rho = is_device_ptr(rho_out), dev_eta = is_device_ptr(eta_out);
-  double2* rho = dev_rho ? (double2*)rho_out : nullptr;
-  double* eta = dev_eta ? eta_out : nullptr;
-  if (!rho) {
-    TRH_CUDA(c->d_rho.ensure(pairs * c->N));
-    rho = c->d_rho.p;
-  }
-  if (!eta) {
-    TRH_CUDA(c->d_eta.ensure(pairs * c->N));
-    eta = c->d_eta.p;
-  }
-  TRH_CUDA(c->d_status.ensure(2 * pairs));
+  TRH_CUDA(cudaEventRecord(c->ev[1], st));
+  c->tables_dirty = false;
+  return TRH_OK;
+}
+
+static trh::IntegrateParams integrate_params(trh_ctx* c, int n_angles, size_t pairs,
+                                             double2* rho, double* eta) {
   trh::IntegrateParams ip{};
   ip.sch = c->scheme;
   ip.ang.theta0 = c->d_theta.p;
@@ -447,6 +452,74 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   ip.L = c->L;
   ip.h = c->h;
   ip.threshold = c->threshold;
+  return ip;
+}
+
+// Reads back the per-pair status words (the stream is synchronised) and fills the counters.
+static int collect_status(trh_ctx* c, int n_angles, size_t pairs, cudaStream_t st) {
+  c->h_status.resize(2 * pairs);
+  TRH_CUDA(cudaMemcpyAsync(c->h_status.data(), c->d_status.p, 2 * pairs * sizeof(int),
+                           cudaMemcpyDeviceToHost, st));
+  TRH_CUDA(cudaStreamSynchronize(st));
+  trh_stats& S = c->stats;
+  S.n_angles = n_angles;
+  S.rhst_total = 0;
+  S.rhst_max = 0;
+  S.n_bad = 0;
+  S.first_bad_set = S.first_bad_angle = -1;
+  S.first_bad_status = TRH_OK;
+  for (size_t q = 0; q < pairs; ++q) {
+    const int stq = c->h_status[q], nr = c->h_status[pairs + q];
+    S.rhst_total += nr;
+    if (nr > S.rhst_max) S.rhst_max = nr;
+    if (stq != 0) {
+      if (S.n_bad == 0) {
+        S.first_bad_set = (int)(q / n_angles);
+        S.first_bad_angle = (int)(q % n_angles);
+        S.first_bad_status = stq;
+      }
+      S.n_bad++;
+    }
+  }
+  return TRH_OK;
+}
+
+static int bad_pairs_error(const trh_ctx* c) {
+  const trh_stats& S = c->stats;
+  return fail(S.first_bad_status, "%d (set, angle) pairs failed; first: set %d angle %d (%s)",
+              S.n_bad, S.first_bad_set, S.first_bad_angle, trh_strerror(S.first_bad_status));
+}
+
+static float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.f;
+}
+
+int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
+                      void* rho_out, double* eta_out, void* stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!c) return fail(TRH_EINVAL, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  int launched = 0;
+  int rc = upload_angles(c, n_angles, theta0, theta1, st);
+  if (rc != TRH_OK) return rc;
+  const size_t pairs = (size_t)c->n_sets * n_angles;
+  bool rebuilt = false;
+  rc = build_tables(c, st, &launched, &rebuilt);
+  if (rc != TRH_OK) return rc;
+  const bool dev_rho = is_device_ptr(rho_out), dev_eta = is_device_ptr(eta_out);
+  double2* rho = dev_rho ? (double2*)rho_out : nullptr;
+  double* eta = dev_eta ? eta_out : nullptr;
+  if (!rho) {
+    TRH_CUDA(c->d_rho.ensure(pairs * c->N));
+    rho = c->d_rho.p;
+  }
+  if (!eta) {
+    TRH_CUDA(c->d_eta.ensure(pairs * c->N));
+    eta = c->d_eta.p;
+  }
+  TRH_CUDA(c->d_status.ensure(2 * pairs));
+  trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, rho, eta);
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
     trh::MixedParams mp{};
@@ -483,41 +556,253 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   if (eta_out && !dev_eta)
     TRH_CUDA(cudaMemcpyAsync(eta_out, eta, pairs * c->N * sizeof(double),
                              cudaMemcpyDeviceToHost, st));
-  c->h_status.resize(2 * pairs);
-  TRH_CUDA(cudaMemcpyAsync(c->h_status.data(), c->d_status.p, 2 * pairs * sizeof(int),
-                           cudaMemcpyDeviceToHost, st));
-  TRH_CUDA(cudaStreamSynchronize(st));
+  rc = collect_status(c, n_angles, pairs, st);
+  if (rc != TRH_OK) return rc;
   trh_stats& S = c->stats;
-  S.n_angles = n_angles;
-  S.rhst_total = 0;
-  S.rhst_max = 0;
-  S.n_bad = 0;
-  S.first_bad_set = S.first_bad_angle = -1;
-  S.first_bad_status = TRH_OK;
-  for (size_t q = 0; q < pairs; ++q) {
-    const int stq = c->h_status[q], nr = c->h_status[pairs + q];
-    S.rhst_total += nr;
-    if (nr > S.rhst_max) S.rhst_max = nr;
-    if (stq != 0) {
-      if (S.n_bad == 0) {
-        S.first_bad_set = (int)(q / n_angles);
-        S.first_bad_angle = (int)(q % n_angles);
-        S.first_bad_status = stq;
-      }
-      S.n_bad++;
-    }
-  }
   S.kernels_launched = launched;
-  float ms = 0.f;
-  S.ms_potential = 0.0;
-  if (rebuilt && cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) S.ms_potential = ms;
-  S.ms_integrate = (cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]) == cudaSuccess) ? ms : 0.0;
+  S.ms_potential = rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
+  S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
+  S.ms_gradient = 0.0;
   S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
                   .count();
-  if (S.n_bad)
-    return fail(S.first_bad_status, "%d (set, angle) pairs failed; first: set %d angle %d (%s)",
-                S.n_bad, S.first_bad_set, S.first_bad_angle, trh_strerror(S.first_bad_status));
+  if (S.n_bad) return bad_pairs_error(c);
   return TRH_OK;
+}
+
+int trh_set_fit(trh_ctx* c, int n_free, const int* free_atoms, int n_classes,
+                const int* dw_class, int ckpt_every) {
+  if (!c) return fail(TRH_EINVAL, "ctx is NULL");
+  if (n_free < 0 || n_classes < 0 || n_free + n_classes < 1)
+    return fail(TRH_EINVAL, "need at least one parameter");
+  if (n_free > 0 && !free_atoms) return fail(TRH_EINVAL, "free_atoms is NULL");
+  if (n_classes > 0 && !dw_class) return fail(TRH_EINVAL, "dw_class is NULL");
+  std::vector<int> fa(free_atoms, free_atoms + n_free);
+  std::vector<int> cls(c->n_atoms, -1);
+  for (int k = 0; k < n_free; ++k) {
+    if (fa[k] < 0 || fa[k] >= c->n_atoms) return fail(TRH_EINVAL, "free_atoms[%d] out of range", k);
+    for (int j = 0; j < k; ++j)
+      if (fa[j] == fa[k]) return fail(TRH_EINVAL, "free_atoms[%d] repeats atom %d", k, fa[k]);
+  }
+  if (n_classes > 0) {
+    std::vector<int> members(n_classes, 0);
+    for (int a = 0; a < c->n_atoms; ++a) {
+      cls[a] = dw_class[a];
+      if (cls[a] < -1 || cls[a] >= n_classes)
+        return fail(TRH_EINVAL, "dw_class[%d] = %d outside [-1, %d)", a, cls[a], n_classes);
+      if (cls[a] >= 0) members[cls[a]]++;
+    }
+    for (int k = 0; k < n_classes; ++k)
+      if (!members[k]) return fail(TRH_EINVAL, "Debye-Waller class %d has no atom", k);
+  }
+  std::vector<int> active, free_active(n_free), class_of_active;
+  std::vector<int> pos(c->n_atoms, -1);
+  for (int a = 0; a < c->n_atoms; ++a) {
+    bool is_free = false;
+    for (int k = 0; k < n_free; ++k) is_free |= (fa[k] == a);
+    if (is_free || cls[a] >= 0) {
+      pos[a] = (int)active.size();
+      active.push_back(a);
+      class_of_active.push_back(cls[a]);
+    }
+  }
+  if (active.size() > 64) return fail(TRH_EUNSUPPORTED, "at most 64 differentiated atoms");
+  for (int k = 0; k < n_free; ++k) free_active[k] = pos[fa[k]];
+  TRH_CUDA(c->d_active.ensure(active.size()));
+  TRH_CUDA(c->d_class_active.ensure(active.size()));
+  TRH_CUDA(c->d_free_active.ensure(n_free > 0 ? n_free : 1));
+  TRH_CUDA(cudaMemcpy(c->d_active.p, active.data(), active.size() * 4, cudaMemcpyHostToDevice));
+  TRH_CUDA(cudaMemcpy(c->d_class_active.p, class_of_active.data(), active.size() * 4,
+                      cudaMemcpyHostToDevice));
+  if (n_free > 0)
+    TRH_CUDA(cudaMemcpy(c->d_free_active.p, free_active.data(), n_free * 4,
+                        cudaMemcpyHostToDevice));
+  c->n_free = n_free;
+  c->n_classes = n_classes;
+  c->free_atoms.swap(fa);
+  c->dw_class.swap(cls);
+  c->active.swap(active);
+  c->free_active.swap(free_active);
+  c->class_of_active.swap(class_of_active);
+  c->ckpt_every = ckpt_every > 0 ? ckpt_every : 64;
+  return TRH_OK;
+}
+
+// Forward pass with checkpoints, then the reverse sweep segment by segment: leaves eta in
+// d_eta and d eta_1 / d(z_a, B_a) of the active atoms in d_jacA.
+static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
+                             const double* theta1, cudaStream_t st, int* launched,
+                             bool* rebuilt) {
+  if (c->n_free + c->n_classes < 1) return fail(TRH_EINVAL, "call trh_set_fit first");
+  int rc = upload_angles(c, n_angles, theta0, theta1, st);
+  if (rc != TRH_OK) return rc;
+  rc = build_tables(c, st, launched, rebuilt);
+  if (rc != TRH_OK) return rc;
+  const size_t pairs = (size_t)c->n_sets * n_angles;
+  const size_t NN = (size_t)c->N * c->N;
+  const int C = c->ckpt_every, s = c->scheme.s;
+  const int n_seg = (c->L + C - 1) / C;
+  const int kseg = s * C + 1;
+  const int n_act = (int)c->active.size();
+  TRH_CUDA(c->d_rho.ensure(pairs * c->N));
+  TRH_CUDA(c->d_eta.ensure(pairs * c->N));
+  TRH_CUDA(c->d_status.ensure(2 * pairs));
+  TRH_CUDA(c->d_ckpt.ensure(pairs * (n_seg + 1) * 2 * NN));
+  TRH_CUDA(c->d_segQ.ensure(pairs * kseg * NN));
+  TRH_CUDA(c->d_segPb.ensure(pairs * kseg * NN));
+  TRH_CUDA(c->d_segR.ensure(pairs * C * 2 * NN));
+  TRH_CUDA(c->d_rflag.ensure(pairs * C));
+  TRH_CUDA(c->d_adjZ.ensure(pairs * 2 * NN));
+  TRH_CUDA(c->d_jacA.ensure(pairs * 2 * n_act));
+  TRH_CUDA(cudaMemsetAsync(c->d_jacA.p, 0, pairs * 2 * n_act * sizeof(double), st));
+
+  trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, c->d_rho.p, c->d_eta.p);
+  ip.ckpt = c->d_ckpt.p;
+  ip.ckpt_every = C;
+  ip.n_ckpt = n_seg + 1;
+  TRH_CUDA(cudaEventRecord(c->ev[2], st));
+  TRH_CUDA(trh::launch_integrate_fp64(ip, st, launched));
+  TRH_CUDA(cudaEventRecord(c->ev[3], st));
+
+  trh::GradParams g{};
+  g.ip = ip;
+  g.segQ = c->d_segQ.p;
+  g.segPb = c->d_segPb.p;
+  g.segR = c->d_segR.p;
+  g.rflag = c->d_rflag.p;
+  g.adjZ = c->d_adjZ.p;
+  g.status = c->d_status.p;
+  g.kseg = kseg;
+  g.F = c->d_F.p;
+  g.gdiff = c->d_g.p;
+  g.atoms = c->d_atoms.p;
+  g.dw = c->d_dw.p;
+  g.species = c->d_species.p;
+  g.sf = c->d_sf.p;
+  g.node_z = c->d_nodes.p;
+  g.active = c->d_active.p;
+  g.n_active = n_act;
+  g.n_atoms = c->n_atoms;
+  g.pref = potential_prefactor(c);
+  g.jac_atoms = c->d_jacA.p;
+  for (int seg = n_seg - 1; seg >= 0; --seg) {
+    g.seg = seg;
+    TRH_CUDA(trh::launch_grad_recompute(g, st, launched));
+    TRH_CUDA(trh::launch_grad_adjoint(g, st, launched));
+    TRH_CUDA(trh::launch_grad_ubar(g, st, launched));
+  }
+  TRH_CUDA(cudaEventRecord(c->ev[4], st));
+  return TRH_OK;
+}
+
+static int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!dst) return TRH_OK;
+  TRH_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyDeviceToHost, st));
+  return TRH_OK;
+}
+
+static int finish_gradient_call(trh_ctx* c, int n_angles, int launched, bool rebuilt,
+                                std::chrono::steady_clock::time_point t_start,
+                                cudaStream_t st) {
+  const size_t pairs = (size_t)c->n_sets * n_angles;
+  int rc = collect_status(c, n_angles, pairs, st);
+  if (rc != TRH_OK) return rc;
+  trh_stats& S = c->stats;
+  S.kernels_launched = launched;
+  S.ms_potential = rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
+  S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
+  S.ms_gradient = elapsed_ms(c->ev[3], c->ev[5]);
+  S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
+                  .count();
+  if (S.n_bad) return bad_pairs_error(c);
+  return TRH_OK;
+}
+
+int trh_curve_jacobian(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
+                       double* eta_out, double* jac_out, void* stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!c || !jac_out) return fail(TRH_EINVAL, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  int launched = 0;
+  bool rebuilt = false;
+  int rc = run_reverse_sweep(c, n_angles, theta0, theta1, st, &launched, &rebuilt);
+  if (rc != TRH_OK) return rc;
+  const size_t pairs = (size_t)c->n_sets * n_angles;
+  const int P = c->n_free + c->n_classes;
+  TRH_CUDA(c->d_jac.ensure(pairs * P));
+  trh::RFactorParams r{};
+  r.eta = c->d_eta.p;
+  r.target = nullptr;
+  r.jac_atoms = c->d_jacA.p;
+  r.free_active = c->d_free_active.p;
+  r.class_of_active = c->d_class_active.p;
+  r.n_free = c->n_free;
+  r.n_classes = c->n_classes;
+  r.n_active = (int)c->active.size();
+  r.n_angles = n_angles;
+  r.n_sets = c->n_sets;
+  r.N = c->N;
+  r.jac = c->d_jac.p;
+  TRH_CUDA(trh::launch_rfactor(r, st, &launched));
+  TRH_CUDA(cudaEventRecord(c->ev[5], st));
+  rc = copy_out(jac_out, c->d_jac.p, pairs * P * sizeof(double), st);
+  if (rc == TRH_OK) rc = copy_out(eta_out, c->d_eta.p, pairs * c->N * sizeof(double), st);
+  if (rc != TRH_OK) return rc;
+  return finish_gradient_call(c, n_angles, launched, rebuilt, t_start, st);
+}
+
+int trh_rfactor_grad(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
+                     const double* target, double* R_out, double* dR_dz, double* dR_dB,
+                     void* stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!c || !target) return fail(TRH_EINVAL, "bad arguments");
+  if (c->n_free > 0 && !dR_dz) return fail(TRH_EINVAL, "dR_dz is NULL");
+  if (c->n_classes > 0 && !dR_dB) return fail(TRH_EINVAL, "dR_dB is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!is_device_ptr(target)) {
+    double sum = 0.0;
+    for (int a = 0; a < n_angles; ++a) {
+      if (!(target[a] >= 0)) return fail(TRH_EINVAL, "target[%d] < 0", a);
+      sum += target[a];
+    }
+    if (!(sum > 0)) return fail(TRH_EINVAL, "target curve sums to zero");
+  }
+  int launched = 0;
+  bool rebuilt = false;
+  int rc = run_reverse_sweep(c, n_angles, theta0, theta1, st, &launched, &rebuilt);
+  if (rc != TRH_OK) return rc;
+  TRH_CUDA(c->d_target.ensure(n_angles));
+  TRH_CUDA(cudaMemcpyAsync(c->d_target.p, target, n_angles * sizeof(double),
+                           is_device_ptr(target) ? cudaMemcpyDeviceToDevice
+                                                 : cudaMemcpyHostToDevice, st));
+  TRH_CUDA(c->d_R.ensure(c->n_sets));
+  TRH_CUDA(c->d_gz.ensure((size_t)c->n_sets * (c->n_free > 0 ? c->n_free : 1)));
+  TRH_CUDA(c->d_gb.ensure((size_t)c->n_sets * (c->n_classes > 0 ? c->n_classes : 1)));
+  trh::RFactorParams r{};
+  r.eta = c->d_eta.p;
+  r.target = c->d_target.p;
+  r.jac_atoms = c->d_jacA.p;
+  r.free_active = c->d_free_active.p;
+  r.class_of_active = c->d_class_active.p;
+  r.n_free = c->n_free;
+  r.n_classes = c->n_classes;
+  r.n_active = (int)c->active.size();
+  r.n_angles = n_angles;
+  r.n_sets = c->n_sets;
+  r.N = c->N;
+  r.jac = nullptr;
+  r.R = c->d_R.p;
+  r.grad_z = c->d_gz.p;
+  r.grad_b = c->d_gb.p;
+  TRH_CUDA(trh::launch_rfactor(r, st, &launched));
+  TRH_CUDA(cudaEventRecord(c->ev[5], st));
+  rc = copy_out(R_out, c->d_R.p, c->n_sets * sizeof(double), st);
+  if (rc == TRH_OK && c->n_free > 0)
+    rc = copy_out(dR_dz, c->d_gz.p, (size_t)c->n_sets * c->n_free * sizeof(double), st);
+  if (rc == TRH_OK && c->n_classes > 0)
+    rc = copy_out(dR_dB, c->d_gb.p, (size_t)c->n_sets * c->n_classes * sizeof(double), st);
+  if (rc != TRH_OK) return rc;
+  return finish_gradient_call(c, n_angles, launched, rebuilt, t_start, st);
 }
 
 int trh_query(const trh_ctx* c, trh_stats* out) {
@@ -529,7 +814,7 @@ int trh_query(const trh_ctx* c, trh_stats* out) {
 void trh_destroy(trh_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 6; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   c->d_kvec.release();
   c->d_g.release();
@@ -546,6 +831,21 @@ void trh_destroy(trh_ctx* c) {
   c->d_lmap.release();
   c->d_status.release();
   c->d_img.release();
+  c->d_active.release();
+  c->d_free_active.release();
+  c->d_class_active.release();
+  c->d_rflag.release();
+  c->d_ckpt.release();
+  c->d_segQ.release();
+  c->d_segPb.release();
+  c->d_segR.release();
+  c->d_adjZ.release();
+  c->d_jacA.release();
+  c->d_target.release();
+  c->d_jac.release();
+  c->d_R.release();
+  c->d_gz.release();
+  c->d_gb.release();
   delete c;
 }
 

@@ -48,6 +48,11 @@ struct IntegrateParams {
   int N, M, n_nodes, n_sets, L;
   double h;
   double threshold;
+  // Optional checkpoints for the reverse sweep (nullptr: none). Slot c < n_ckpt - 1 holds the
+  // state [Q; P] at the start of step c * ckpt_every, slot n_ckpt - 1 the final state;
+  // layout [n_sets][n_angles][n_ckpt][2][N][N] complex.
+  double2* ckpt;
+  int ckpt_every, n_ckpt;
 };
 
 // Potential tables (kernels in potential.cu).
@@ -89,6 +94,51 @@ struct MixedParams {
   float kick_hi[kMaxStages + 2], kick_lo[kMaxStages + 2];
   float drift_hi[kMaxStages], drift_lo[kMaxStages];
 };
+
+// Reverse sweep of the FP64 path (adjoint_fp64.cu): gradients of the specular intensity with
+// respect to atomic z coordinates and Debye-Waller factors. Pair = (set, angle), pair-major.
+struct GradParams {
+  IntegrateParams ip;          // geometry, tables and scheme of the forward pass (ckpt set)
+  double2* segQ;               // [pairs][kseg][N][N]  Q at each kick of the segment
+  double2* segPb;              // [pairs][kseg][N][N]  Pbar entering each kick's adjoint
+  double2* segR;               // [pairs][C][2][N][N]  (Q before, P after) of each RHST
+  int* rflag;                  // [pairs][C]           1 if that step ended in an RHST
+  double2* adjZ;               // [pairs][2][N][N]     adjoint state carried between segments
+  int* status;                 // [pairs]              forward status (0 = ok); failures skip
+  int seg;                     // segment: steps [seg * C, min(seg * C + C, L)), C = ckpt_every
+  int kseg;                    // kick slots per segment: s * C + 1
+  // contraction with the derivatives of the potential model
+  const double2* F;            // [n_sets][4 * n_atoms][M] z-independent factors (no pref)
+  const double2* gdiff;        // [M] difference vectors g (1/A)
+  const double* atoms;         // [n_sets][n_atoms][3]
+  const double* dw;            // [n_sets][n_atoms]
+  const int* species;          // [n_atoms]
+  const double* sf;            // [n_species][8]
+  const double* node_z;        // [n_nodes]
+  const int* active;           // [n_active] atoms whose z and B derivatives are accumulated
+  int n_active, n_atoms;
+  double2 pref;                // (s - i*absorption) 4 pi gamma_L / A_cell
+  double* jac_atoms;           // [pairs][n_active][2]  d eta_1/d z_a, d eta_1/d B_a (accumulated)
+};
+
+// R-factor of the specular curve and the chain rule to the fit parameters (adjoint_fp64.cu).
+struct RFactorParams {
+  const double* eta;           // [pairs][N] (eta_1 = column 0)
+  const double* target;        // [n_angles], or nullptr (Jacobian only)
+  const double* jac_atoms;     // [pairs][n_active][2]
+  const int* free_active;      // [n_free] index into the active list of each free z
+  const int* class_of_active;  // [n_active] Debye-Waller class or -1
+  int n_free, n_classes, n_active, n_angles, n_sets, N;
+  double* jac;                 // [pairs][n_free + n_classes] or nullptr
+  double* R;                   // [n_sets] (written if target != nullptr)
+  double* grad_z;              // [n_sets][n_free]    (written if target != nullptr)
+  double* grad_b;              // [n_sets][n_classes] (written if target != nullptr)
+};
+
+cudaError_t launch_grad_recompute(const GradParams& g, cudaStream_t st, int* n_launched);
+cudaError_t launch_grad_adjoint(const GradParams& g, cudaStream_t st, int* n_launched);
+cudaError_t launch_grad_ubar(const GradParams& g, cudaStream_t st, int* n_launched);
+cudaError_t launch_rfactor(const RFactorParams& r, cudaStream_t st, int* n_launched);
 
 cudaError_t launch_potential(const PotentialParams& p, cudaStream_t st, int* n_launched);
 cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* n_launched);

@@ -1,0 +1,138 @@
+"""Reverse sweep (adjoint of Algorithm 1 on the FP64 path) vs the oracle's central differences.
+
+Bar: gradients within 1e-5 relative (max abs difference over parameters / max abs oracle
+gradient); the oracle's central differences themselves agree with a 40-digit five-point
+derivative to ~1e-10 (tests/test_oracle_gradient.py), so the bar is set by the CUDA path."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gradient as G
+from paper_2306_00271_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rfactor_fit_n61.npz")
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2306_00271_gb300 import api as a
+    a.load()
+    return a
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _small():
+    # 37 beams (three 16-row tiles and a ragged tail), 240 steps over a 12 A slab: dozens of
+    # RHSTs, and with checkpoints every 32 steps eight segments of which the last is ragged
+    return W.tiny(n_beams=37, n_steps=240, seed=31, depth=12.0, theta0=(0.6, 1.4, 2.9, 4.1))
+
+
+def test_jacobian_matches_oracle_differences(api):
+    wl = _small()
+    free, cls = np.array([0, 1, 2, 3]), np.array([0, 1, 1, 0])
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_fit(free, cls, ckpt_every=32)
+    eta, jac = eng.curve_jacobian(wl.theta0, wl.theta1)
+    fd = G.fd_gradient(wl, free, cls, target=np.ones(len(wl.theta0)))
+    jac = jac.cpu().numpy()[0]
+    assert jac.shape == fd["jac"].shape
+    assert _rel(jac, fd["jac"]) <= 1e-6, _rel(jac, fd["jac"])
+    assert np.allclose(eta.cpu().numpy()[0][:, 0], fd["eta1"], rtol=1e-10, atol=0)
+    st = eng.stats()
+    assert st["rhst_total"] > 10 * len(wl.theta0) and st["ms_gradient"] > 0
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(api):
+    wl = _small()
+    free, cls = np.array([0, 2]), np.array([-1, 0, 0, -1])
+    eng = api.Engine(wl, "fp64", "sp4")
+    out = []
+    for C in (7, 64, 240, 1000):
+        eng.set_fit(free, cls, ckpt_every=C)
+        out.append(eng.curve_jacobian(wl.theta0, wl.theta1)[1].cpu().numpy())
+    for o in out[1:]:
+        assert _rel(o, out[0]) <= 1e-12
+
+
+def test_rfactor_gradient_small(api):
+    wl = _small()
+    free, cls = np.array([1, 3]), np.array([0, 0, 1, 1])
+    target = np.array([0.05, 0.02, 0.01, 0.004])
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_fit(free, cls, ckpt_every=50)
+    R, gz, gb = eng.rfactor_grad(wl.theta0, wl.theta1, target)
+    fd = G.fd_gradient(wl, free, cls, target)
+    g = np.concatenate([gz.cpu().numpy()[0], gb.cpu().numpy()[0]])
+    assert float(R[0]) == pytest.approx(fd["R"], rel=1e-10)
+    assert _rel(g, fd["grad"]) <= 1e-6, _rel(g, fd["grad"])
+
+
+def test_parameter_sets_are_independent(api):
+    wl = W.tiny(n_beams=13, n_steps=120, seed=5, depth=9.0, theta0=(1.0, 2.0, 3.0))
+    free, cls = np.array([0, 1, 2]), np.array([0, 0, 1, 1])
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_fit(free, cls, ckpt_every=40)
+    a2 = wl.atoms.copy()
+    a2[:, 2] -= 0.3
+    dw2 = wl.dw + 0.2
+    eng.set_structures(np.stack([wl.atoms, a2]), np.stack([wl.dw, dw2]))
+    _, jac2 = eng.curve_jacobian(wl.theta0, wl.theta1)
+    for k, (at, dw) in enumerate(((wl.atoms, wl.dw), (a2, dw2))):
+        eng.set_structures(at[None], dw[None])
+        _, jac1 = eng.curve_jacobian(wl.theta0, wl.theta1)
+        assert _rel(jac2.cpu().numpy()[k], jac1.cpu().numpy()[0]) <= 1e-13
+
+
+def test_full_size_rfactor_gradient_matches_golden(api):
+    """12 surface z and 6 Debye-Waller classes at N = 61, 2000 slices, 60 angles, checkpoints
+    every 64 steps; target and gradient from the oracle (tests/golden/make_golden_grad.py)."""
+    gold = np.load(GOLDEN)
+    fp = W.rfactor_fit()
+    wl = fp.workload
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_fit(fp.free_atoms, fp.dw_class, ckpt_every=64)
+    R, gz, gb = eng.rfactor_grad(wl.theta0, wl.theta1, gold["target"])
+    g = np.concatenate([gz.cpu().numpy()[0], gb.cpu().numpy()[0]])
+    assert float(R[0]) == pytest.approx(float(gold["R"]), rel=1e-9)
+    assert _rel(g, gold["grad"]) <= TOL, _rel(g, gold["grad"])
+    st = eng.stats()
+    assert st["n_bad"] == 0 and st["kernels_launched"] >= 3 * 32
+
+
+def test_autograd_function(api):
+    import torch
+    wl = W.tiny(n_beams=13, n_steps=100, seed=8, depth=8.0, theta0=(0.9, 1.7, 2.6))
+    free, cls = np.array([0, 3]), np.array([0, -1, 0, 1])
+    target = np.array([0.03, 0.01, 0.02])
+    eng = api.Engine(wl, "fp64", "sp4")
+    fit = api.RFactor(eng, free, cls, wl.theta0, wl.theta1, target, ckpt_every=25)
+    z = torch.tensor(wl.atoms[free, 2][None], dtype=torch.float64, device="cuda",
+                     requires_grad=True)
+    b = torch.tensor([[wl.dw[0], wl.dw[3]]], dtype=torch.float64, device="cuda",
+                     requires_grad=True)
+    R = fit(z, b)
+    (2.0 * R.sum()).backward()
+    fd = G.fd_gradient(wl, free, cls, target)
+    assert float(R[0]) == pytest.approx(fd["R"], rel=1e-10)
+    g = np.concatenate([z.grad.cpu().numpy()[0], b.grad.cpu().numpy()[0]])
+    assert _rel(g, 2.0 * fd["grad"]) <= 1e-6
+
+
+def test_fit_argument_errors(api):
+    wl = W.tiny(n_beams=3, n_steps=10)
+    eng = api.Engine(wl, "fp64", "sp4")
+    t0, t1, jac = np.array([1.5]), np.array([0.0]), np.zeros(8)
+    code = eng.lib.trh_curve_jacobian(eng.ctx, 1, api._ptr(t0), api._ptr(t1), None,
+                                      api._ptr(jac), None)
+    assert code == api.TRH_EINVAL            # no trh_set_fit yet
+    for free, cls in (([7], None), ([0, 0], None), ([], [0, 2, -1, -1]), ([], None)):
+        with pytest.raises(api.TrhError) as e:
+            eng.set_fit(free, cls)
+        assert e.value.code == api.TRH_EINVAL
