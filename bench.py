@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+from dataclasses import replace
 import os
 import subprocess
 import sys
@@ -103,6 +104,13 @@ def cpu_baseline(wl, n_angles: int):
     return {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(idx)} of 60 angles of the 61-beam curve (full 2000 slices each), "
                       f"{dt:.1f} s wall"}
+
+
+# DRAM bytes per kick node of the integration kernels, from one ncu capture each (dram__bytes_read
+# + dram__bytes_write of a small case, divided by its node count; the traffic of both kernels is
+# proportional to the node count). Summaries: profiles/k_integrate_mixed_trhepd_n61_L400.md and
+# profiles/k_integrate_fp64_trhepd_n61_L60.md. Set to None when the kernel changes.
+TRAFFIC_PER_NODE = {"mixed": 325.42e6 / 2401, "fp64": None}
 
 
 def algorithmic_flops(N: int, s_eff: int, L: int, n_angles: int, n_rhst_total: int) -> float:
@@ -193,13 +201,15 @@ def run_ours(args):
     return wl, results, ws, rank
 
 
-def run_gradient(local: int, warmup: int = 1):
+def run_gradient(local: int, slices: int = 0, warmup: int = 1):
     """One R-factor gradient at the differentiation workload (N = 61, 2000 slices, 60 angles,
     12 free z + 6 Debye-Waller classes, checkpoints every 64 steps), FP64 reverse sweep. The
     target curve is this library's own FP64 curve at the hidden true structure."""
     import torch
     from paper_2306_00271_gb300 import api
     fp = W.rfactor_fit()
+    if slices:
+        fp = replace(fp, workload=fp.workload.with_steps(slices))
     wl = fp.workload
     eng = api.Engine(wl, "fp64", "sp4")
     truth = W.fit_structure(fp, fp.z_true, fp.b_true)
@@ -283,15 +293,19 @@ def main():
     achieved = flops / (head["ms_integrate"] / 1e3) / 1e12
     if paths[0] == "mixed":
         peak = peaks.get("bf16_tflops", 1900.0)
+        tpn = TRAFFIC_PER_NODE["mixed"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": None if tpn is None else tpn * (6 * L + 1),
                 "peak_source": "MEASURED_PEAKS.json bf16 burst (of measured)",
                 "note": "achieved counts complex FP32-equivalent algorithmic flops"}
     else:
         bf = peaks.get("bf16_tflops", 1900.0)
         peak = bf * 1.25 / 2250.0
+        tpn = TRAFFIC_PER_NODE["fp64"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": None if tpn is None else tpn * (6 * L + 1),
                 "peak_source": "fp64: measured bf16 burst x nominal fp64/bf16 ratio (1.25/2250); "
                                "DMMA microbenchmark on this pool: 1.05 TFLOP/s"}
     out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
@@ -310,8 +324,8 @@ def main():
     if "mixed" in res and "fp64" in res:
         from oracle.curve import curve_error
         out["mixed_vs_fp64_curve_error"] = curve_error(res["mixed"]["eta"], res["fp64"]["eta"])
-    if not args.no_grad and not args.slices:
-        out["gradient"] = run_gradient(int(os.environ.get("LOCAL_RANK", "0")))
+    if not args.no_grad:
+        out["gradient"] = run_gradient(int(os.environ.get("LOCAL_RANK", "0")), args.slices)
     if ws == 1 and not args.no_cpu:
         n = args.cpu_angles or min(60, max(8, len(os.sched_getaffinity(0))))
         try:
