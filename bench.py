@@ -230,8 +230,8 @@ def run_gradient(local: int, slices: int = 0, warmup: int = 1):
     ms = ev0.elapsed_time(ev1)
     st = eng.stats()
     eng.close()
-    return {"metric": "R-factor gradients/s (N=61, L=2000, 60 angles, 18 parameters, FP64 "
-                      "reverse sweep, checkpoints every 64 steps)",
+    return {"metric": f"R-factor gradients/s (N=61, L={wl.n_steps}, 60 angles, 18 parameters, "
+                      "FP64 reverse sweep, checkpoints every 64 steps)",
             "value": 1000.0 / ms, "unit": "gradients/s", "ms_per_gradient": ms,
             "ms_forward": st["ms_integrate"], "ms_reverse": st["ms_gradient"],
             "kernels_launched": st["kernels_launched"], "R": float(R[0])}
