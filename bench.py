@@ -110,7 +110,7 @@ def cpu_baseline(wl, n_angles: int):
 # + dram__bytes_write of a small case, divided by its node count; the traffic of both kernels is
 # proportional to the node count). Summaries: profiles/k_integrate_mixed_trhepd_n61_L400.md and
 # profiles/k_integrate_fp64_trhepd_n61_L60.md. Set to None when the kernel changes.
-TRAFFIC_PER_NODE = {"mixed": 325.42e6 / 2401, "fp64": None}
+TRAFFIC_PER_NODE = {"mixed": 325.42e6 / 2401, "fp64": 1.624832e6 / 361}
 
 
 def algorithmic_flops(N: int, s_eff: int, L: int, n_angles: int, n_rhst_total: int) -> float:

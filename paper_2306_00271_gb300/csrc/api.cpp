@@ -133,6 +133,7 @@ struct trh_ctx {
   DevBuf<double> d_atoms, d_dw, d_sf, d_nodes, d_theta, d_eta;
   DevBuf<int> d_species, d_lmap, d_status;
   DevBuf<unsigned char> d_img;
+  DevBuf<double2> d_wide;         // state of the wide FP64 kernel (N > 64)
   std::vector<int> h_status;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   trh_stats stats{};
@@ -197,8 +198,8 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
   if (p->integrator == TRH_RK4) return fail(TRH_EUNSUPPORTED, "RK4 is not implemented on the GPU");
   if (p->precision == TRH_MIXED && !trh::mixed_available())
     return fail(TRH_EUNSUPPORTED, "mixed path is not built in this library");
-  if (p->precision == TRH_FP64 && p->n_beams > trh::kMaxBeamsFp64)
-    return fail(TRH_EUNSUPPORTED, "FP64 path supports N <= %d", trh::kMaxBeamsFp64);
+  if (p->precision == TRH_FP64 && p->n_beams > trh::kMaxBeamsWide)
+    return fail(TRH_EUNSUPPORTED, "FP64 path supports N <= %d", trh::kMaxBeamsWide);
   if (p->precision == TRH_MIXED && p->n_beams > trh::kMaxBeamsMixed)
     return fail(TRH_EUNSUPPORTED, "mixed path supports N <= %d", trh::kMaxBeamsMixed);
   const double det = p->a1[0] * p->a2[1] - p->a1[1] * p->a2[0];
@@ -546,8 +547,11 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
     split(c->h * c->scheme.b[sc], &mp.kick_hi[sc + 1], &mp.kick_lo[sc + 1]);
     for (int r = 0; r < sc; ++r) split(c->h * c->scheme.a[r], &mp.drift_hi[r], &mp.drift_lo[r]);
     TRH_CUDA(trh::launch_integrate_mixed(mp, st, &launched));
-  } else {
+  } else if (c->N <= trh::kMaxBeamsFp64) {
     TRH_CUDA(trh::launch_integrate_fp64(ip, st, &launched));
+  } else {
+    TRH_CUDA(c->d_wide.ensure(pairs * trh::integrate_fp64_wide_state_bytes(c->N) / sizeof(double2)));
+    TRH_CUDA(trh::launch_integrate_fp64_wide(ip, c->d_wide.p, st, &launched));
   }
   TRH_CUDA(cudaEventRecord(c->ev[3], st));
   if (rho_out && !dev_rho)
@@ -633,6 +637,8 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
                              const double* theta1, cudaStream_t st, int* launched,
                              bool* rebuilt) {
   if (c->n_free + c->n_classes < 1) return fail(TRH_EINVAL, "call trh_set_fit first");
+  if (c->N > trh::kMaxBeamsFp64)
+    return fail(TRH_EUNSUPPORTED, "the reverse sweep supports N <= %d", trh::kMaxBeamsFp64);
   int rc = upload_angles(c, n_angles, theta0, theta1, st);
   if (rc != TRH_OK) return rc;
   rc = build_tables(c, st, launched, rebuilt);
@@ -831,6 +837,7 @@ void trh_destroy(trh_ctx* c) {
   c->d_lmap.release();
   c->d_status.release();
   c->d_img.release();
+  c->d_wide.release();
   c->d_active.release();
   c->d_free_active.release();
   c->d_class_active.release();

@@ -1,0 +1,384 @@
+// FP64 path for wide beam sets (64 < N <= 256): one CTA integrates one (parameter set, angle)
+// pair from z_e to 0 (Algorithm 1) with the state Z = [Q; P] in global memory (L2-resident;
+// 2 N^2 complex128 per pair) instead of shared memory.
+//
+// Per kick (Section 3.4, FSAL-merged BAB splitting), column block by column block (64 columns):
+// the product U(tau) Q is formed in 64 x 64 x 64 tiles on the FP64 tensor pipe (DMMA), U's tile
+// gathered from the node's compact table u[M] (shared memory) through the index map l(j, k)
+// (Eq. sch2) and Q's tile read from global memory; the epilogue applies the kick
+// P <- P - h b (U Q + Gamma^2 Q) to the block's rows, and once every row block of the column block
+// is done the drift Q <- Q + h a P (columns are independent under both updates). The badness xi,
+// the RHST Z <- Z Q^{-1} (Section 3.2) and the final solve are Gauss-Jordan eliminations with
+// column operations on two stacked N x N blocks in global memory: [Q; P] -> [I; P Q^{-1}] for the
+// RHST, and [A; B] -> [I; B A^{-1}] with A = Gamma Q - i P, B = Gamma Q + i P for the assembly,
+// whose first column is rho(0) = B A^{-1} e_1 (Eq. vrhocomp times Q).
+//
+// GB300's FP64 rate bounds this kernel: a kick at N = 255 is 66 M real multiply-adds, about 40 M
+// cycles on one SM's FP64 pipe; the state traffic (a few MB of L2 reads per kick) is negligible
+// next to it.
+#include "internal.h"
+
+namespace trh {
+
+namespace {
+
+constexpr int TB = 64;               // tile edge
+constexpr int TLD = TB + 4;          // tile row stride (doubles)
+constexpr int NW = kMaxBeamsWide;    // largest N
+constexpr int WT = 256;              // threads
+constexpr double kPiW = 3.14159265358979323846;
+
+struct WideSmem {
+  double Ar[TB * TLD], Ai[TB * TLD];   // U tile
+  double Br[TB * TLD], Bi[TB * TLD];   // Q tile
+  double gam2[NW], Gr[NW], Gi[NW];
+  double cr[2 * NW], ci[2 * NW];       // scaled pivot column
+  double fr[NW], fi[NW];               // pivot row
+  double red0[WT / 32], red1[WT / 32];
+  double sin_t0;
+  int piv, flag, status, n_rhst;
+  // followed by the node's compact table: double2 tbl[M]
+};
+
+__device__ __forceinline__ void dmma_w(double (&c)[4], double a0, double a1, double b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+      "{%0,%1,%2,%3};\n"
+      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+      : "d"(a0), "d"(a1), "d"(b));
+}
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// acc += A_tile B_tile (64 x 64 complex tiles in shared memory); 8 warps in a 4 x 2 grid of
+// 16 x 32 output tiles; fixed accumulation order.
+__device__ __forceinline__ void tile_gemm(const WideSmem& S, double (&wr)[4][4], double (&wi)[4][4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mt = warp & 3, nt = warp >> 2;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll 4
+  for (int k0 = 0; k0 < TB; k0 += 4) {
+    const int a0 = (16 * mt + g) * TLD + k0 + t, a1 = a0 + 8 * TLD;
+    const double ar0 = S.Ar[a0], ar1 = S.Ar[a1], ai0 = S.Ai[a0], ai1 = S.Ai[a1];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int cb = (k0 + t) * TLD + 32 * nt + 8 * s + g;
+      const double br = S.Br[cb], bi = S.Bi[cb];
+      dmma_w(wr[s], ar0, ar1, br);
+      dmma_w(wr[s], -ai0, -ai1, bi);
+      dmma_w(wi[s], ar0, ar1, bi);
+      dmma_w(wi[s], ai0, ai1, br);
+    }
+  }
+}
+
+struct WideArgs {
+  IntegrateParams p;
+  double2* Zq;   // [pairs][N][N] Q
+  double2* Zp;   // [pairs][N][N] P
+};
+
+// One kick with coefficient hb and (if do_drift) the drift with ha, for the table in shared
+// memory.
+__device__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, double2* Q, double2* P,
+                          int N, double hb, double ha, bool do_drift) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (N + TB - 1) / TB;
+  for (int jb = 0; jb < nb; ++jb) {
+    for (int ib = 0; ib < nb; ++ib) {
+      double wr[4][4], wi[4][4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wr[s][q] = wi[s][q] = 0.0;
+      for (int kb = 0; kb < nb; ++kb) {
+        for (int e = tid; e < TB * TB; e += WT) {
+          const int r = e / TB, k = e - r * TB;
+          const int gr = ib * TB + r, gk = kb * TB + k, gc = jb * TB + k;
+          double ur = 0.0, ui = 0.0;
+          if (gr < N && gk < N) {
+            const double2 v = tbl[__ldg(lmap + gr * N + gk)];
+            ur = v.x;
+            ui = v.y;
+          }
+          S.Ar[r * TLD + k] = ur;
+          S.Ai[r * TLD + k] = ui;
+          const int qr = kb * TB + r;            // B tile row = K index
+          double br = 0.0, bi = 0.0;
+          if (qr < N && gc < N) {
+            const double2 v = Q[(size_t)qr * N + gc];
+            br = v.x;
+            bi = v.y;
+          }
+          S.Br[r * TLD + k] = br;
+          S.Bi[r * TLD + k] = bi;
+        }
+        __syncthreads();
+        tile_gemm(S, wr, wi);
+        __syncthreads();
+      }
+      const int mt = warp & 3, nt = warp >> 2, g = lane >> 2, t = lane & 3;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = ib * TB + 16 * mt + g + 8 * (q >> 1);
+          const int col = jb * TB + 32 * nt + 8 * s + 2 * t + (q & 1);
+          if (row < N && col < N) {
+            const size_t o = (size_t)row * N + col;
+            const double2 qv = Q[o], pv = P[o];
+            const double g2 = S.gam2[row];
+            P[o] = make_double2(pv.x - hb * (wr[s][q] + g2 * qv.x),
+                                pv.y - hb * (wi[s][q] + g2 * qv.y));
+          }
+        }
+    }
+    __syncthreads();   // the column block's P is final and no tile of it is still read
+    if (do_drift) {
+      for (int e = tid; e < N * TB; e += WT) {
+        const int row = e / TB, col = jb * TB + (e - (e / TB) * TB);
+        if (col < N) {
+          const size_t o = (size_t)row * N + col;
+          const double2 qv = Q[o], pv = P[o];
+          Q[o] = make_double2(qv.x + ha * pv.x, qv.y + ha * pv.y);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// xi of Q (Varah bound); sets S.flag = (xi > threshold).
+__device__ void wide_badness(WideSmem& S, const double2* Q, int N, double threshold) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double rowmax = 0.0, minmargin = INFINITY;
+  for (int r = warp; r < N; r += WT / 32) {
+    double sum = 0.0, dg = 0.0;
+    for (int c = lane; c < N; c += 32) {
+      const double2 v = Q[(size_t)r * N + c];
+      const double a = sqrt(v.x * v.x + v.y * v.y);
+      sum += a;
+      if (c == r) dg = a;
+    }
+    sum = wsum(sum);
+    dg = wsum(dg);
+    rowmax = fmax(rowmax, sum);
+    minmargin = fmin(minmargin, dg - (sum - dg));
+  }
+  if (lane == 0) {
+    S.red0[warp] = rowmax;
+    S.red1[warp] = minmargin;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double rm = 0.0, mm = INFINITY;
+    for (int w = 0; w < WT / 32; ++w) {
+      rm = fmax(rm, S.red0[w]);
+      mm = fmin(mm, S.red1[w]);
+    }
+    const double xi = (mm > 0.0) ? rm / mm : INFINITY;
+    S.flag = !(xi <= threshold);
+  }
+  __syncthreads();
+}
+
+// [X; Y] <- [X; Y] X^{-1} by Gauss-Jordan elimination with column operations and pivoting along
+// the rows of X (both N x N complex, row-major in global memory): X ends as the identity (up to
+// the discarded pivot columns) and Y as Y X^{-1}.
+__device__ void wide_gauss_jordan(WideSmem& S, double2* X, double2* Y, int N) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < N; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = k;
+      for (int c = k + lane; c < N; c += 32) {
+        const double2 v = X[(size_t)k * N + c];
+        const double m2 = v.x * v.x + v.y * v.y;
+        if (m2 > best) {
+          best = m2;
+          bi = c;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > best || (v2 == best && i2 < bi)) {
+          best = v2;
+          bi = i2;
+        }
+      }
+      if (lane == 0) {
+        S.piv = bi;
+        if (!(best > 0.0) || !isfinite(best)) S.status = kSingular;
+      }
+    }
+    __syncthreads();
+    if (S.status != kOk) return;
+    const int pc = S.piv;
+    if (pc != k) {
+      for (int r = tid; r < 2 * N; r += WT) {
+        double2* row = (r < N) ? X + (size_t)r * N : Y + (size_t)(r - N) * N;
+        const double2 a = row[k];
+        row[k] = row[pc];
+        row[pc] = a;
+      }
+      __syncthreads();
+    }
+    {
+      const double2 d = X[(size_t)k * N + k];
+      const double dd = d.x * d.x + d.y * d.y;
+      const double ivr = d.x / dd, ivi = -d.y / dd;
+      for (int c = tid; c < N; c += WT) {
+        const double2 v = X[(size_t)k * N + c];
+        S.fr[c] = (c == k) ? 0.0 : v.x;
+        S.fi[c] = (c == k) ? 0.0 : v.y;
+      }
+      for (int r = tid; r < 2 * N; r += WT) {
+        const double2 z = (r < N) ? X[(size_t)r * N + k] : Y[(size_t)(r - N) * N + k];
+        S.cr[r] = z.x * ivr - z.y * ivi;
+        S.ci[r] = z.x * ivi + z.y * ivr;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < 2 * N * N; e += WT) {
+      const int r = e / N, c = e - r * N;
+      double2* z = (r < N) ? X + (size_t)r * N + c : Y + (size_t)(r - N) * N + c;
+      const double cr = S.cr[r], ci = S.ci[r];
+      if (c == k) {
+        *z = make_double2(cr, ci);
+      } else {
+        const double fr = S.fr[c], fi = S.fi[c];
+        const double2 v = *z;
+        *z = make_double2(v.x - (cr * fr - ci * fi), v.y - (cr * fi + ci * fr));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void load_table(double2* tbl, const IntegrateParams& p, int set, int node) {
+  const double2* un = p.u + ((size_t)set * p.n_nodes + node) * p.M;
+  for (int m = threadIdx.x; m < p.M; m += WT) tbl[m] = __ldg(un + m);
+}
+
+__global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
+  double2* tbl = reinterpret_cast<double2*>(smem_raw + sizeof(WideSmem));
+  const IntegrateParams& p = w.p;
+  const int angle = blockIdx.x, set = blockIdx.y, tid = threadIdx.x, N = p.N;
+  const size_t pair = (size_t)set * p.ang.n_angles + angle;
+  const size_t NN = (size_t)N * N;
+  double2* Q = w.Zq + pair * NN;
+  double2* P = w.Zp + pair * NN;
+
+  if (tid == 0) {
+    S.status = kOk;
+    S.n_rhst = 0;
+  }
+  const double t0 = p.ang.theta0[angle] * (kPiW / 180.0);
+  const double phi = p.ang.phi_a1 + p.ang.theta1[angle] * (kPiW / 180.0);
+  const double bmag = p.ang.gamma * cos(t0);
+  const double b0x = bmag * cos(phi), b0y = bmag * sin(phi);
+  __syncthreads();
+  if (tid == 0) S.sin_t0 = sin(t0);
+  for (int j = tid; j < N; j += WT) {
+    const double qx = b0x + p.ang.kvec[j].x, qy = b0y + p.ang.kvec[j].y;
+    const double g2 = p.ang.gamma * p.ang.gamma - (qx * qx + qy * qy);
+    double gr = 0.0, gi = 0.0;
+    if (g2 >= 0.0) gr = sqrt(g2);
+    else gi = -sqrt(-g2);
+    if (fabs(g2) < 1e-12 * p.ang.gamma * p.ang.gamma) S.status = kGrazing;
+    S.gam2[j] = g2;
+    S.Gr[j] = gr;
+    S.Gi[j] = gi;
+  }
+  __syncthreads();
+  // initial value [I; i Gamma]
+  for (size_t e = tid; e < NN; e += WT) {
+    const int r = (int)(e / N), c = (int)(e - (size_t)r * N);
+    Q[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    P[e] = (r == c) ? make_double2(-S.Gi[r], S.Gr[r]) : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int s = p.sch.s;
+  if (S.status == kOk) {
+    for (int i = 0; i < p.L && S.status == kOk; ++i) {
+      for (int r = 0; r < s; ++r) {
+        const int n = s * i + r;
+        const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
+        load_table(tbl, p, set, n);
+        __syncthreads();
+        wide_kick(S, tbl, p.lmap, Q, P, N, p.h * coef, p.h * p.sch.a[r], true);
+      }
+      wide_badness(S, Q, N, p.threshold);
+      if (S.flag) {
+        wide_gauss_jordan(S, Q, P, N);
+        if (S.status != kOk) break;
+        for (size_t e = tid; e < NN; e += WT) {
+          const int r = (int)(e / N), c = (int)(e - (size_t)r * N);
+          Q[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+        }
+        if (tid == 0) S.n_rhst++;
+        __syncthreads();
+      }
+    }
+  }
+  if (S.status == kOk) {
+    load_table(tbl, p, set, s * p.L);
+    __syncthreads();
+    wide_kick(S, tbl, p.lmap, Q, P, N, p.h * p.sch.b[s], 0.0, false);
+    // A = Gamma Q - i P into Q's storage, B = Gamma Q + i P into P's
+    for (size_t e = tid; e < NN; e += WT) {
+      const int j = (int)(e / N);
+      const double2 q = Q[e], pp = P[e];
+      const double gqr = S.Gr[j] * q.x - S.Gi[j] * q.y, gqi = S.Gr[j] * q.y + S.Gi[j] * q.x;
+      Q[e] = make_double2(gqr + pp.y, gqi - pp.x);
+      P[e] = make_double2(gqr - pp.y, gqi + pp.x);
+    }
+    __syncthreads();
+    wide_gauss_jordan(S, Q, P, N);   // P <- B A^{-1}; rho = its first column
+  }
+  __syncthreads();
+  const double g1 = sqrt(S.gam2[0]);
+  for (int j = tid; j < N; j += WT) {
+    double2 rho = make_double2(NAN, NAN);
+    double eta = NAN;
+    if (S.status == kOk) {
+      rho = P[(size_t)j * N];
+      const double g2 = S.gam2[j];
+      eta = (g2 > 0.0) ? (rho.x * rho.x + rho.y * rho.y) * S.sin_t0 * g1 / sqrt(g2) : 0.0;
+    }
+    p.out.rho[pair * N + j] = rho;
+    p.out.eta[pair * N + j] = eta;
+  }
+  if (tid == 0) {
+    p.out.status[pair] = S.status;
+    p.out.n_rhst[pair] = S.n_rhst;
+  }
+}
+
+}  // namespace
+
+size_t integrate_fp64_wide_state_bytes(int N) { return 2 * (size_t)N * N * sizeof(double2); }
+
+cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, cudaStream_t st,
+                                       int* n_launched) {
+  const size_t smem = sizeof(WideSmem) + (size_t)p.M * sizeof(double2);
+  if (smem > 227 * 1024 || p.N > NW) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_integrate_fp64_wide,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const size_t pairs = (size_t)p.n_sets * p.ang.n_angles;
+  WideArgs w{p, state, state + pairs * (size_t)p.N * p.N};
+  k_integrate_fp64_wide<<<dim3(p.ang.n_angles, p.n_sets), WT, smem, st>>>(w);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace trh

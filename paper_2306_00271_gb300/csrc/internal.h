@@ -8,6 +8,7 @@ namespace trh {
 constexpr int kMaxStages = 12;       // kicks per step of the longest splitting scheme (SRKN_11^b)
 constexpr int kMaxBeamsFp64 = 64;    // FP64 path: state resident in shared memory up to N = 64
 constexpr int kMaxBeamsMixed = 64;   // mixed path: one 128-row UMMA tile holds [Re; Im] of N <= 64
+constexpr int kMaxBeamsWide = 256;   // FP64 path with the state in global memory (64 < N <= 256)
 
 // Status words written by kernels (mirrors the TRH_E* codes of trheed.h).
 enum DevStatus : int {
@@ -148,6 +149,11 @@ size_t mixed_image_bytes_per_node();
 void set_last_error(const char* msg);
 cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int* n_launched);
 size_t integrate_fp64_smem_bytes();
+// Wide beam sets on the FP64 path (integrate_fp64_wide.cu); `state` holds 2 N^2 complex128 per
+// (set, angle) pair (integrate_fp64_wide_state_bytes).
+cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, cudaStream_t st,
+                                       int* n_launched);
+size_t integrate_fp64_wide_state_bytes(int N);
 bool mixed_available();
 
 }  // namespace trh

@@ -1,0 +1,73 @@
+"""FP64 CUDA path for wide beam sets (64 < N <= 256, state in global memory) vs the oracle's
+Algorithm 1, through the C ABI. Same bar as the shared-memory kernel: <= 1e-10 relative per curve
+and elementwise on rho."""
+import numpy as np
+import pytest
+
+from oracle.curve import curve_error, rocking_curve
+from paper_2306_00271_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2306_00271_gb300 import api as a
+    a.load()
+    return a
+
+
+def _check(rho_g, eta_g, rho_o, eta_o):
+    assert np.all(np.isfinite(rho_g))
+    err = curve_error(eta_g, eta_o)
+    assert err <= TOL, err
+    assert np.max(np.abs(rho_g - rho_o)) <= TOL * np.max(np.abs(rho_o))
+
+
+@pytest.mark.parametrize("n_beams", [65, 91, 128, 150])
+def test_wide_ragged_beam_counts(api, n_beams):
+    wl = W.tiny(n_beams=n_beams, seed=40 + n_beams, n_steps=40, theta0=(0.8, 2.6), depth=8.0)
+    eng = api.Engine(wl, "fp64", "sp4")
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    rho_o, eta_o, _, n_o = rocking_curve(wl, "sp4")
+    _check(rho.cpu().numpy()[0], eta.cpu().numpy()[0], rho_o, eta_o)
+    st = eng.stats()
+    assert st["rhst_total"] > 0 and abs(st["rhst_total"] - int(n_o.sum())) <= 2
+
+
+def test_121_beam_shell_parameter_sets(api):
+    """The 121-beam class of the batched workload, two parameter sets in one launch."""
+    sets = [s for s in W.batch_sets(6) if s.beams.shape[0] == 121]
+    wl = sets[0].with_steps(60).with_angles([1.2, 3.4])
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_structures(np.stack([s.atoms for s in sets]))
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    for k, s in enumerate(sets):
+        rho_o, eta_o, _, _ = rocking_curve(s.with_steps(60).with_angles([1.2, 3.4]), "sp4")
+        _check(rho.cpu().numpy()[k], eta.cpu().numpy()[k], rho_o, eta_o)
+
+
+def test_255_beams_short_slab(api):
+    """The 255-beam recipe (square 5.4 A cell) at 24 slices, two angles: the largest N."""
+    wl = W.large_n255(1)[0].with_steps(24).with_angles([0.7, 4.0])
+    eng = api.Engine(wl, "fp64", "sp4")
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    rho_o, eta_o, _, _ = rocking_curve(wl, "sp4")
+    _check(rho.cpu().numpy()[0], eta.cpu().numpy()[0], rho_o, eta_o)
+
+
+def test_limits(api):
+    wl = W.tiny(n_beams=257, seed=1, n_steps=4)
+    with pytest.raises(api.TrhError) as e:
+        api.Engine(wl, "fp64", "sp4")
+    assert e.value.code == api.TRH_EUNSUPPORTED
+    wl = W.tiny(n_beams=65, seed=1, n_steps=4)
+    with pytest.raises(api.TrhError) as e:
+        api.Engine(wl, "mixed", "sp4")
+    assert e.value.code == api.TRH_EUNSUPPORTED
+    eng = api.Engine(wl, "fp64", "sp4")
+    with pytest.raises(api.TrhError) as e:
+        eng.set_fit([0], None)
+        eng.curve_jacobian(wl.theta0, wl.theta1)
+    assert e.value.code == api.TRH_EUNSUPPORTED
