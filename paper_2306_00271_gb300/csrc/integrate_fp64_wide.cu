@@ -37,8 +37,10 @@ struct WideSmem {
   double red0[WT / 32], red1[WT / 32];
   double sin_t0;
   int piv, flag, status, n_rhst;
-  // followed by the node's compact table: double2 tbl[M]
 };
+// The node's compact table double2 tbl[M] follows the struct at a 16-byte boundary (double2
+// accesses need 16-byte alignment; sizeof(WideSmem) is only a multiple of 8).
+constexpr size_t kTblOffset = (sizeof(WideSmem) + 15) & ~size_t(15);
 
 __device__ __forceinline__ void dmma_w(double (&c)[4], double a0, double a1, double b) {
   asm volatile(
@@ -269,7 +271,7 @@ __device__ void load_table(double2* tbl, const IntegrateParams& p, int set, int 
 __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
-  double2* tbl = reinterpret_cast<double2*>(smem_raw + sizeof(WideSmem));
+  double2* tbl = reinterpret_cast<double2*>(smem_raw + kTblOffset);
   const IntegrateParams& p = w.p;
   const int angle = blockIdx.x, set = blockIdx.y, tid = threadIdx.x, N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
@@ -369,7 +371,7 @@ size_t integrate_fp64_wide_state_bytes(int N) { return 2 * (size_t)N * N * sizeo
 
 cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, cudaStream_t st,
                                        int* n_launched) {
-  const size_t smem = sizeof(WideSmem) + (size_t)p.M * sizeof(double2);
+  const size_t smem = kTblOffset + (size_t)p.M * sizeof(double2);
   if (smem > 227 * 1024 || p.N > NW) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_integrate_fp64_wide,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
