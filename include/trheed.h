@@ -111,6 +111,9 @@ typedef struct trh_stats {
   double ms_integrate;    /* device time of the integration kernel of the last call              */
   double ms_gradient;     /* device time of the reverse sweep of the last trh_curve_jacobian /
                              trh_rfactor_grad call (0 after trh_rocking_curve)                   */
+  int wide_tile;          /* tile edge the autotuner chose for the wide FP64 kernel (N > 64) of
+                             the last call, 0 if that kernel did not run                         */
+  int graph_replay;       /* trh_batch_run: 1 if the work was replayed from the captured graph   */
 } trh_stats;
 
 /* Create a context for one beam set and method. Validates and copies `p` (the caller may free
@@ -194,6 +197,41 @@ int trh_curve_jacobian(trh_ctx* ctx, int n_angles, const double* theta0, const d
 int trh_rfactor_grad(trh_ctx* ctx, int n_angles, const double* theta0, const double* theta1,
                      const double* target, double* R_out, double* dR_dz, double* dR_dB,
                      void* stream);
+
+/* ---- batches ----------------------------------------------------------------------------------
+ * Many rocking curves of different beam sets (one context each, any N) and parameter sets in as
+ * few launches as possible (Section 3.4's parallelisation over angles, extended across problems):
+ * all binary64 work items (context, set, angle) with N <= 64 go to one persistent kernel and all
+ * with 64 < N <= 256 to a second one; each persistent CTA takes items from an atomic counter in
+ * decreasing-cost order (N^3 L, longest first), so uneven beam counts balance across the SMs.
+ * Contexts of precision TRH_MIXED add one launch each. The first trh_batch_run executes eagerly
+ * and captures the same launch sequence in a CUDA graph; later runs replay the graph (the
+ * potential tables of contexts whose structure changed are rebuilt before the replay, and the
+ * plan and graph are rebuilt when a context's device tables moved). The wide kernel's tile edge
+ * comes from the autotuner (trh_stats.wide_tile). */
+typedef struct trh_batch trh_batch;
+
+/* Empty batch. Errors: TRH_EINVAL (out is NULL). */
+int trh_batch_create(trh_batch** out);
+
+/* Queue all parameter sets of `ctx` at n_angles directions. theta0, theta1 ([n_angles], degrees),
+ * rho_out ([n_sets][n_angles][N] complex128) and eta_out ([n_sets][n_angles][N] float64) must be
+ * DEVICE memory; the batch keeps the pointers (not the data) and the context, which must outlive
+ * the batch. Angle values may change between runs; their count may not.
+ * Errors: TRH_EINVAL (NULL, n_angles < 1, host pointers). */
+int trh_batch_add(trh_batch* batch, trh_ctx* ctx, int n_angles, const double* theta0,
+                  const double* theta1, void* rho_out, double* eta_out);
+
+/* Run every queued job on `stream` (cudaStream_t, NULL = legacy default stream) and synchronise.
+ * Outputs and errors as trh_rocking_curve; trh_batch_query then reports the batch's counters
+ * (first_bad_set = job index and first_bad_angle = pair index within that job). */
+int trh_batch_run(trh_batch* batch, void* stream);
+
+/* Counters of the last trh_batch_run. Errors: TRH_EINVAL (NULL arguments). */
+int trh_batch_query(const trh_batch* batch, trh_stats* out);
+
+/* Free the batch (not its contexts). NULL is accepted. Synchronises the device. */
+void trh_batch_destroy(trh_batch* batch);
 
 /* Counters of the last call (see trh_stats). Errors: TRH_EINVAL (NULL arguments). */
 int trh_query(const trh_ctx* ctx, trh_stats* out);

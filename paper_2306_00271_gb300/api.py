@@ -42,7 +42,7 @@ class TrhStats(C.Structure):
         ("first_bad_set", C.c_int), ("first_bad_angle", C.c_int), ("first_bad_status", C.c_int),
         ("kernels_launched", C.c_int), ("ms_last", C.c_double),
         ("ms_potential", C.c_double), ("ms_integrate", C.c_double),
-        ("ms_gradient", C.c_double),
+        ("ms_gradient", C.c_double), ("wide_tile", C.c_int), ("graph_replay", C.c_int),
     ]
 
     def as_dict(self):
@@ -89,8 +89,15 @@ def load():
     lib.trh_set_fit.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.c_int]
     lib.trh_curve_jacobian.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     lib.trh_rfactor_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+    lib.trh_batch_create.argtypes = [C.POINTER(vp)]
+    lib.trh_batch_add.argtypes = [vp, vp, C.c_int, vp, vp, vp, vp]
+    lib.trh_batch_run.argtypes = [vp, vp]
+    lib.trh_batch_query.argtypes = [vp, C.POINTER(TrhStats)]
+    lib.trh_batch_destroy.argtypes = [vp]
+    lib.trh_batch_destroy.restype = None
     for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query", "trh_set_fit",
-              "trh_curve_jacobian", "trh_rfactor_grad"):
+              "trh_curve_jacobian", "trh_rfactor_grad", "trh_batch_create", "trh_batch_add",
+              "trh_batch_run", "trh_batch_query"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -304,6 +311,52 @@ class Engine:
         if self.ctx:
             self.lib.trh_destroy(self.ctx)
             self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Rocking curves of several engines (any beam counts) in persistent launches replayed from a
+    CUDA graph (trh_batch_*). Angles and outputs are CUDA tensors owned by the batch."""
+
+    def __init__(self):
+        self.lib = load()
+        self.h = C.c_void_p()
+        _check(self.lib.trh_batch_create(C.byref(self.h)))
+        self.jobs = []
+
+    def add(self, engine: "Engine", theta0, theta1=None):
+        """Queue all parameter sets of ``engine`` at the given angles; returns (rho, eta) CUDA
+        tensors (n_sets, A, N) that every run() overwrites."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t0, t1 = engine._angles(theta0, theta1, dev)
+        A = t0.numel()
+        rho = torch.empty((engine.n_sets, A, engine.N), dtype=torch.complex128, device=dev)
+        eta = torch.empty((engine.n_sets, A, engine.N), dtype=torch.float64, device=dev)
+        _check(self.lib.trh_batch_add(self.h, engine.ctx, A, _ptr(t0), _ptr(t1), _ptr(rho),
+                                      _ptr(eta)))
+        self.jobs.append((engine, t0, t1, rho, eta))
+        return rho, eta
+
+    def run(self, stream=None):
+        import torch
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(self.lib.trh_batch_run(self.h, C.c_void_p(st)))
+
+    def stats(self) -> dict:
+        s = TrhStats()
+        _check(self.lib.trh_batch_query(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            self.lib.trh_batch_destroy(self.h)
+            self.h = C.c_void_p()
 
     def __del__(self):
         try:

@@ -5,12 +5,14 @@
 #include "trheed.h"
 #include "internal.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -128,6 +130,7 @@ struct trh_ctx {
   int n_sets = 0;
   std::vector<double> atoms, dw;  // [n_sets][n_atoms][3], [n_sets][n_atoms]
   bool tables_dirty = true;
+  unsigned long long generation = 0;  // bumped whenever device tables may move (batch plans)
   // device
   DevBuf<double2> d_kvec, d_g, d_u, d_F, d_rho;
   DevBuf<double> d_atoms, d_dw, d_sf, d_nodes, d_theta, d_eta;
@@ -174,6 +177,7 @@ static int upload_sets(trh_ctx* c) {
   TRH_CUDA(c->d_u.ensure((size_t)c->n_sets * c->n_nodes * c->M));
   TRH_CUDA(c->d_F.ensure((size_t)c->n_sets * c->M * 4 * c->n_atoms));
   c->tables_dirty = true;
+  c->generation++;
   return TRH_OK;
 }
 
@@ -351,6 +355,7 @@ int trh_set_structure(trh_ctx* c, int n_sets, const double* atoms, const double*
     TRH_CUDA(c->d_u.ensure((size_t)n_sets * c->n_nodes * c->M));
     TRH_CUDA(c->d_F.ensure((size_t)n_sets * c->M * 4 * c->n_atoms));
     c->tables_dirty = true;
+    c->generation++;
     return TRH_OK;
   }
   for (size_t a = 0; a < na; ++a) {
@@ -456,6 +461,33 @@ static trh::IntegrateParams integrate_params(trh_ctx* c, int n_angles, size_t pa
   return ip;
 }
 
+static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParams& ip) {
+  trh::MixedParams mp{};
+  mp.sch = ip.sch;
+  mp.ang = ip.ang;
+  mp.out = ip.out;
+  mp.img = c->d_img.p;
+  mp.N = c->N;
+  mp.n_nodes = c->n_nodes;
+  mp.n_sets = c->n_sets;
+  mp.L = c->L;
+  mp.n_mma = (c->N + 15) / 16 * 16;
+  mp.k_slices = (2 * c->N + 15) / 16;
+  mp.h = c->h;
+  mp.threshold = c->threshold;
+  const int sc = c->scheme.s;
+  auto split = [](double v, float* hi, float* lo) {
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
+  };
+  split(c->h * c->scheme.b[0], &mp.kick_hi[0], &mp.kick_lo[0]);
+  for (int r = 1; r < sc; ++r) split(c->h * c->scheme.b[r], &mp.kick_hi[r], &mp.kick_lo[r]);
+  split(c->h * (c->scheme.b[sc] + c->scheme.b[0]), &mp.kick_hi[sc], &mp.kick_lo[sc]);
+  split(c->h * c->scheme.b[sc], &mp.kick_hi[sc + 1], &mp.kick_lo[sc + 1]);
+  for (int r = 0; r < sc; ++r) split(c->h * c->scheme.a[r], &mp.drift_hi[r], &mp.drift_lo[r]);
+  return mp;
+}
+
 // Reads back the per-pair status words (the stream is synchronised) and fills the counters.
 static int collect_status(trh_ctx* c, int n_angles, size_t pairs, cudaStream_t st) {
   c->h_status.resize(2 * pairs);
@@ -496,6 +528,48 @@ static float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
   return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.f;
 }
 
+// Autotuner for the wide FP64 kernel's tile edge (64 or 32): times each candidate on a probe
+// (first angle of the first set, 2 steps, outputs later overwritten by the real run) after one
+// warm-up launch, and keeps the fastest per beam count for the life of the process. Padding
+// decides most of it: N = 65 pads to 128 with 64-tiles but to 96 with 32-tiles, while N = 255
+// pads to 256 either way and the larger tile has less overhead.
+static std::mutex g_tune_mu;
+static std::map<int, int> g_wide_tile;
+
+static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* state,
+                          cudaStream_t st, int* tile) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_wide_tile.find(c->N);
+    if (it != g_wide_tile.end()) {
+      *tile = it->second;
+      return TRH_OK;
+    }
+  }
+  trh::IntegrateParams pp = ip;
+  pp.L = ip.L < 2 ? ip.L : 2;
+  pp.ang.n_angles = 1;
+  pp.n_sets = 1;
+  float best = 3.0e38f;
+  int best_tile = 64;
+  for (int cand : {64, 32}) {
+    TRH_CUDA(trh::launch_integrate_fp64_wide(pp, state, cand, st, nullptr));
+    TRH_CUDA(cudaEventRecord(c->ev[4], st));
+    TRH_CUDA(trh::launch_integrate_fp64_wide(pp, state, cand, st, nullptr));
+    TRH_CUDA(cudaEventRecord(c->ev[5], st));
+    TRH_CUDA(cudaEventSynchronize(c->ev[5]));
+    const float ms = elapsed_ms(c->ev[4], c->ev[5]);
+    if (ms < best) {
+      best = ms;
+      best_tile = cand;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_wide_tile[c->N] = best_tile;
+  *tile = best_tile;
+  return TRH_OK;
+}
+
 int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
                       void* rho_out, double* eta_out, void* stream) {
   const auto t_start = std::chrono::steady_clock::now();
@@ -521,37 +595,20 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   }
   TRH_CUDA(c->d_status.ensure(2 * pairs));
   trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, rho, eta);
+  int tile = 0;
+  if (c->precision == TRH_FP64 && c->N > trh::kMaxBeamsFp64) {
+    TRH_CUDA(c->d_wide.ensure(pairs * trh::integrate_fp64_wide_state_bytes(c->N) / sizeof(double2)));
+    rc = tune_wide_tile(c, ip, c->d_wide.p, st, &tile);
+    if (rc != TRH_OK) return rc;
+  }
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
-    trh::MixedParams mp{};
-    mp.sch = ip.sch;
-    mp.ang = ip.ang;
-    mp.out = ip.out;
-    mp.img = c->d_img.p;
-    mp.N = c->N;
-    mp.n_nodes = c->n_nodes;
-    mp.n_sets = c->n_sets;
-    mp.L = c->L;
-    mp.n_mma = (c->N + 15) / 16 * 16;
-    mp.k_slices = (2 * c->N + 15) / 16;
-    mp.h = c->h;
-    mp.threshold = c->threshold;
-    const int sc = c->scheme.s;
-    auto split = [](double v, float* hi, float* lo) {
-      *hi = (float)v;
-      *lo = (float)(v - (double)*hi);
-    };
-    split(c->h * c->scheme.b[0], &mp.kick_hi[0], &mp.kick_lo[0]);
-    for (int r = 1; r < sc; ++r) split(c->h * c->scheme.b[r], &mp.kick_hi[r], &mp.kick_lo[r]);
-    split(c->h * (c->scheme.b[sc] + c->scheme.b[0]), &mp.kick_hi[sc], &mp.kick_lo[sc]);
-    split(c->h * c->scheme.b[sc], &mp.kick_hi[sc + 1], &mp.kick_lo[sc + 1]);
-    for (int r = 0; r < sc; ++r) split(c->h * c->scheme.a[r], &mp.drift_hi[r], &mp.drift_lo[r]);
+    trh::MixedParams mp = mixed_params(c, ip);
     TRH_CUDA(trh::launch_integrate_mixed(mp, st, &launched));
   } else if (c->N <= trh::kMaxBeamsFp64) {
     TRH_CUDA(trh::launch_integrate_fp64(ip, st, &launched));
   } else {
-    TRH_CUDA(c->d_wide.ensure(pairs * trh::integrate_fp64_wide_state_bytes(c->N) / sizeof(double2)));
-    TRH_CUDA(trh::launch_integrate_fp64_wide(ip, c->d_wide.p, st, &launched));
+    TRH_CUDA(trh::launch_integrate_fp64_wide(ip, c->d_wide.p, tile, st, &launched));
   }
   TRH_CUDA(cudaEventRecord(c->ev[3], st));
   if (rho_out && !dev_rho)
@@ -567,6 +624,7 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   S.ms_potential = rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
   S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
   S.ms_gradient = 0.0;
+  S.wide_tile = tile;
   S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
                   .count();
   if (S.n_bad) return bad_pairs_error(c);
@@ -718,6 +776,7 @@ static int finish_gradient_call(trh_ctx* c, int n_angles, int launched, bool reb
   S.ms_potential = rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
   S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
   S.ms_gradient = elapsed_ms(c->ev[3], c->ev[5]);
+  S.wide_tile = 0;
   S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
                   .count();
   if (S.n_bad) return bad_pairs_error(c);
@@ -854,6 +913,265 @@ void trh_destroy(trh_ctx* c) {
   c->d_gz.release();
   c->d_gb.release();
   delete c;
+}
+
+// ---- batches: many contexts (beam sets of any N) in persistent launches, replayed as a graph ----
+
+struct trh_batch {
+  struct Job {
+    trh_ctx* c;
+    int n_angles;
+    const double* theta0;
+    const double* theta1;
+    double2* rho;
+    double* eta;
+    unsigned long long generation;
+  };
+  std::vector<Job> jobs;
+  bool prepared = false;
+  std::vector<size_t> offset;            // first pair of each job in the status array
+  size_t total_pairs = 0;
+  int n_small = 0, n_wide = 0, wide_tile = 0, wide_ctas = 0, small_ctas = 0, max_m_wide = 0;
+  size_t slot_elems = 0;
+  std::vector<trh::IntegrateParams> params;
+  DevBuf<trh::IntegrateParams> d_params;
+  DevBuf<int4> d_items;                  // small items, then wide items
+  DevBuf<int> d_status, d_counter;
+  DevBuf<double2> d_state;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<int> h_status;
+  trh_stats stats{};
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+};
+
+int trh_batch_create(trh_batch** out) {
+  if (!out) return fail(TRH_EINVAL, "out is NULL");
+  *out = new trh_batch();
+  return TRH_OK;
+}
+
+int trh_batch_add(trh_batch* b, trh_ctx* c, int n_angles, const double* theta0,
+                  const double* theta1, void* rho_out, double* eta_out) {
+  if (!b || !c || n_angles < 1) return fail(TRH_EINVAL, "bad arguments");
+  if (!is_device_ptr(theta0) || !is_device_ptr(theta1) || !is_device_ptr(rho_out) ||
+      !is_device_ptr(eta_out))
+    return fail(TRH_EINVAL, "batch angles and outputs must be device memory");
+  b->jobs.push_back({c, n_angles, theta0, theta1, (double2*)rho_out, eta_out, 0});
+  b->prepared = false;
+  b->drop_graph();
+  return TRH_OK;
+}
+
+// Work lists, job parameters and scratch for the current jobs and tables.
+static int batch_prepare(trh_batch* b, cudaStream_t st) {
+  b->drop_graph();
+  b->offset.clear();
+  b->params.clear();
+  b->total_pairs = 0;
+  struct Item {
+    double cost;
+    int4 w;
+    bool wide;
+  };
+  std::vector<Item> items;
+  int max_n_wide = 0;
+  trh_ctx* tune_ctx = nullptr;
+  b->max_m_wide = 0;
+  for (size_t j = 0; j < b->jobs.size(); ++j) {
+    trh_batch::Job& J = b->jobs[j];
+    trh_ctx* c = J.c;
+    const size_t pairs = (size_t)c->n_sets * J.n_angles;
+    b->offset.push_back(b->total_pairs);
+    trh::IntegrateParams ip = integrate_params(c, J.n_angles, pairs, J.rho, J.eta);
+    ip.ang.theta0 = J.theta0;
+    ip.ang.theta1 = J.theta1;
+    b->params.push_back(ip);
+    J.generation = c->generation;
+    b->total_pairs += pairs;
+    if (c->precision == TRH_MIXED) continue;
+    const bool wide = c->N > trh::kMaxBeamsFp64;
+    const double cost = (double)c->N * c->N * c->N * c->L * c->scheme.s;
+    for (int set = 0; set < c->n_sets; ++set)
+      for (int a = 0; a < J.n_angles; ++a)
+        items.push_back({cost, make_int4((int)j, set, a, 0), wide});
+    if (wide) {
+      if (c->N > max_n_wide) {
+        max_n_wide = c->N;
+        tune_ctx = c;
+      }
+      if (c->M > b->max_m_wide) b->max_m_wide = c->M;
+    }
+  }
+  // statuses of job j live at offset[j] (and n_rhst at total_pairs + offset[j])
+  TRH_CUDA(b->d_status.ensure(2 * b->total_pairs));
+  for (size_t j = 0; j < b->jobs.size(); ++j) {
+    b->params[j].out.status = b->d_status.p + b->offset[j];
+    b->params[j].out.n_rhst = b->d_status.p + b->total_pairs + b->offset[j];
+  }
+  // longest-processing-time first within each kernel family
+  std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
+    if (x.wide != y.wide) return !x.wide;
+    return x.cost > y.cost;
+  });
+  std::vector<int4> w;
+  b->n_small = b->n_wide = 0;
+  for (const Item& it : items) {
+    w.push_back(it.w);
+    (it.wide ? b->n_wide : b->n_small)++;
+  }
+  int dev = 0, n_sm = 0;
+  TRH_CUDA(cudaGetDevice(&dev));
+  TRH_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  b->small_ctas = std::min(b->n_small, n_sm);
+  b->wide_ctas = std::min(b->n_wide, n_sm);
+  TRH_CUDA(b->d_params.ensure(b->params.size()));
+  TRH_CUDA(cudaMemcpy(b->d_params.p, b->params.data(),
+                      b->params.size() * sizeof(trh::IntegrateParams), cudaMemcpyHostToDevice));
+  TRH_CUDA(b->d_items.ensure(w.size() > 0 ? w.size() : 1));
+  if (!w.empty())
+    TRH_CUDA(cudaMemcpy(b->d_items.p, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  TRH_CUDA(b->d_counter.ensure(2));
+  b->wide_tile = 0;
+  if (b->n_wide > 0) {
+    b->slot_elems = 2 * (size_t)max_n_wide * max_n_wide;
+    TRH_CUDA(b->d_state.ensure(b->wide_ctas * b->slot_elems));
+    // the tuner probes the largest wide job with its own parameters and scratch
+    for (size_t j = 0; j < b->jobs.size(); ++j)
+      if (b->jobs[j].c == tune_ctx) {
+        int rc = tune_wide_tile(tune_ctx, b->params[j], b->d_state.p, st, &b->wide_tile);
+        if (rc != TRH_OK) return rc;
+        break;
+      }
+  }
+  if (!b->ev[0])
+    for (int i = 0; i < 2; ++i) TRH_CUDA(cudaEventCreate(&b->ev[i]));
+  b->prepared = true;
+  return TRH_OK;
+}
+
+// The batch's device work: counters reset, the persistent FP64 launches, one launch per
+// mixed-precision job.
+static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
+  TRH_CUDA(cudaMemsetAsync(b->d_counter.p, 0, 2 * sizeof(int), st));
+  if (b->n_small > 0)
+    TRH_CUDA(trh::launch_integrate_fp64_items(b->d_params.p, b->d_items.p, b->n_small,
+                                              b->d_counter.p, b->small_ctas, st, launched));
+  if (b->n_wide > 0)
+    TRH_CUDA(trh::launch_integrate_fp64_wide_items(
+        b->d_params.p, b->d_items.p + b->n_small, b->n_wide, b->d_counter.p + 1, b->d_state.p,
+        b->slot_elems, b->max_m_wide, b->wide_tile, b->wide_ctas, st, launched));
+  for (size_t j = 0; j < b->jobs.size(); ++j) {
+    trh_ctx* c = b->jobs[j].c;
+    if (c->precision != TRH_MIXED) continue;
+    trh::MixedParams mp = mixed_params(c, b->params[j]);
+    TRH_CUDA(trh::launch_integrate_mixed(mp, st, launched));
+  }
+  return TRH_OK;
+}
+
+int trh_batch_run(trh_batch* b, void* stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!b || b->jobs.empty()) return fail(TRH_EINVAL, "empty batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  int launched = 0;
+  bool stale = !b->prepared;
+  for (auto& J : b->jobs) {
+    if (!J.c->ev[0])
+      for (int i = 0; i < 6; ++i) TRH_CUDA(cudaEventCreate(&J.c->ev[i]));
+    bool rebuilt = false;
+    int rc = build_tables(J.c, st, &launched, &rebuilt);
+    if (rc != TRH_OK) return rc;
+    if (J.c->generation != J.generation) stale = true;
+  }
+  if (stale) {
+    int rc = batch_prepare(b, st);
+    if (rc != TRH_OK) return rc;
+  }
+  TRH_CUDA(cudaEventRecord(b->ev[0], st));
+  bool replayed = false;
+  if (b->exec) {
+    TRH_CUDA(cudaGraphLaunch(b->exec, st));
+    replayed = true;
+  } else {
+    // eager run (sets every kernel attribute), then capture the same sequence for next time
+    int rc = batch_launch(b, st, &launched);
+    if (rc != TRH_OK) return rc;
+    int ignored = 0;
+    TRH_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    rc = batch_launch(b, st, &ignored);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (rc != TRH_OK) return rc;
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    b->graph = g;
+    TRH_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  }
+  TRH_CUDA(cudaEventRecord(b->ev[1], st));
+  b->h_status.resize(2 * b->total_pairs);
+  TRH_CUDA(cudaMemcpyAsync(b->h_status.data(), b->d_status.p, 2 * b->total_pairs * sizeof(int),
+                           cudaMemcpyDeviceToHost, st));
+  TRH_CUDA(cudaStreamSynchronize(st));
+  trh_stats& S = b->stats;
+  S = trh_stats{};
+  S.first_bad_set = S.first_bad_angle = -1;
+  for (size_t j = 0; j < b->jobs.size(); ++j) {
+    const size_t pairs = (size_t)b->jobs[j].c->n_sets * b->jobs[j].n_angles;
+    S.n_sets += b->jobs[j].c->n_sets;
+    S.n_angles += b->jobs[j].n_angles;
+    for (size_t q = 0; q < pairs; ++q) {
+      const int stq = b->h_status[b->offset[j] + q];
+      const int nr = b->h_status[b->total_pairs + b->offset[j] + q];
+      S.rhst_total += nr;
+      if (nr > S.rhst_max) S.rhst_max = nr;
+      if (stq != 0) {
+        if (S.n_bad == 0) {
+          S.first_bad_set = (int)j;   // for a batch: the job index
+          S.first_bad_angle = (int)q;  // and the pair index within the job
+          S.first_bad_status = stq;
+        }
+        S.n_bad++;
+      }
+    }
+  }
+  int n_mixed = 0;
+  for (const auto& J : b->jobs) n_mixed += (J.c->precision == TRH_MIXED);
+  S.kernels_launched = replayed ? (b->n_small > 0) + (b->n_wide > 0) + n_mixed : launched;
+  S.ms_integrate = elapsed_ms(b->ev[0], b->ev[1]);
+  S.wide_tile = b->wide_tile;
+  S.graph_replay = replayed ? 1 : 0;
+  S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
+                  .count();
+  if (S.n_bad)
+    return fail(S.first_bad_status, "%d pairs of the batch failed; first: job %d pair %d (%s)",
+                S.n_bad, S.first_bad_set, S.first_bad_angle, trh_strerror(S.first_bad_status));
+  return TRH_OK;
+}
+
+int trh_batch_query(const trh_batch* b, trh_stats* out) {
+  if (!b || !out) return fail(TRH_EINVAL, "bad arguments");
+  *out = b->stats;
+  return TRH_OK;
+}
+
+void trh_batch_destroy(trh_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  b->drop_graph();
+  for (int i = 0; i < 2; ++i)
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  b->d_params.release();
+  b->d_items.release();
+  b->d_status.release();
+  b->d_counter.release();
+  b->d_state.release();
+  delete b;
 }
 
 }  // extern "C"

@@ -65,10 +65,8 @@ __device__ __forceinline__ void write_checkpoint(const Smem& S, const IntegrateP
   store_mat(dst + nn, S.Pr, S.Pi, p.N);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_integrate_fp64(IntegrateParams p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-  const int angle = blockIdx.x, set = blockIdx.y;
+// Integrates one (set, angle) pair of `p` and writes rho, eta, status and the RHST count.
+__device__ void integrate_pair(Smem& S, const IntegrateParams& p, int angle, int set) {
   const int tid = threadIdx.x;
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
@@ -114,6 +112,35 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_fp64(IntegrateParams p) {
     p.out.status[pair] = S.status;
     p.out.n_rhst[pair] = S.n_rhst;
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT, 1) k_integrate_fp64(IntegrateParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  integrate_pair(S, p, blockIdx.x, blockIdx.y);
+}
+
+// Persistent form for batches: each CTA takes work items (job, set, angle) in list order from an
+// atomic counter until the list is exhausted; the list is sorted by decreasing cost, so the
+// longest jobs start first and the tail is short (longest-processing-time-first).
+__global__ void __launch_bounds__(NT, 1) k_integrate_fp64_items(const IntegrateParams* jobs,
+                                                                const int4* items, int n_items,
+                                                                int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  __shared__ int next;
+  __shared__ IntegrateParams job;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = next;
+    if (it >= n_items) break;
+    const int4 w = items[it];
+    if (threadIdx.x == 0) job = jobs[w.x];
+    __syncthreads();
+    integrate_pair(S, job, w.z, w.y);   // ends with a barrier: `next` and `job` are free again
+  }
 }
 
 }  // namespace
@@ -127,6 +154,18 @@ cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int
   if (e != cudaSuccess) return e;
   dim3 grid(p.ang.n_angles, p.n_sets);
   k_integrate_fp64<<<grid, NT, smem, st>>>(p);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_fp64_items(const IntegrateParams* jobs, const int4* items,
+                                        int n_items, int* counter, int n_ctas, cudaStream_t st,
+                                        int* n_launched) {
+  const size_t smem = sizeof(Smem);
+  cudaError_t e = cudaFuncSetAttribute(k_integrate_fp64_items,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_integrate_fp64_items<<<n_ctas, NT, smem, st>>>(jobs, items, n_items, counter);
   if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }

@@ -22,15 +22,23 @@ namespace trh {
 
 namespace {
 
-constexpr int TB = 64;               // tile edge
-constexpr int TLD = TB + 4;          // tile row stride (doubles)
 constexpr int NW = kMaxBeamsWide;    // largest N
 constexpr int WT = 256;              // threads
 constexpr double kPiW = 3.14159265358979323846;
 
+// Tile edge TB (64 or 32; chosen per beam count by the autotuner in api.cpp): 8 warps in an
+// MW x (8 / MW) grid, MW = TB / 16, each warp owning 16 rows and S groups of 8 columns.
+template <int TB>
+struct Tile {
+  static constexpr int LD = TB + 4;           // row stride (doubles)
+  static constexpr int MW = TB / 16;          // warp rows
+  static constexpr int NWC = 8 / MW;          // warp columns
+  static constexpr int S = TB / (8 * NWC);    // 8-column fragments per warp
+};
+
 struct WideSmem {
-  double Ar[TB * TLD], Ai[TB * TLD];   // U tile
-  double Br[TB * TLD], Bi[TB * TLD];   // Q tile
+  double Ar[64 * 68], Ai[64 * 68];     // U tile (the TB = 32 tiling uses the first 32 x 36)
+  double Br[64 * 68], Bi[64 * 68];     // Q tile
   double gam2[NW], Gr[NW], Gi[NW];
   double cr[2 * NW], ci[2 * NW];       // scaled pivot column
   double fr[NW], fi[NW];               // pivot row
@@ -56,19 +64,21 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// acc += A_tile B_tile (64 x 64 complex tiles in shared memory); 8 warps in a 4 x 2 grid of
-// 16 x 32 output tiles; fixed accumulation order.
-__device__ __forceinline__ void tile_gemm(const WideSmem& S, double (&wr)[4][4], double (&wi)[4][4]) {
+// acc += A_tile B_tile (TB x TB complex tiles in shared memory); fixed accumulation order.
+template <int TB>
+__device__ __forceinline__ void tile_gemm(const WideSmem& S, double (&wr)[Tile<TB>::S][4],
+                                          double (&wi)[Tile<TB>::S][4]) {
+  using T = Tile<TB>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int mt = warp & 3, nt = warp >> 2;
+  const int mt = warp % T::MW, nt = warp / T::MW;
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll 4
   for (int k0 = 0; k0 < TB; k0 += 4) {
-    const int a0 = (16 * mt + g) * TLD + k0 + t, a1 = a0 + 8 * TLD;
+    const int a0 = (16 * mt + g) * T::LD + k0 + t, a1 = a0 + 8 * T::LD;
     const double ar0 = S.Ar[a0], ar1 = S.Ar[a1], ai0 = S.Ai[a0], ai1 = S.Ai[a1];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int cb = (k0 + t) * TLD + 32 * nt + 8 * s + g;
+    for (int s = 0; s < T::S; ++s) {
+      const int cb = (k0 + t) * T::LD + 8 * T::S * nt + 8 * s + g;
       const double br = S.Br[cb], bi = S.Bi[cb];
       dmma_w(wr[s], ar0, ar1, br);
       dmma_w(wr[s], -ai0, -ai1, bi);
@@ -86,15 +96,18 @@ struct WideArgs {
 
 // One kick with coefficient hb and (if do_drift) the drift with ha, for the table in shared
 // memory.
+template <int TB>
 __device__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, double2* Q, double2* P,
                           int N, double hb, double ha, bool do_drift) {
+  using T = Tile<TB>;
+  constexpr int TLD = T::LD;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = (N + TB - 1) / TB;
   for (int jb = 0; jb < nb; ++jb) {
     for (int ib = 0; ib < nb; ++ib) {
-      double wr[4][4], wi[4][4];
+      double wr[T::S][4], wi[T::S][4];
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+      for (int s = 0; s < T::S; ++s)
 #pragma unroll
         for (int q = 0; q < 4; ++q) wr[s][q] = wi[s][q] = 0.0;
       for (int kb = 0; kb < nb; ++kb) {
@@ -120,16 +133,16 @@ __device__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, doub
           S.Bi[r * TLD + k] = bi;
         }
         __syncthreads();
-        tile_gemm(S, wr, wi);
+        tile_gemm<TB>(S, wr, wi);
         __syncthreads();
       }
-      const int mt = warp & 3, nt = warp >> 2, g = lane >> 2, t = lane & 3;
+      const int mt = warp % T::MW, nt = warp / T::MW, g = lane >> 2, t = lane & 3;
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+      for (int s = 0; s < T::S; ++s)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int row = ib * TB + 16 * mt + g + 8 * (q >> 1);
-          const int col = jb * TB + 32 * nt + 8 * s + 2 * t + (q & 1);
+          const int col = jb * TB + 8 * T::S * nt + 8 * s + 2 * t + (q & 1);
           if (row < N && col < N) {
             const size_t o = (size_t)row * N + col;
             const double2 qv = Q[o], pv = P[o];
@@ -268,16 +281,13 @@ __device__ void load_table(double2* tbl, const IntegrateParams& p, int set, int 
   for (int m = threadIdx.x; m < p.M; m += WT) tbl[m] = __ldg(un + m);
 }
 
-__global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
-  double2* tbl = reinterpret_cast<double2*>(smem_raw + kTblOffset);
-  const IntegrateParams& p = w.p;
-  const int angle = blockIdx.x, set = blockIdx.y, tid = threadIdx.x, N = p.N;
+// Integrates one (set, angle) pair of `p` with its state at Q, P (N x N each).
+template <int TB>
+__device__ void wide_pair(WideSmem& S, double2* tbl, const IntegrateParams& p, int angle, int set,
+                          double2* Q, double2* P) {
+  const int tid = threadIdx.x, N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   const size_t NN = (size_t)N * N;
-  double2* Q = w.Zq + pair * NN;
-  double2* P = w.Zp + pair * NN;
 
   if (tid == 0) {
     S.status = kOk;
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
         const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
         load_table(tbl, p, set, n);
         __syncthreads();
-        wide_kick(S, tbl, p.lmap, Q, P, N, p.h * coef, p.h * p.sch.a[r], true);
+        wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * coef, p.h * p.sch.a[r], true);
       }
       wide_badness(S, Q, N, p.threshold);
       if (S.flag) {
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
   if (S.status == kOk) {
     load_table(tbl, p, set, s * p.L);
     __syncthreads();
-    wide_kick(S, tbl, p.lmap, Q, P, N, p.h * p.sch.b[s], 0.0, false);
+    wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * p.sch.b[s], 0.0, false);
     // A = Gamma Q - i P into Q's storage, B = Gamma Q + i P into P's
     for (size_t e = tid; e < NN; e += WT) {
       const int j = (int)(e / N);
@@ -363,22 +373,82 @@ __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
     p.out.status[pair] = S.status;
     p.out.n_rhst[pair] = S.n_rhst;
   }
+  __syncthreads();
+}
+
+template <int TB>
+__global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
+  double2* tbl = reinterpret_cast<double2*>(smem_raw + kTblOffset);
+  const size_t NN = (size_t)w.p.N * w.p.N;
+  const size_t pair = (size_t)blockIdx.y * w.p.ang.n_angles + blockIdx.x;
+  wide_pair<TB>(S, tbl, w.p, blockIdx.x, blockIdx.y, w.Zq + pair * NN, w.Zp + pair * NN);
+}
+
+// Persistent form for batches (see k_integrate_fp64_items): work items (job, set, angle, -) in
+// decreasing-cost order; each CTA keeps its current item's state in its own slot of `state`
+// (slot_elems = 2 N_max^2 complex128 per CTA).
+template <int TB>
+__global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide_items(
+    const IntegrateParams* jobs, const int4* items, int n_items, int* counter, double2* state,
+    size_t slot_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
+  double2* tbl = reinterpret_cast<double2*>(smem_raw + kTblOffset);
+  __shared__ int next;
+  __shared__ IntegrateParams job;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = next;
+    if (it >= n_items) break;
+    const int4 w = items[it];
+    if (threadIdx.x == 0) job = jobs[w.x];
+    __syncthreads();
+    double2* Q = state + (size_t)blockIdx.x * slot_elems;
+    wide_pair<TB>(S, tbl, job, w.z, w.y, Q, Q + (size_t)job.N * job.N);
+  }
 }
 
 }  // namespace
 
 size_t integrate_fp64_wide_state_bytes(int N) { return 2 * (size_t)N * N * sizeof(double2); }
 
-cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, cudaStream_t st,
-                                       int* n_launched) {
+cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, int tile,
+                                       cudaStream_t st, int* n_launched) {
   const size_t smem = kTblOffset + (size_t)p.M * sizeof(double2);
-  if (smem > 227 * 1024 || p.N > NW) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_integrate_fp64_wide,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 227 * 1024 || p.N > NW || (tile != 32 && tile != 64)) return cudaErrorInvalidValue;
+  const void* fn = tile == 64 ? (const void*)k_integrate_fp64_wide<64>
+                              : (const void*)k_integrate_fp64_wide<32>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const size_t pairs = (size_t)p.n_sets * p.ang.n_angles;
   WideArgs w{p, state, state + pairs * (size_t)p.N * p.N};
-  k_integrate_fp64_wide<<<dim3(p.ang.n_angles, p.n_sets), WT, smem, st>>>(w);
+  const dim3 grid(p.ang.n_angles, p.n_sets);
+  if (tile == 64) k_integrate_fp64_wide<64><<<grid, WT, smem, st>>>(w);
+  else k_integrate_fp64_wide<32><<<grid, WT, smem, st>>>(w);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_fp64_wide_items(const IntegrateParams* jobs, const int4* items,
+                                             int n_items, int* counter, double2* state,
+                                             size_t slot_elems, int max_m, int tile, int n_ctas,
+                                             cudaStream_t st, int* n_launched) {
+  const size_t smem = kTblOffset + (size_t)max_m * sizeof(double2);
+  if (smem > 227 * 1024 - sizeof(IntegrateParams) - 16 || (tile != 32 && tile != 64))
+    return cudaErrorInvalidValue;
+  const void* fn = tile == 64 ? (const void*)k_integrate_fp64_wide_items<64>
+                              : (const void*)k_integrate_fp64_wide_items<32>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (tile == 64)
+    k_integrate_fp64_wide_items<64><<<n_ctas, WT, smem, st>>>(jobs, items, n_items, counter,
+                                                               state, slot_elems);
+  else
+    k_integrate_fp64_wide_items<32><<<n_ctas, WT, smem, st>>>(jobs, items, n_items, counter,
+                                                               state, slot_elems);
   if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }

@@ -151,8 +151,17 @@ cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int
 size_t integrate_fp64_smem_bytes();
 // Wide beam sets on the FP64 path (integrate_fp64_wide.cu); `state` holds 2 N^2 complex128 per
 // (set, angle) pair (integrate_fp64_wide_state_bytes).
-cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, cudaStream_t st,
-                                       int* n_launched);
+cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, int tile,
+                                       cudaStream_t st, int* n_launched);
+// Persistent batch kernels: items (job, set, angle, -) sorted by decreasing cost; `counter` must
+// be zero at launch. The wide form needs 2 N_max^2 complex128 of state per CTA.
+cudaError_t launch_integrate_fp64_items(const IntegrateParams* jobs, const int4* items,
+                                        int n_items, int* counter, int n_ctas, cudaStream_t st,
+                                        int* n_launched);
+cudaError_t launch_integrate_fp64_wide_items(const IntegrateParams* jobs, const int4* items,
+                                             int n_items, int* counter, double2* state,
+                                             size_t slot_elems, int max_m, int tile, int n_ctas,
+                                             cudaStream_t st, int* n_launched);
 size_t integrate_fp64_wide_state_bytes(int N);
 bool mixed_available();
 

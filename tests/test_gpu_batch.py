@@ -1,0 +1,106 @@
+"""Batches of beam sets with uneven N in persistent launches replayed from a CUDA graph.
+
+Every item of a batch runs the same per-pair code as the standalone call, so batch outputs must
+equal the standalone outputs bit for bit (the standalone paths are checked against the oracle in
+test_gpu_fp64.py, test_gpu_wide.py and test_gpu_mixed.py); one job is also checked against the
+oracle directly."""
+import numpy as np
+import pytest
+
+from oracle.curve import curve_error, rocking_curve
+from paper_2306_00271_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2306_00271_gb300 import api as a
+    a.load()
+    return a
+
+
+def _jobs():
+    sets = W.batch_sets(6)          # beam classes 31, 61, 121 round robin
+    out = []
+    for k, angles in ((0, [0.6, 1.7, 3.9]), (1, [1.1, 4.4]), (2, [0.9, 2.2])):
+        wl = sets[k].with_steps(48).with_angles(angles)
+        atoms = np.stack([sets[k].atoms, sets[k + 3].atoms])
+        out.append((wl, atoms, "fp64"))
+    wl = W.tiny(n_beams=37, seed=9, n_steps=48, theta0=(1.3, 2.8), depth=8.0)
+    out.append((wl, wl.atoms[None], "mixed"))
+    return out
+
+
+def _standalone(api, wl, atoms, path):
+    eng = api.Engine(wl, path, "sp4")
+    eng.set_structures(atoms)
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    return rho.cpu().numpy(), eta.cpu().numpy()
+
+
+def test_batch_equals_standalone_and_replays(api):
+    import torch
+    jobs = _jobs()
+    engines, outs = [], []
+    batch = api.Batch()
+    for wl, atoms, path in jobs:
+        eng = api.Engine(wl, path, "sp4")
+        eng.set_structures(atoms)
+        engines.append(eng)
+        outs.append(batch.add(eng, wl.theta0, wl.theta1))
+    batch.run()
+    st = batch.stats()
+    assert st["graph_replay"] == 0 and st["n_bad"] == 0
+    assert st["wide_tile"] in (32, 64)
+    assert st["kernels_launched"] <= 2 + 1 + 6 * len(jobs)   # tables + 2 persistent + mixed
+    ref = [_standalone(api, wl, atoms, path) for wl, atoms, path in jobs]
+    for (rho, eta), (rho_s, eta_s) in zip(outs, ref):
+        assert np.array_equal(rho.cpu().numpy(), rho_s)
+        assert np.array_equal(eta.cpu().numpy(), eta_s)
+    # second run: replayed graph, same results
+    first = [(r.clone(), e.clone()) for r, e in outs]
+    batch.run()
+    st = batch.stats()
+    assert st["graph_replay"] == 1 and st["kernels_launched"] == 3   # 2 persistent + 1 mixed
+    for (rho, eta), (r0, e0) in zip(outs, first):
+        assert torch.equal(rho, r0) and torch.equal(eta, e0)
+    # new angle values in the same buffers: the replay reads them
+    t0 = batch.jobs[0][1]
+    t0.copy_(torch.tensor([0.8, 2.0, 5.0], dtype=torch.float64))
+    batch.run()
+    wl0, atoms0, _ = jobs[0]
+    rho_s, eta_s = _standalone(api, wl0.with_angles([0.8, 2.0, 5.0]), atoms0, "fp64")
+    assert np.array_equal(outs[0][1].cpu().numpy(), eta_s)
+    # a changed structure rebuilds that job's tables and the plan
+    atoms2 = atoms0.copy()
+    atoms2[:, 0, 2] -= 0.2
+    engines[0].set_structures(atoms2)
+    batch.run()
+    rho_s, eta_s = _standalone(api, wl0.with_angles([0.8, 2.0, 5.0]), atoms2, "fp64")
+    assert np.array_equal(outs[0][1].cpu().numpy(), eta_s)
+    batch.close()
+
+
+def test_batch_wide_job_against_oracle(api):
+    sets = W.batch_sets(3)
+    wl = sets[2].with_steps(40).with_angles([1.5, 3.0])      # N = 121
+    eng = api.Engine(wl, "fp64", "sp4")
+    batch = api.Batch()
+    rho, eta = batch.add(eng, wl.theta0, wl.theta1)
+    batch.run()
+    rho_o, eta_o, _, _ = rocking_curve(wl, "sp4")
+    assert curve_error(eta.cpu().numpy()[0], eta_o) <= 1e-10
+    batch.close()
+
+
+def test_batch_rejects_host_buffers(api):
+    wl = W.tiny(n_beams=5, n_steps=8)
+    eng = api.Engine(wl, "fp64", "sp4")
+    b = api.Batch()
+    t = np.array([1.0])
+    code = b.lib.trh_batch_add(b.h, eng.ctx, 1, api._ptr(t), api._ptr(t), api._ptr(t),
+                               api._ptr(t))
+    assert code == api.TRH_EINVAL
+    assert b.lib.trh_batch_run(b.h, None) == api.TRH_EINVAL   # empty batch
+    b.close()

@@ -1,6 +1,8 @@
 """FP64 CUDA path for wide beam sets (64 < N <= 256, state in global memory) vs the oracle's
 Algorithm 1, through the C ABI. Same bar as the shared-memory kernel: <= 1e-10 relative per curve
 and elementwise on rho."""
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -48,9 +50,12 @@ def test_121_beam_shell_parameter_sets(api):
         _check(rho.cpu().numpy()[k], eta.cpu().numpy()[k], rho_o, eta_o)
 
 
-def test_255_beams_short_slab(api):
-    """The 255-beam recipe (square 5.4 A cell) at 24 slices, two angles: the largest N."""
-    wl = W.large_n255(1)[0].with_steps(24).with_angles([0.7, 4.0])
+def test_255_beams_thin_slab(api):
+    """The 255-beam recipe (square 5.4 A cell), the largest N, on its top 6 A in 60 slices of
+    0.1 A, two angles. Steps of ~1 A are too coarse for a 1e-10 comparison at this N: the fastest
+    evanescent beams grow by ~e^12 within one step, and the merged (FSAL) and unmerged kick
+    orders, equal in exact arithmetic, then differ by 1.7e-8 in the oracle itself at 4 deg."""
+    wl = replace(W.large_n255(1)[0], z_e=-6.0, n_steps=60).with_angles([0.7, 4.0])
     eng = api.Engine(wl, "fp64", "sp4")
     rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
     rho_o, eta_o, _, _ = rocking_curve(wl, "sp4")
