@@ -941,6 +941,7 @@ struct trh_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;  // the legacy default stream cannot be captured
   std::vector<int> h_status;
   trh_stats stats{};
   void drop_graph() {
@@ -1100,14 +1101,17 @@ int trh_batch_run(trh_batch* b, void* stream) {
     TRH_CUDA(cudaGraphLaunch(b->exec, st));
     replayed = true;
   } else {
-    // eager run (sets every kernel attribute), then capture the same sequence for next time
+    // eager run (sets every kernel attribute), then capture the same sequence for next time on
+    // the batch's own stream (capturing records the work without running it)
     int rc = batch_launch(b, st, &launched);
     if (rc != TRH_OK) return rc;
+    if (!b->capture_stream)
+      TRH_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
     int ignored = 0;
-    TRH_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-    rc = batch_launch(b, st, &ignored);
+    TRH_CUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeRelaxed));
+    rc = batch_launch(b, b->capture_stream, &ignored);
     cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    const cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
     if (rc != TRH_OK) return rc;
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
     b->graph = g;
@@ -1166,6 +1170,7 @@ void trh_batch_destroy(trh_batch* b) {
   b->drop_graph();
   for (int i = 0; i < 2; ++i)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   b->d_params.release();
   b->d_items.release();
   b->d_status.release();
