@@ -1,9 +1,11 @@
 """Batches of beam sets with uneven N in persistent launches replayed from a CUDA graph.
 
-Every item of a batch runs the same per-pair code as the standalone call, so batch outputs must
-equal the standalone outputs bit for bit (the standalone paths are checked against the oracle in
-test_gpu_fp64.py, test_gpu_wide.py and test_gpu_mixed.py); one job is also checked against the
-oracle directly."""
+Every item of a batch runs the same per-pair device code as the standalone call, inlined into a
+different kernel, so the compiler may contract a different set of multiply-adds: batch outputs
+must equal the standalone outputs to rounding (1e-13 of the largest |rho|; the standalone paths
+are checked against the oracle in test_gpu_fp64.py, test_gpu_wide.py and test_gpu_mixed.py), and
+a replayed graph must reproduce its own eager run bit for bit. One job is also checked against
+the oracle directly."""
 import numpy as np
 import pytest
 
@@ -32,6 +34,11 @@ def _jobs():
     return out
 
 
+def _same(a, b):
+    assert np.all(np.isfinite(a))
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+
+
 def _standalone(api, wl, atoms, path):
     eng = api.Engine(wl, path, "sp4")
     eng.set_structures(atoms)
@@ -56,8 +63,8 @@ def test_batch_equals_standalone_and_replays(api):
     assert st["kernels_launched"] <= 2 + 1 + 6 * len(jobs)   # tables + 2 persistent + mixed
     ref = [_standalone(api, wl, atoms, path) for wl, atoms, path in jobs]
     for (rho, eta), (rho_s, eta_s) in zip(outs, ref):
-        assert np.array_equal(rho.cpu().numpy(), rho_s)
-        assert np.array_equal(eta.cpu().numpy(), eta_s)
+        _same(rho.cpu().numpy(), rho_s)
+        _same(eta.cpu().numpy(), eta_s)
     # second run: replayed graph, same results
     first = [(r.clone(), e.clone()) for r, e in outs]
     batch.run()
@@ -71,14 +78,14 @@ def test_batch_equals_standalone_and_replays(api):
     batch.run()
     wl0, atoms0, _ = jobs[0]
     rho_s, eta_s = _standalone(api, wl0.with_angles([0.8, 2.0, 5.0]), atoms0, "fp64")
-    assert np.array_equal(outs[0][1].cpu().numpy(), eta_s)
+    _same(outs[0][1].cpu().numpy(), eta_s)
     # a changed structure rebuilds that job's tables and the plan
     atoms2 = atoms0.copy()
     atoms2[:, 0, 2] -= 0.2
     engines[0].set_structures(atoms2)
     batch.run()
     rho_s, eta_s = _standalone(api, wl0.with_angles([0.8, 2.0, 5.0]), atoms2, "fp64")
-    assert np.array_equal(outs[0][1].cpu().numpy(), eta_s)
+    _same(outs[0][1].cpu().numpy(), eta_s)
     batch.close()
 
 
