@@ -2,7 +2,8 @@
 
 Every item of a batch runs the same per-pair device code as the standalone call, inlined into a
 different kernel, so the compiler may contract a different set of multiply-adds: batch outputs
-must equal the standalone outputs to rounding (1e-13 of the largest |rho|; the standalone paths
+must equal the standalone outputs to rounding (1e-11 of the largest |rho|: the RHSTs amplify the
+last-bit differences by up to the threshold, 1000, over the slab; the standalone paths
 are checked against the oracle in test_gpu_fp64.py, test_gpu_wide.py and test_gpu_mixed.py), and
 a replayed graph must reproduce its own eager run bit for bit. One job is also checked against
 the oracle directly."""
@@ -36,7 +37,7 @@ def _jobs():
 
 def _same(a, b):
     assert np.all(np.isfinite(a))
-    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+    assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(b))
 
 
 def _standalone(api, wl, atoms, path):
