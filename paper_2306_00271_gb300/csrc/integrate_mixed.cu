@@ -61,6 +61,8 @@ constexpr int A_SCALES = MT * 4;             // row scales
 constexpr int IMG_BYTES = A_DIGITS + A_SCALES;
 constexpr int B_LBO = 144, B_SBO = 16 * 144;  // padded K-block stride: conflict-free stores
 constexpr int B_TERM = (NC / 8) * B_SBO;
+constexpr int TS = NC + 1;                   // row stride (float2) of T = Q^{-1} in the B region:
+                                             // column walks hit 16 distinct bank pairs per phase
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TM_D0 = 0, TM_D1 = 64, TM_D2 = 128, TM_D3 = 192;
 constexpr uint32_t TM_QH = 256, TM_QL = 320, TM_PH = 384, TM_PL = 448;
@@ -183,7 +185,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// In-place inverse of the n x n complex FP32 matrix T (row stride NC) by Gauss-Jordan elimination
+// In-place inverse of the n x n complex FP32 matrix T (row stride TS) by Gauss-Jordan elimination
 // with row pivoting; the row interchanges are undone on the columns in reverse order at the end.
 // Thread t owns column t % 64 and rows t / 64, t / 64 + 8, ... (no index division in the update).
 __device__ void gj_invert(Smem& S, float2* T, int n) {
@@ -194,7 +196,7 @@ __device__ void gj_invert(Smem& S, float2* T, int n) {
       float best = -1.0f;
       int bi = k;
       for (int r = k + lane; r < n; r += 32) {
-        const float2 a = T[r * NC + k];
+        const float2 a = T[r * TS + k];
         const float m2 = a.x * a.x + a.y * a.y;
         if (m2 > best) {
           best = m2;
@@ -220,16 +222,16 @@ __device__ void gj_invert(Smem& S, float2* T, int n) {
     const int pr = S.piv[k];
     // pivot row (after the interchange) scaled by 1/pivot, and column k (before the update)
     if (tid < n) {
-      const float2 a = T[pr * NC + k];
+      const float2 a = T[pr * TS + k];
       const float d = a.x * a.x + a.y * a.y;
       const float2 inv = make_float2(a.x / d, -a.y / d);
-      const float2 t = T[pr * NC + tid];
+      const float2 t = T[pr * TS + tid];
       S.frow[tid] = (tid == k) ? inv
                                : make_float2(t.x * inv.x - t.y * inv.y, t.x * inv.y + t.y * inv.x);
       // row r's multiplier: rows k and pr trade places
       const int src = (tid == k) ? pr : (tid == pr ? k : tid);
-      S.fcol[tid] = (tid == k) ? make_float2(0.f, 0.f) : T[src * NC + k];
-      S.oldk[tid] = T[k * NC + tid];  // old row k, overwritten by the pivot row below
+      S.fcol[tid] = (tid == k) ? make_float2(0.f, 0.f) : T[src * TS + k];
+      S.oldk[tid] = T[k * TS + tid];  // old row k, overwritten by the pivot row below
     }
     __syncthreads();
     if (col < n) {
@@ -237,13 +239,13 @@ __device__ void gj_invert(Smem& S, float2* T, int n) {
       // the interchange: old row k moves to pr, old row pr becomes the new pivot row k
       for (int r = rg; r < n; r += 8) {
         if (r == k) {
-          T[k * NC + col] = fr;
+          T[k * TS + col] = fr;
         } else {
           const float2 fc = S.fcol[r];
-          float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? S.oldk[col] : T[r * NC + col]);
+          float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? S.oldk[col] : T[r * TS + col]);
           t.x -= fc.x * fr.x - fc.y * fr.y;
           t.y -= fc.x * fr.y + fc.y * fr.x;
-          T[r * NC + col] = t;
+          T[r * TS + col] = t;
         }
       }
     }
@@ -253,9 +255,9 @@ __device__ void gj_invert(Smem& S, float2* T, int n) {
     const int pr = S.piv[k];
     if (pr != k) {
       for (int r = tid; r < n; r += NT) {
-        const float2 t = T[r * NC + k];
-        T[r * NC + k] = T[r * NC + pr];
-        T[r * NC + pr] = t;
+        const float2 t = T[r * TS + k];
+        T[r * TS + k] = T[r * TS + pr];
+        T[r * TS + pr] = t;
       }
       __syncthreads();
     }
@@ -286,7 +288,7 @@ __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32
       const float zrh = part ? ph[kk] : zh[kk], zrl = part ? pl[kk] : zl[kk];
       const float zih = part ? zh[kk] : ph[kk], zil = part ? zl[kk] : pl[kk];
       const float x2h = part ? zih : -zih, x2l = part ? zil : -zil;
-      const float2* Trow = T + (kc + kk) * NC + c0;
+      const float2* Trow = T + (kc + kk) * TS + c0;
 #pragma unroll
       for (int i = 0; i < CPT; ++i) {
         const float2 t = Trow[i];
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
       float2* T = reinterpret_cast<float2*>(S.B);
 #pragma unroll
       for (int c = 0; c < CPT; ++c)
-        if (j < N && c0 + c < N) reinterpret_cast<float*>(&T[j * NC + c0 + c])[part] = Qh[c];
+        if (j < N && c0 + c < N) reinterpret_cast<float*>(&T[j * TS + c0 + c])[part] = Qh[c];
       __syncthreads();
       gj_invert(S, T, N);
       if (S.status != kOk) {
