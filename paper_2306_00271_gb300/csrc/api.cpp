@@ -144,8 +144,12 @@ struct trh_ctx {
   // derivatives the reverse sweep accumulates (union of both)
   int n_free = 0, n_classes = 0, ckpt_every = 64;
   std::vector<int> free_atoms, dw_class, active, free_active, class_of_active;
-  DevBuf<int> d_active, d_free_active, d_class_active, d_rflag;
-  DevBuf<double2> d_ckpt, d_segQ, d_segPb, d_segR, d_adjZ;
+  DevBuf<int> d_active, d_free_active, d_class_active, d_rflag[2];
+  DevBuf<double2> d_ckpt, d_segQ[2], d_segPb[2], d_segR[2], d_adjZ;
+  // reverse-sweep pipeline: recompute / adjoint / contraction on their own streams, buffers
+  // double-buffered by segment parity
+  cudaStream_t gs[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t gev[4][2] = {};   // forward done / recompute / adjoint / contraction, by slot
   DevBuf<double> d_jacA, d_target, d_jac, d_R, d_gz, d_gb;
 };
 
@@ -711,13 +715,21 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   TRH_CUDA(c->d_eta.ensure(pairs * c->N));
   TRH_CUDA(c->d_status.ensure(2 * pairs));
   TRH_CUDA(c->d_ckpt.ensure(pairs * (n_seg + 1) * 2 * NN));
-  TRH_CUDA(c->d_segQ.ensure(pairs * kseg * NN));
-  TRH_CUDA(c->d_segPb.ensure(pairs * kseg * NN));
-  TRH_CUDA(c->d_segR.ensure(pairs * C * 2 * NN));
-  TRH_CUDA(c->d_rflag.ensure(pairs * C));
+  for (int b = 0; b < 2; ++b) {
+    TRH_CUDA(c->d_segQ[b].ensure(pairs * kseg * NN));
+    TRH_CUDA(c->d_segPb[b].ensure(pairs * kseg * NN));
+    TRH_CUDA(c->d_segR[b].ensure(pairs * C * 2 * NN));
+    TRH_CUDA(c->d_rflag[b].ensure(pairs * C));
+  }
   TRH_CUDA(c->d_adjZ.ensure(pairs * 2 * NN));
   TRH_CUDA(c->d_jacA.ensure(pairs * 2 * n_act));
   TRH_CUDA(cudaMemsetAsync(c->d_jacA.p, 0, pairs * 2 * n_act * sizeof(double), st));
+  if (!c->gs[0]) {
+    for (int k = 0; k < 3; ++k) TRH_CUDA(cudaStreamCreateWithFlags(&c->gs[k], cudaStreamNonBlocking));
+    for (int k = 0; k < 4; ++k)
+      for (int b = 0; b < 2; ++b)
+        TRH_CUDA(cudaEventCreateWithFlags(&c->gev[k][b], cudaEventDisableTiming));
+  }
 
   trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, c->d_rho.p, c->d_eta.p);
   ip.ckpt = c->d_ckpt.p;
@@ -729,10 +741,6 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
 
   trh::GradParams g{};
   g.ip = ip;
-  g.segQ = c->d_segQ.p;
-  g.segPb = c->d_segPb.p;
-  g.segR = c->d_segR.p;
-  g.rflag = c->d_rflag.p;
   g.adjZ = c->d_adjZ.p;
   g.status = c->d_status.p;
   g.kseg = kseg;
@@ -748,12 +756,36 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   g.n_atoms = c->n_atoms;
   g.pref = potential_prefactor(c);
   g.jac_atoms = c->d_jacA.p;
+  // Pipeline: while segment g's adjoint runs (stream 1), segment g-1 is recomputed (stream 0)
+  // and segment g+1's contraction runs (stream 2). Buffers of parity b are reused two segments
+  // later, after the contraction and adjoint that read them.
+  cudaStream_t rs = c->gs[0], as = c->gs[1], us = c->gs[2];
+  TRH_CUDA(cudaEventRecord(c->gev[0][0], st));
+  for (int k = 0; k < 3; ++k) TRH_CUDA(cudaStreamWaitEvent(c->gs[k], c->gev[0][0], 0));
   for (int seg = n_seg - 1; seg >= 0; --seg) {
+    const int b = seg & 1;
     g.seg = seg;
-    TRH_CUDA(trh::launch_grad_recompute(g, st, launched));
-    TRH_CUDA(trh::launch_grad_adjoint(g, st, launched));
-    TRH_CUDA(trh::launch_grad_ubar(g, st, launched));
+    g.segQ = c->d_segQ[b].p;
+    g.segPb = c->d_segPb[b].p;
+    g.segR = c->d_segR[b].p;
+    g.rflag = c->d_rflag[b].p;
+    if (seg + 2 < n_seg) {   // slot b was last used by segment seg + 2
+      TRH_CUDA(cudaStreamWaitEvent(rs, c->gev[2][b], 0));
+      TRH_CUDA(cudaStreamWaitEvent(rs, c->gev[3][b], 0));
+    }
+    TRH_CUDA(trh::launch_grad_recompute(g, rs, launched));
+    TRH_CUDA(cudaEventRecord(c->gev[1][b], rs));
+    TRH_CUDA(cudaStreamWaitEvent(as, c->gev[1][b], 0));
+    if (seg + 2 < n_seg) TRH_CUDA(cudaStreamWaitEvent(as, c->gev[3][b], 0));
+    TRH_CUDA(trh::launch_grad_adjoint(g, as, launched));
+    TRH_CUDA(cudaEventRecord(c->gev[2][b], as));
+    TRH_CUDA(cudaStreamWaitEvent(us, c->gev[2][b], 0));
+    TRH_CUDA(trh::launch_grad_ubar(g, us, launched));
+    TRH_CUDA(cudaEventRecord(c->gev[3][b], us));
   }
+  // join: the last contraction ran after every adjoint and recompute it depends on
+  TRH_CUDA(cudaStreamWaitEvent(st, c->gev[3][0], 0));
+  TRH_CUDA(cudaStreamWaitEvent(st, c->gev[3][n_seg > 1 ? 1 : 0], 0));
   TRH_CUDA(cudaEventRecord(c->ev[4], st));
   return TRH_OK;
 }
@@ -900,11 +932,18 @@ void trh_destroy(trh_ctx* c) {
   c->d_active.release();
   c->d_free_active.release();
   c->d_class_active.release();
-  c->d_rflag.release();
   c->d_ckpt.release();
-  c->d_segQ.release();
-  c->d_segPb.release();
-  c->d_segR.release();
+  for (int b = 0; b < 2; ++b) {
+    c->d_rflag[b].release();
+    c->d_segQ[b].release();
+    c->d_segPb[b].release();
+    c->d_segR[b].release();
+  }
+  for (int k = 0; k < 3; ++k)
+    if (c->gs[k]) cudaStreamDestroy(c->gs[k]);
+  for (int k = 0; k < 4; ++k)
+    for (int b = 0; b < 2; ++b)
+      if (c->gev[k][b]) cudaEventDestroy(c->gev[k][b]);
   c->d_adjZ.release();
   c->d_jacA.release();
   c->d_target.release();
