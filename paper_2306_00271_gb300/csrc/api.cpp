@@ -49,6 +49,14 @@ constexpr double kMc2 = 510998.95;       // electron rest energy, eV
 // SRKN_6^b and SRKN_11^b (Blanes & Moan 2002), the coefficients of the paper's sp4 / sp6.
 void bab_scheme(int integrator, trh::Scheme* s) {
   std::vector<double> a, b;
+  if (integrator == TRH_RK4) {
+    // classical Runge-Kutta: no splitting coefficients; two potential nodes per step (z_i and
+    // z_i + h/2), expressed as node fractions 0 and 1/2
+    s->s = 2;
+    s->a[0] = s->a[1] = 0.5;
+    for (int i = 0; i <= 2; ++i) s->b[i] = 0.0;
+    return;
+  }
   if (integrator == TRH_SP4) {
     const double a1 = 0.209515106613362, a2 = -0.143851773179818, a3 = 0.5 - a1 - a2;
     const double b1 = 0.0792036964311957, b2 = 0.353172906049774, b3 = -0.0420650803577195;
@@ -203,7 +211,8 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
     return fail(TRH_EINVAL, "unknown integrator");
   if (p->precision != TRH_FP64 && p->precision != TRH_MIXED)
     return fail(TRH_EINVAL, "unknown precision");
-  if (p->integrator == TRH_RK4) return fail(TRH_EUNSUPPORTED, "RK4 is not implemented on the GPU");
+  if (p->integrator == TRH_RK4 && p->precision != TRH_FP64)
+    return fail(TRH_EUNSUPPORTED, "RK4 runs on the FP64 path only");
   if (p->precision == TRH_MIXED && !trh::mixed_available())
     return fail(TRH_EUNSUPPORTED, "mixed path is not built in this library");
   if (p->precision == TRH_FP64 && p->n_beams > trh::kMaxBeamsWide)
@@ -462,6 +471,7 @@ static trh::IntegrateParams integrate_params(trh_ctx* c, int n_angles, size_t pa
   ip.L = c->L;
   ip.h = c->h;
   ip.threshold = c->threshold;
+  ip.method = c->integrator == TRH_RK4 ? trh::kMethodRK4 : trh::kMethodBAB;
   return ip;
 }
 
@@ -538,13 +548,13 @@ static float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
 // decides most of it: N = 65 pads to 128 with 64-tiles but to 96 with 32-tiles, while N = 255
 // pads to 256 either way and the larger tile has less overhead.
 static std::mutex g_tune_mu;
-static std::map<int, int> g_wide_tile;
+static std::map<int, int> g_wide_tile;  // key 2 N + method
 
 static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* state,
                           cudaStream_t st, int* tile) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_wide_tile.find(c->N);
+    auto it = g_wide_tile.find(2 * c->N + ip.method);
     if (it != g_wide_tile.end()) {
       *tile = it->second;
       return TRH_OK;
@@ -569,7 +579,7 @@ static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* s
     }
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_wide_tile[c->N] = best_tile;
+  g_wide_tile[2 * c->N + ip.method] = best_tile;
   *tile = best_tile;
   return TRH_OK;
 }
@@ -600,8 +610,11 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   TRH_CUDA(c->d_status.ensure(2 * pairs));
   trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, rho, eta);
   int tile = 0;
-  if (c->precision == TRH_FP64 && c->N > trh::kMaxBeamsFp64) {
-    TRH_CUDA(c->d_wide.ensure(pairs * trh::integrate_fp64_wide_state_bytes(c->N) / sizeof(double2)));
+  const bool wide = c->precision == TRH_FP64 &&
+                    (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4);
+  if (wide) {
+    TRH_CUDA(c->d_wide.ensure(pairs * trh::integrate_fp64_wide_state_bytes(c->N, ip.method) /
+                              sizeof(double2)));
     rc = tune_wide_tile(c, ip, c->d_wide.p, st, &tile);
     if (rc != TRH_OK) return rc;
   }
@@ -609,7 +622,7 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   if (c->precision == TRH_MIXED) {
     trh::MixedParams mp = mixed_params(c, ip);
     TRH_CUDA(trh::launch_integrate_mixed(mp, st, &launched));
-  } else if (c->N <= trh::kMaxBeamsFp64) {
+  } else if (!wide) {
     TRH_CUDA(trh::launch_integrate_fp64(ip, st, &launched));
   } else {
     TRH_CUDA(trh::launch_integrate_fp64_wide(ip, c->d_wide.p, tile, st, &launched));
@@ -701,6 +714,8 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   if (c->n_free + c->n_classes < 1) return fail(TRH_EINVAL, "call trh_set_fit first");
   if (c->N > trh::kMaxBeamsFp64)
     return fail(TRH_EUNSUPPORTED, "the reverse sweep supports N <= %d", trh::kMaxBeamsFp64);
+  if (c->integrator == TRH_RK4)
+    return fail(TRH_EUNSUPPORTED, "the reverse sweep supports the splitting integrators");
   int rc = upload_angles(c, n_angles, theta0, theta1, st);
   if (rc != TRH_OK) return rc;
   rc = build_tables(c, st, launched, rebuilt);
@@ -1015,6 +1030,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   b->offset.clear();
   b->params.clear();
   b->total_pairs = 0;
+  b->slot_elems = 0;
   struct Item {
     double cost;
     int4 w;
@@ -1036,7 +1052,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
     J.generation = c->generation;
     b->total_pairs += pairs;
     if (c->precision == TRH_MIXED) continue;
-    const bool wide = c->N > trh::kMaxBeamsFp64;
+    const bool wide = c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4;
     const double cost = (double)c->N * c->N * c->N * c->L * c->scheme.s;
     for (int set = 0; set < c->n_sets; ++set)
       for (int a = 0; a < J.n_angles; ++a)
@@ -1047,6 +1063,9 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
         tune_ctx = c;
       }
       if (c->M > b->max_m_wide) b->max_m_wide = c->M;
+      const size_t elems =
+          trh::integrate_fp64_wide_state_bytes(c->N, ip.method) / sizeof(double2);
+      if (elems > b->slot_elems) b->slot_elems = elems;
     }
   }
   // statuses of job j live at offset[j] (and n_rhst at total_pairs + offset[j])
@@ -1080,7 +1099,6 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   TRH_CUDA(b->d_counter.ensure(2));
   b->wide_tile = 0;
   if (b->n_wide > 0) {
-    b->slot_elems = 2 * (size_t)max_n_wide * max_n_wide;
     TRH_CUDA(b->d_state.ensure(b->wide_ctas * b->slot_elems));
     // the tuner probes the largest wide job with its own parameters and scratch
     for (size_t j = 0; j < b->jobs.size(); ++j)

@@ -90,8 +90,8 @@ __device__ __forceinline__ void tile_gemm(const WideSmem& S, double (&wr)[Tile<T
 
 struct WideArgs {
   IntegrateParams p;
-  double2* Zq;   // [pairs][N][N] Q
-  double2* Zp;   // [pairs][N][N] P
+  double2* Z;     // [pairs][mats][N][N]: Q, P (and the RK4 scratch)
+  int mats;
 };
 
 // One kick with coefficient hb and (if do_drift) the drift with ha, for the table in shared
@@ -164,6 +164,108 @@ __device__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, doub
       }
       __syncthreads();
     }
+  }
+}
+
+__device__ void load_table(double2* tbl, const IntegrateParams& p, int set, int node) {
+  const double2* un = p.u + ((size_t)set * p.n_nodes + node) * p.M;
+  for (int m = threadIdx.x; m < p.M; m += WT) tbl[m] = __ldg(un + m);
+}
+
+// K = -(U + Gamma^2) X for the table in shared memory (a classical Runge-Kutta stage; Section
+// 3.4 writes the ODE as Z' = B Z, whose lower block is -(U + Gamma^2) Q). X is not modified.
+template <int TB>
+__device__ void wide_stage(WideSmem& S, const double2* tbl, const int* lmap, const double2* X,
+                           double2* K, int N) {
+  using T = Tile<TB>;
+  constexpr int TLD = T::LD;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (N + TB - 1) / TB;
+  for (int jb = 0; jb < nb; ++jb)
+    for (int ib = 0; ib < nb; ++ib) {
+      double wr[T::S][4], wi[T::S][4];
+#pragma unroll
+      for (int s = 0; s < T::S; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wr[s][q] = wi[s][q] = 0.0;
+      for (int kb = 0; kb < nb; ++kb) {
+        for (int e = tid; e < TB * TB; e += WT) {
+          const int r = e / TB, k = e - r * TB;
+          const int gr = ib * TB + r, gk = kb * TB + k, gc = jb * TB + k, xr = kb * TB + r;
+          double2 u = make_double2(0.0, 0.0), x = make_double2(0.0, 0.0);
+          if (gr < N && gk < N) u = tbl[__ldg(lmap + gr * N + gk)];
+          if (xr < N && gc < N) x = X[(size_t)xr * N + gc];
+          S.Ar[r * TLD + k] = u.x;
+          S.Ai[r * TLD + k] = u.y;
+          S.Br[r * TLD + k] = x.x;
+          S.Bi[r * TLD + k] = x.y;
+        }
+        __syncthreads();
+        tile_gemm<TB>(S, wr, wi);
+        __syncthreads();
+      }
+      const int mt = warp % T::MW, nt = warp / T::MW, g = lane >> 2, t = lane & 3;
+#pragma unroll
+      for (int s = 0; s < T::S; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = ib * TB + 16 * mt + g + 8 * (q >> 1);
+          const int col = jb * TB + 8 * T::S * nt + 8 * s + 2 * t + (q & 1);
+          if (row < N && col < N) {
+            const size_t o = (size_t)row * N + col;
+            const double2 xv = X[o];
+            const double g2 = S.gam2[row];
+            K[o] = make_double2(-(wr[s][q] + g2 * xv.x), -(wi[s][q] + g2 * xv.y));
+          }
+        }
+    }
+  __syncthreads();
+}
+
+// One classical Runge-Kutta step (Section 3.4's rk4) for c'' = -M(z) c in the economical form:
+// with k_r the derivative increments of P (k_r = -M X_r),
+//   X_1 = Q, X_2 = Q + h/2 P, X_3 = X_2 + h^2/4 k_1, X_4 = Q + h P + h^2/2 k_2,
+//   Q <- Q + h P + h^2/6 (k_1 + k_2 + k_3),  P <- P + h/6 (k_1 + 2 k_2 + 2 k_3 + k_4),
+// M at z_i (node 2i), z_i + h/2 (node 2i+1, stages 2 and 3) and z_i + h (node 2i+2).
+// Scratch after Q, P: X, K, dP (= k_1 + 2 k_2 + ...), dQ (= k_1 + k_2 + ...).
+template <int TB>
+__device__ void wide_rk4_step(WideSmem& S, double2* tbl, const IntegrateParams& p, int set,
+                              int i, double2* Q, double2* P) {
+  const int tid = threadIdx.x, N = p.N;
+  const size_t NN = (size_t)N * N;
+  double2 *X = P + NN, *K = X + NN, *dP = K + NN, *dQ = dP + NN;
+  const double h = p.h, h2 = h * h;
+  for (int stage = 0; stage < 4; ++stage) {
+    if (stage != 2) {   // stages 2 and 3 share the midpoint node
+      load_table(tbl, p, set, 2 * i + (stage == 0 ? 0 : (stage == 1 ? 1 : 2)));
+      __syncthreads();
+    }
+    wide_stage<TB>(S, tbl, p.lmap, stage == 0 ? Q : X, K, N);
+    for (size_t e = tid; e < NN; e += WT) {
+      const double2 k = K[e];
+      if (stage == 0) {
+        const double2 q = Q[e], pp = P[e];
+        dP[e] = k;
+        dQ[e] = k;
+        X[e] = make_double2(q.x + 0.5 * h * pp.x, q.y + 0.5 * h * pp.y);
+      } else if (stage == 1) {
+        const double2 x = X[e], dq = dQ[e], dp = dP[e];
+        X[e] = make_double2(x.x + 0.25 * h2 * dq.x, x.y + 0.25 * h2 * dq.y);
+        dP[e] = make_double2(dp.x + 2.0 * k.x, dp.y + 2.0 * k.y);
+        dQ[e] = make_double2(dq.x + k.x, dq.y + k.y);
+      } else if (stage == 2) {
+        const double2 q = Q[e], pp = P[e], dq = dQ[e], dp = dP[e];
+        X[e] = make_double2(q.x + h * pp.x + 0.5 * h2 * (dp.x - dq.x),
+                            q.y + h * pp.y + 0.5 * h2 * (dp.y - dq.y));
+        dP[e] = make_double2(dp.x + 2.0 * k.x, dp.y + 2.0 * k.y);
+        dQ[e] = make_double2(dq.x + k.x, dq.y + k.y);
+      } else {
+        const double2 q = Q[e], pp = P[e], dq = dQ[e], dp = dP[e];
+        Q[e] = make_double2(q.x + h * pp.x + (h2 / 6.0) * dq.x, q.y + h * pp.y + (h2 / 6.0) * dq.y);
+        P[e] = make_double2(pp.x + (h / 6.0) * (dp.x + k.x), pp.y + (h / 6.0) * (dp.y + k.y));
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -276,18 +378,16 @@ __device__ void wide_gauss_jordan(WideSmem& S, double2* X, double2* Y, int N) {
   }
 }
 
-__device__ void load_table(double2* tbl, const IntegrateParams& p, int set, int node) {
-  const double2* un = p.u + ((size_t)set * p.n_nodes + node) * p.M;
-  for (int m = threadIdx.x; m < p.M; m += WT) tbl[m] = __ldg(un + m);
-}
-
-// Integrates one (set, angle) pair of `p` with its state at Q, P (N x N each).
+// Integrates one (set, angle) pair of `p` with its state block Z (Q, P and, for RK4, four more
+// N x N scratch matrices).
 template <int TB>
 __device__ void wide_pair(WideSmem& S, double2* tbl, const IntegrateParams& p, int angle, int set,
-                          double2* Q, double2* P) {
+                          double2* Z) {
   const int tid = threadIdx.x, N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   const size_t NN = (size_t)N * N;
+  double2* Q = Z;
+  double2* P = Z + NN;
 
   if (tid == 0) {
     S.status = kOk;
@@ -321,12 +421,16 @@ __device__ void wide_pair(WideSmem& S, double2* tbl, const IntegrateParams& p, i
   const int s = p.sch.s;
   if (S.status == kOk) {
     for (int i = 0; i < p.L && S.status == kOk; ++i) {
-      for (int r = 0; r < s; ++r) {
-        const int n = s * i + r;
-        const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
-        load_table(tbl, p, set, n);
-        __syncthreads();
-        wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * coef, p.h * p.sch.a[r], true);
+      if (p.method == kMethodRK4) {
+        wide_rk4_step<TB>(S, tbl, p, set, i, Q, P);
+      } else {
+        for (int r = 0; r < s; ++r) {
+          const int n = s * i + r;
+          const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
+          load_table(tbl, p, set, n);
+          __syncthreads();
+          wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * coef, p.h * p.sch.a[r], true);
+        }
       }
       wide_badness(S, Q, N, p.threshold);
       if (S.flag) {
@@ -342,9 +446,11 @@ __device__ void wide_pair(WideSmem& S, double2* tbl, const IntegrateParams& p, i
     }
   }
   if (S.status == kOk) {
-    load_table(tbl, p, set, s * p.L);
-    __syncthreads();
-    wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * p.sch.b[s], 0.0, false);
+    if (p.method != kMethodRK4) {   // the final kick of the splitting
+      load_table(tbl, p, set, s * p.L);
+      __syncthreads();
+      wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * p.sch.b[s], 0.0, false);
+    }
     // A = Gamma Q - i P into Q's storage, B = Gamma Q + i P into P's
     for (size_t e = tid; e < NN; e += WT) {
       const int j = (int)(e / N);
@@ -383,12 +489,12 @@ __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide(WideArgs w) {
   double2* tbl = reinterpret_cast<double2*>(smem_raw + kTblOffset);
   const size_t NN = (size_t)w.p.N * w.p.N;
   const size_t pair = (size_t)blockIdx.y * w.p.ang.n_angles + blockIdx.x;
-  wide_pair<TB>(S, tbl, w.p, blockIdx.x, blockIdx.y, w.Zq + pair * NN, w.Zp + pair * NN);
+  wide_pair<TB>(S, tbl, w.p, blockIdx.x, blockIdx.y, w.Z + pair * w.mats * NN);
 }
 
 // Persistent form for batches (see k_integrate_fp64_items): work items (job, set, angle, -) in
 // decreasing-cost order; each CTA keeps its current item's state in its own slot of `state`
-// (slot_elems = 2 N_max^2 complex128 per CTA).
+// (slot_elems = mats N_max^2 complex128 per CTA).
 template <int TB>
 __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide_items(
     const IntegrateParams* jobs, const int4* items, int n_items, int* counter, double2* state,
@@ -406,14 +512,15 @@ __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide_items(
     const int4 w = items[it];
     if (threadIdx.x == 0) job = jobs[w.x];
     __syncthreads();
-    double2* Q = state + (size_t)blockIdx.x * slot_elems;
-    wide_pair<TB>(S, tbl, job, w.z, w.y, Q, Q + (size_t)job.N * job.N);
+    wide_pair<TB>(S, tbl, job, w.z, w.y, state + (size_t)blockIdx.x * slot_elems);
   }
 }
 
 }  // namespace
 
-size_t integrate_fp64_wide_state_bytes(int N) { return 2 * (size_t)N * N * sizeof(double2); }
+size_t integrate_fp64_wide_state_bytes(int N, int method) {
+  return (method == kMethodRK4 ? 6 : 2) * (size_t)N * N * sizeof(double2);
+}
 
 cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, int tile,
                                        cudaStream_t st, int* n_launched) {
@@ -423,8 +530,7 @@ cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state,
                               : (const void*)k_integrate_fp64_wide<32>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const size_t pairs = (size_t)p.n_sets * p.ang.n_angles;
-  WideArgs w{p, state, state + pairs * (size_t)p.N * p.N};
+  WideArgs w{p, state, p.method == kMethodRK4 ? 6 : 2};
   const dim3 grid(p.ang.n_angles, p.n_sets);
   if (tile == 64) k_integrate_fp64_wide<64><<<grid, WT, smem, st>>>(w);
   else k_integrate_fp64_wide<32><<<grid, WT, smem, st>>>(w);

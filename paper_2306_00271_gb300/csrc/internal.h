@@ -10,6 +10,10 @@ constexpr int kMaxBeamsFp64 = 64;    // FP64 path: state resident in shared memo
 constexpr int kMaxBeamsMixed = 64;   // mixed path: one 128-row UMMA tile holds [Re; Im] of N <= 64
 constexpr int kMaxBeamsWide = 256;   // FP64 path with the state in global memory (64 < N <= 256)
 
+// Integration methods of the kernels (IntegrateParams::method).
+constexpr int kMethodBAB = 0;        // splitting scheme (Scheme), FSAL-merged
+constexpr int kMethodRK4 = 1;        // classical Runge-Kutta (wide FP64 kernel only)
+
 // Status words written by kernels (mirrors the TRH_E* codes of trheed.h).
 enum DevStatus : int {
   kOk = 0, kSingular = -3, kGrazing = -2, kTimeout = -4
@@ -49,6 +53,7 @@ struct IntegrateParams {
   int N, M, n_nodes, n_sets, L;
   double h;
   double threshold;
+  int method;                  // kMethodBAB or kMethodRK4 (nodes z_i, z_i + h/2 per step)
   // Optional checkpoints for the reverse sweep (nullptr: none). Slot c < n_ckpt - 1 holds the
   // state [Q; P] at the start of step c * ckpt_every, slot n_ckpt - 1 the final state;
   // layout [n_sets][n_angles][n_ckpt][2][N][N] complex.
@@ -149,8 +154,8 @@ size_t mixed_image_bytes_per_node();
 void set_last_error(const char* msg);
 cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int* n_launched);
 size_t integrate_fp64_smem_bytes();
-// Wide beam sets on the FP64 path (integrate_fp64_wide.cu); `state` holds 2 N^2 complex128 per
-// (set, angle) pair (integrate_fp64_wide_state_bytes).
+// Wide beam sets and RK4 on the FP64 path (integrate_fp64_wide.cu); `state` holds 2 N^2 (6 N^2
+// for RK4) complex128 per (set, angle) pair (integrate_fp64_wide_state_bytes).
 cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, int tile,
                                        cudaStream_t st, int* n_launched);
 // Persistent batch kernels: items (job, set, angle, -) sorted by decreasing cost; `counter` must
@@ -162,7 +167,7 @@ cudaError_t launch_integrate_fp64_wide_items(const IntegrateParams* jobs, const 
                                              int n_items, int* counter, double2* state,
                                              size_t slot_elems, int max_m, int tile, int n_ctas,
                                              cudaStream_t st, int* n_launched);
-size_t integrate_fp64_wide_state_bytes(int N);
+size_t integrate_fp64_wide_state_bytes(int N, int method);
 bool mixed_available();
 
 }  // namespace trh

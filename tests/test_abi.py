@@ -95,6 +95,9 @@ def test_large_beam_sets_are_unsupported_not_wrong(lib):
     wl.beams = W.beam_shell(a1, a2, 31.0)
     p, keep = _problem(wl, precision=1)
     assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
+    # RK4 runs on the FP64 path only
+    p, keep = _problem(W.rheed_row(), precision=1, integrator=2)
+    assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
 
 
 def test_null_arguments(lib):

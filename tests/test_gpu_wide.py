@@ -76,3 +76,25 @@ def test_limits(api):
         eng.set_fit([0], None)
         eng.curve_jacobian(wl.theta0, wl.theta1)
     assert e.value.code == api.TRH_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n_beams", [7, 37, 91])
+def test_rk4_against_oracle(api, n_beams):
+    """Classical Runge-Kutta (Section 3.4's rk4) on the FP64 path, small and wide beam sets."""
+    wl = W.tiny(n_beams=n_beams, seed=60 + n_beams, n_steps=50, theta0=(0.9, 2.4), depth=8.0)
+    eng = api.Engine(wl, "fp64", "rk4")
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    rho_o, eta_o, _, n_o = rocking_curve(wl, "rk4")
+    _check(rho.cpu().numpy()[0], eta.cpu().numpy()[0], rho_o, eta_o)
+    assert eng.stats()["rhst_total"] > 0
+
+
+def test_rk4_in_a_batch(api):
+    wl = W.tiny(n_beams=19, seed=3, n_steps=40, theta0=(1.2, 3.1), depth=6.0)
+    eng = api.Engine(wl, "fp64", "rk4")
+    batch = api.Batch()
+    rho, eta = batch.add(eng, wl.theta0, wl.theta1)
+    batch.run()
+    rho_o, eta_o, _, _ = rocking_curve(wl, "rk4")
+    _check(rho.cpu().numpy()[0], eta.cpu().numpy()[0], rho_o, eta_o)
+    batch.close()
