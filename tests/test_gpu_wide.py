@@ -80,8 +80,11 @@ def test_limits(api):
 
 @pytest.mark.parametrize("n_beams", [7, 37, 91])
 def test_rk4_against_oracle(api, n_beams):
-    """Classical Runge-Kutta (Section 3.4's rk4) on the FP64 path, small and wide beam sets."""
-    wl = W.tiny(n_beams=n_beams, seed=60 + n_beams, n_steps=50, theta0=(0.9, 2.4), depth=8.0)
+    """Classical Runge-Kutta (Section 3.4's rk4) on the FP64 path, small and wide beam sets, at
+    0.05 A steps. (At 0.16 A steps and 37 beams an RHST follows almost every step and two
+    algebraically equal groupings of the RK4 update differ by 3e-8 in the oracle itself; the
+    kernel's grouping, Q + h P + h^2/6 (k1 + k2 + k3), is one of them.)"""
+    wl = W.tiny(n_beams=n_beams, seed=60 + n_beams, n_steps=160, theta0=(0.9, 2.4), depth=8.0)
     eng = api.Engine(wl, "fp64", "rk4")
     rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
     rho_o, eta_o, _, n_o = rocking_curve(wl, "rk4")
@@ -90,7 +93,7 @@ def test_rk4_against_oracle(api, n_beams):
 
 
 def test_rk4_in_a_batch(api):
-    wl = W.tiny(n_beams=19, seed=3, n_steps=40, theta0=(1.2, 3.1), depth=6.0)
+    wl = W.tiny(n_beams=19, seed=3, n_steps=120, theta0=(1.2, 3.1), depth=6.0)
     eng = api.Engine(wl, "fp64", "rk4")
     batch = api.Batch()
     rho, eta = batch.add(eng, wl.theta0, wl.theta1)
