@@ -202,9 +202,9 @@ int trh_rfactor_grad(trh_ctx* ctx, int n_angles, const double* theta0, const dou
  * Many rocking curves of different beam sets (one context each, any N) and parameter sets in as
  * few launches as possible (Section 3.4's parallelisation over angles, extended across problems):
  * all binary64 work items (context, set, angle) with N <= 64 go to one persistent kernel and all
- * with 64 < N <= 256 to a second one; each persistent CTA takes items from an atomic counter in
- * decreasing-cost order (N^3 L, longest first), so uneven beam counts balance across the SMs.
- * Contexts of precision TRH_MIXED add one launch each. The first trh_batch_run executes eagerly
+ * with 64 < N <= 256 (and all RK4 items) to a second one, and all TRH_MIXED items to a third;
+ * each persistent CTA takes items from an atomic counter in decreasing-cost order (N^3 L,
+ * longest first), so uneven beam counts balance across the SMs. The first trh_batch_run executes eagerly
  * and captures the same launch sequence in a CUDA graph; later runs replay the graph (the
  * potential tables of contexts whose structure changed are rebuilt before the replay, and the
  * plan and graph are rebuilt when a context's device tables moved). The wide kernel's tile edge

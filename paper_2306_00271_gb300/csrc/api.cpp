@@ -985,10 +985,13 @@ struct trh_batch {
   bool prepared = false;
   std::vector<size_t> offset;            // first pair of each job in the status array
   size_t total_pairs = 0;
-  int n_small = 0, n_wide = 0, wide_tile = 0, wide_ctas = 0, small_ctas = 0, max_m_wide = 0;
+  int n_small = 0, n_wide = 0, n_mixed = 0, wide_tile = 0, wide_ctas = 0, small_ctas = 0,
+      mixed_ctas = 0, max_m_wide = 0;
   size_t slot_elems = 0;
   std::vector<trh::IntegrateParams> params;
+  std::vector<trh::MixedParams> mparams;
   DevBuf<trh::IntegrateParams> d_params;
+  DevBuf<trh::MixedParams> d_mparams;
   DevBuf<int4> d_items;                  // small items, then wide items
   DevBuf<int> d_status, d_counter;
   DevBuf<double2> d_state;
@@ -1034,7 +1037,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   struct Item {
     double cost;
     int4 w;
-    bool wide;
+    int family;   // 0: FP64 N <= 64, 1: FP64 wide or RK4, 2: mixed precision
   };
   std::vector<Item> items;
   int max_n_wide = 0;
@@ -1051,12 +1054,13 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
     b->params.push_back(ip);
     J.generation = c->generation;
     b->total_pairs += pairs;
-    if (c->precision == TRH_MIXED) continue;
-    const bool wide = c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4;
+    const bool wide = c->precision == TRH_FP64 &&
+                      (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4);
+    const int family = c->precision == TRH_MIXED ? 2 : (wide ? 1 : 0);
     const double cost = (double)c->N * c->N * c->N * c->L * c->scheme.s;
     for (int set = 0; set < c->n_sets; ++set)
       for (int a = 0; a < J.n_angles; ++a)
-        items.push_back({cost, make_int4((int)j, set, a, 0), wide});
+        items.push_back({cost, make_int4((int)j, set, a, 0), family});
     if (wide) {
       if (c->N > max_n_wide) {
         max_n_wide = c->N;
@@ -1070,33 +1074,39 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   }
   // statuses of job j live at offset[j] (and n_rhst at total_pairs + offset[j])
   TRH_CUDA(b->d_status.ensure(2 * b->total_pairs));
+  b->mparams.clear();
   for (size_t j = 0; j < b->jobs.size(); ++j) {
     b->params[j].out.status = b->d_status.p + b->offset[j];
     b->params[j].out.n_rhst = b->d_status.p + b->total_pairs + b->offset[j];
+    b->mparams.push_back(mixed_params(b->jobs[j].c, b->params[j]));
   }
   // longest-processing-time first within each kernel family
   std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
-    if (x.wide != y.wide) return !x.wide;
+    if (x.family != y.family) return x.family < y.family;
     return x.cost > y.cost;
   });
   std::vector<int4> w;
-  b->n_small = b->n_wide = 0;
+  b->n_small = b->n_wide = b->n_mixed = 0;
   for (const Item& it : items) {
     w.push_back(it.w);
-    (it.wide ? b->n_wide : b->n_small)++;
+    (it.family == 0 ? b->n_small : (it.family == 1 ? b->n_wide : b->n_mixed))++;
   }
   int dev = 0, n_sm = 0;
   TRH_CUDA(cudaGetDevice(&dev));
   TRH_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   b->small_ctas = std::min(b->n_small, n_sm);
   b->wide_ctas = std::min(b->n_wide, n_sm);
+  b->mixed_ctas = std::min(b->n_mixed, n_sm);
   TRH_CUDA(b->d_params.ensure(b->params.size()));
   TRH_CUDA(cudaMemcpy(b->d_params.p, b->params.data(),
                       b->params.size() * sizeof(trh::IntegrateParams), cudaMemcpyHostToDevice));
+  TRH_CUDA(b->d_mparams.ensure(b->mparams.size()));
+  TRH_CUDA(cudaMemcpy(b->d_mparams.p, b->mparams.data(),
+                      b->mparams.size() * sizeof(trh::MixedParams), cudaMemcpyHostToDevice));
   TRH_CUDA(b->d_items.ensure(w.size() > 0 ? w.size() : 1));
   if (!w.empty())
     TRH_CUDA(cudaMemcpy(b->d_items.p, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  TRH_CUDA(b->d_counter.ensure(2));
+  TRH_CUDA(b->d_counter.ensure(3));
   b->wide_tile = 0;
   if (b->n_wide > 0) {
     TRH_CUDA(b->d_state.ensure(b->wide_ctas * b->slot_elems));
@@ -1114,10 +1124,9 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   return TRH_OK;
 }
 
-// The batch's device work: counters reset, the persistent FP64 launches, one launch per
-// mixed-precision job.
+// The batch's device work: counters reset, then the persistent launches of the three families.
 static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
-  TRH_CUDA(cudaMemsetAsync(b->d_counter.p, 0, 2 * sizeof(int), st));
+  TRH_CUDA(cudaMemsetAsync(b->d_counter.p, 0, 3 * sizeof(int), st));
   if (b->n_small > 0)
     TRH_CUDA(trh::launch_integrate_fp64_items(b->d_params.p, b->d_items.p, b->n_small,
                                               b->d_counter.p, b->small_ctas, st, launched));
@@ -1125,12 +1134,10 @@ static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
     TRH_CUDA(trh::launch_integrate_fp64_wide_items(
         b->d_params.p, b->d_items.p + b->n_small, b->n_wide, b->d_counter.p + 1, b->d_state.p,
         b->slot_elems, b->max_m_wide, b->wide_tile, b->wide_ctas, st, launched));
-  for (size_t j = 0; j < b->jobs.size(); ++j) {
-    trh_ctx* c = b->jobs[j].c;
-    if (c->precision != TRH_MIXED) continue;
-    trh::MixedParams mp = mixed_params(c, b->params[j]);
-    TRH_CUDA(trh::launch_integrate_mixed(mp, st, launched));
-  }
+  if (b->n_mixed > 0)
+    TRH_CUDA(trh::launch_integrate_mixed_items(b->d_mparams.p,
+                                               b->d_items.p + b->n_small + b->n_wide, b->n_mixed,
+                                               b->d_counter.p + 2, b->mixed_ctas, st, launched));
   return TRH_OK;
 }
 
@@ -1201,9 +1208,8 @@ int trh_batch_run(trh_batch* b, void* stream) {
       }
     }
   }
-  int n_mixed = 0;
-  for (const auto& J : b->jobs) n_mixed += (J.c->precision == TRH_MIXED);
-  S.kernels_launched = replayed ? (b->n_small > 0) + (b->n_wide > 0) + n_mixed : launched;
+  S.kernels_launched =
+      replayed ? (b->n_small > 0) + (b->n_wide > 0) + (b->n_mixed > 0) : launched;
   S.ms_integrate = elapsed_ms(b->ev[0], b->ev[1]);
   S.wide_tile = b->wide_tile;
   S.graph_replay = replayed ? 1 : 0;
@@ -1229,6 +1235,7 @@ void trh_batch_destroy(trh_batch* b) {
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   b->d_params.release();
+  b->d_mparams.release();
   b->d_items.release();
   b->d_status.release();
   b->d_counter.release();

@@ -77,6 +77,7 @@ struct __align__(128) Smem {
   float gamma[2][NC];           // column scales of B, by kick parity
   uint4 colmax[2][NC];          // per-quadrant column maxima of Q (float bits of |Q|), by parity
   int ovf;                      // a digit outgrew its scale (set before the end-of-kick barrier)
+  int drained;                  // a pending image copy was waited for at the end of a pair
   uint64_t bar_tma, bar_mma;
   uint32_t tmem_base;
   int status, flag, n_rhst;
@@ -320,16 +321,36 @@ __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32
 
 // KS = number of 16-wide K slices (ceil(2N / 16)), a template parameter so the MMA issue loop of
 // the single issuing thread is fully unrolled with constant descriptor offsets.
+// Per-CTA setup shared by all pairs a CTA integrates: the two mbarriers and the TMEM allocation.
+__device__ __forceinline__ uint32_t mixed_prologue(Smem& S) {
+  if (threadIdx.x == 0) {
+    mbar_init(&S.bar_tma, 1);
+    mbar_init(&S.bar_mma, 1);
+    mbar_fence_init();
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&S.tmem_base, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return S.tmem_base;
+}
+
+__device__ __forceinline__ void mixed_epilogue(Smem& S, uint32_t tmem) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Integrates one (set, angle) pair. The mbarrier phases carry over from pair to pair.
 template <int KS>
-__global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+__device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int angle, int set,
+                                           uint32_t tmem, uint32_t& ph_tma, uint32_t& ph_mma) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int qd = warp & 3, cq = warp >> 2;
   const int m = 32 * qd + lane;  // real-ified row = TMEM lane
   const int j = m >> 1, part = m & 1;
   const int c0 = CPT * cq;
-  const int angle = blockIdx.x, set = blockIdx.y;
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   const unsigned char* img_set = p.img + (size_t)set * p.n_nodes * IMG_BYTES;
@@ -337,9 +358,6 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
   if (tid == 0) {
     S.status = kOk;
     S.n_rhst = 0;
-    mbar_init(&S.bar_tma, 1);
-    mbar_init(&S.bar_mma, 1);
-    mbar_fence_init();
   }
   // Row A1: Gamma for this angle (binary64)
   const double t0 = p.ang.theta0[angle] * (kPi / 180.0);
@@ -360,11 +378,9 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
     S.Gr[tid] = gr;
     S.Gi[tid] = gi;
   }
-  if (warp == 0) tmem_alloc(&S.tmem_base, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = S.tmem_base;
   const uint32_t t_lane = tmem + ((uint32_t)(32 * qd) << 16);
   const double g2d = (j < N) ? S.gam2[j] : 0.0;
   const float g2h = (float)g2d, g2l = (float)(g2d - (double)g2h);
@@ -397,7 +413,6 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
   __syncthreads();
   tc_fence_after();
 
-  uint32_t ph_tma = 0, ph_mma = 0;
   const int s = p.sch.s;
   const uint32_t idesc = idesc_bf16_f32(MT, p.n_mma);
   const uint32_t a_base = smem_u32(S.A), b_base = smem_u32(S.B);
@@ -597,12 +612,15 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
     }
   }
 
-  // drain: a bulk copy issued but never waited for must land before the CTA exits
+  // drain: a bulk copy issued but never waited for must land before the CTA moves on or exits
+  if (tid == 0) S.drained = 0;
   if (tid == 0 && tma_pending) {
     if (!mbar_wait(&S.bar_tma, ph_tma, kWaitCycles)) S.status = kTimeout;
+    S.drained = 1;
   }
   if (abort && tid == 0 && S.status == kOk) S.status = kTimeout;
   __syncthreads();
+  if (S.drained) ph_tma ^= 1;
 
   if (S.status == kOk) {
     // ---- assembly in FP64: A0 = Gamma Q - i P, x = A0^{-1} e_1 (+1 refinement), rho = B0 x
@@ -688,7 +706,52 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+template <int KS>
+__global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const uint32_t tmem = mixed_prologue(S);
+  uint32_t ph_tma = 0, ph_mma = 0;
+  mixed_pair<KS>(S, p, blockIdx.x, blockIdx.y, tmem, ph_tma, ph_mma);
+  mixed_epilogue(S, tmem);
+}
+
+// Persistent form for batches: items (job, set, angle, -) in decreasing-cost order from an atomic
+// counter; each item runs with its job's K-slice count. The job's parameters are staged in the
+// dynamic shared memory after Smem. A CTA stops after a timed-out wait (its barriers are then in
+// an unknown phase).
+__global__ void __launch_bounds__(NT, 1) k_integrate_mixed_items(const MixedParams* jobs,
+                                                                 const int4* items, int n_items,
+                                                                 int* counter) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  MixedParams& job = *reinterpret_cast<MixedParams*>(smem_raw + sizeof(Smem));
+  int& next = *reinterpret_cast<int*>(smem_raw + sizeof(Smem) + sizeof(MixedParams));
+  const uint32_t tmem = mixed_prologue(S);
+  uint32_t ph_tma = 0, ph_mma = 0;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = next;
+    if (it >= n_items) break;
+    const int4 w = items[it];
+    if (threadIdx.x == 0) job = jobs[w.x];
+    __syncthreads();
+    switch (job.k_slices) {
+      case 1: mixed_pair<1>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      case 2: mixed_pair<2>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      case 3: mixed_pair<3>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      case 4: mixed_pair<4>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      case 5: mixed_pair<5>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      case 6: mixed_pair<6>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      case 7: mixed_pair<7>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      default: mixed_pair<8>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+    }
+    if (S.status == kTimeout) break;
+  }
+  mixed_epilogue(S, tmem);
 }
 
 // Fixed-point digit images of the real-ified U(tau), one CTA per node: row scales
@@ -774,6 +837,18 @@ static cudaError_t launch_ks(const MixedParams& p, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   dim3 grid(p.ang.n_angles, p.n_sets);
   k_integrate_mixed<KS><<<grid, NT, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_mixed_items(const MixedParams* jobs, const int4* items, int n_items,
+                                         int* counter, int n_ctas, cudaStream_t st,
+                                         int* n_launched) {
+  const size_t smem = sizeof(Smem) + sizeof(MixedParams) + 16 + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_integrate_mixed_items,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_integrate_mixed_items<<<n_ctas, NT, smem, st>>>(jobs, items, n_items, counter);
+  if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }
 

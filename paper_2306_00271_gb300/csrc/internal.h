@@ -149,6 +149,10 @@ cudaError_t launch_rfactor(const RFactorParams& r, cudaStream_t st, int* n_launc
 cudaError_t launch_potential(const PotentialParams& p, cudaStream_t st, int* n_launched);
 cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* n_launched);
 cudaError_t launch_integrate_mixed(const MixedParams& p, cudaStream_t st, int* n_launched);
+// Persistent mixed-precision batch kernel (items as for launch_integrate_fp64_items; any k_slices).
+cudaError_t launch_integrate_mixed_items(const MixedParams* jobs, const int4* items, int n_items,
+                                         int* counter, int n_ctas, cudaStream_t st,
+                                         int* n_launched);
 size_t mixed_image_bytes_per_node();
 // Records the message trh_last_error() returns on this thread.
 void set_last_error(const char* msg);

@@ -70,7 +70,7 @@ def test_batch_equals_standalone_and_replays(api):
     first = [(r.clone(), e.clone()) for r, e in outs]
     batch.run()
     st = batch.stats()
-    assert st["graph_replay"] == 1 and st["kernels_launched"] == 3   # 2 persistent + 1 mixed
+    assert st["graph_replay"] == 1 and st["kernels_launched"] == 3   # one per kernel family
     for (rho, eta), (r0, e0) in zip(outs, first):
         assert torch.equal(rho, r0) and torch.equal(eta, e0)
     # new angle values in the same buffers: the replay reads them
