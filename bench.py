@@ -237,6 +237,56 @@ def run_gradient(local: int, slices: int = 0, warmup: int = 1):
             "kernels_launched": st["kernels_launched"], "R": float(R[0])}
 
 
+def run_batches(slices: int = 0):
+    """Batched-workload lines (parameter sets of uneven beam counts, 60 angles each), each batch
+    one persistent launch per kernel family replayed from its CUDA graph, timed with CUDA events
+    around the replay (after one eager run that also captures the graph).
+
+    mixed: 8 perturbed structures, 4 with 31 and 4 with 61 beams, mixed path, 2000 slices.
+    fp64_wide: 2 structures with 121 beams on the FP64 path (N > 64), 250 slices (an FP64 step
+    at this N costs ~8 ms per angle on one SM, so the full 2000 slices would take minutes)."""
+    import torch
+    from paper_2306_00271_gb300 import api
+    sets = W.batch_sets(12)
+    out = {}
+    plans = {"mixed": ("mixed", {31: [], 61: []}, slices or 2000),
+             "fp64_wide": ("fp64", {121: []}, slices or 250)}
+    for s_ in sets:
+        for name, (_, classes, _) in plans.items():
+            n = s_.beams.shape[0]
+            if n in classes and len(classes[n]) < (4 if name == "mixed" else 2):
+                classes[n].append(s_)
+    for name, (path, classes, L) in plans.items():
+        batch = api.Batch()
+        engines, n_angles = [], 0
+        for n, members in classes.items():
+            wl = members[0].with_steps(L)
+            eng = api.Engine(wl, path, "sp4")
+            eng.set_structures(np.stack([m.atoms for m in members]))
+            batch.add(eng, wl.theta0, wl.theta1)
+            engines.append(eng)
+            n_angles += len(members) * len(wl.theta0)
+        batch.run()                      # eager run + capture
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        batch.run()                      # graph replay
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = batch.stats()
+        out[name] = {"value": n_angles / (ms / 1e3), "unit": "angles/s", "ms": ms,
+                     "angles": n_angles, "slices": L, "path": path,
+                     "beam_classes": {str(n): len(m) for n, m in classes.items()},
+                     "graph_replay": st["graph_replay"], "launches": st["kernels_launched"],
+                     "wide_tile": st["wide_tile"]}
+        batch.close()
+        for e in engines:
+            e.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,6 +299,7 @@ def main():
                     help="override the slice count (small cases for profiling; not a bench line)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload lines")
     args = ap.parse_args()
     ws, rank, _ = _dist()
     wl = W.trhepd_n61()
@@ -326,6 +377,8 @@ def main():
         out["mixed_vs_fp64_curve_error"] = curve_error(res["mixed"]["eta"], res["fp64"]["eta"])
     if not args.no_grad:
         out["gradient"] = run_gradient(int(os.environ.get("LOCAL_RANK", "0")), args.slices)
+    if not args.no_batch:
+        out["batches"] = run_batches(args.slices)
     if ws == 1 and not args.no_cpu:
         n = args.cpu_angles or min(60, max(8, len(os.sched_getaffinity(0))))
         try:
