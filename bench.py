@@ -86,10 +86,8 @@ class Clocks:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2306_00271_gb300 import dist as D
+    return D.env()
 
 
 def cpu_baseline(wl, n_angles: int):
@@ -121,11 +119,10 @@ def algorithmic_flops(N: int, s_eff: int, L: int, n_angles: int, n_rhst_total: i
 
 def run_ours(args):
     import torch
+    from paper_2306_00271_gb300 import dist as D
     ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    D.init()
     from paper_2306_00271_gb300 import api
     wl = W.trhepd_n61()
     if args.slices:
@@ -172,10 +169,7 @@ def run_ours(args):
             rhst += st["rhst_total"]
         clk = clocks.stop()
         total_ms = float(np.sum(ms_steps))
-        if ws > 1:
-            tt = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(tt.item())
+        total_ms = D.max_over_ranks(total_ms)
         # end to end through the public API with host buffers: H2D of the step's inputs and
         # D2H of its outputs inside the timed region
         atoms_h = np.ascontiguousarray(wl.atoms)
