@@ -129,3 +129,17 @@ def test_full_rocking_curve_61_beams_sampled(api):
         idx = [0, 15, 37, 59]
         rho_o, eta_o, _, _ = rocking_curve(wl, "sp4", angles=idx)
         _check(rho[idx], eta[idx], rho_o, eta_o)
+
+
+def test_azimuth_scan_and_all_beams(api):
+    """A (theta0, theta1) grid: glancing angles x azimuths in one call (Section 2.1, eta as a
+    function of both directions), every beam's intensity checked."""
+    t0, t1 = np.meshgrid([0.9, 2.1, 3.6], [0.0, 12.5, 30.0, 47.0], indexing="ij")
+    wl = W.tiny(n_beams=19, seed=12, n_steps=80, depth=8.0).with_angles(t0.ravel(), t1.ravel())
+    eng = api.Engine(wl, "fp64", "sp4")
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    rho_o, eta_o, _, _ = rocking_curve(wl, "sp4")
+    _check(rho.cpu().numpy()[0], eta.cpu().numpy()[0], rho_o, eta_o)
+    # the azimuth matters: curves at different theta1 differ beyond rounding
+    e = eta.cpu().numpy()[0].reshape(3, 4, -1)
+    assert np.max(np.abs(e[:, 0] - e[:, 2])) > 1e-6 * np.max(np.abs(e))
