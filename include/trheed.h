@@ -57,7 +57,11 @@ extern "C" {
 enum trh_integrator {
   TRH_SP4 = 0, /* BAB splitting, SRKN_6^b coefficients (Section 3.4; 6 kicks per step with FSAL) */
   TRH_SP6 = 1, /* BAB splitting, SRKN_11^b coefficients (11 kicks per step with FSAL)            */
-  TRH_RK4 = 2  /* classical Runge-Kutta (Section 3.4)                                           */
+  TRH_RK4 = 2, /* classical Runge-Kutta (Section 3.4); FP64 path only                         */
+  TRH_CONVENTIONAL = 3 /* the conventional multi-slice method (Section 2.2): per-slice
+                          exponential at the slice midpoint and recursive reflection, the
+                          comparison point for the others; FP64 path only; the RHST threshold
+                          and RHST counts do not apply                                        */
 };
 
 enum trh_precision {

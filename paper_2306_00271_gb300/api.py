@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 TRH_OK, TRH_EINVAL, TRH_EGRAZING, TRH_ESINGULAR = 0, -1, -2, -3
 TRH_ETIMEOUT, TRH_ENOMEM, TRH_ECUDA, TRH_EUNSUPPORTED = -4, -5, -6, -7
-INTEGRATORS = {"sp4": 0, "sp6": 1, "rk4": 2}
+INTEGRATORS = {"sp4": 0, "sp6": 1, "rk4": 2, "conventional": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 

@@ -49,9 +49,9 @@ constexpr double kMc2 = 510998.95;       // electron rest energy, eV
 // SRKN_6^b and SRKN_11^b (Blanes & Moan 2002), the coefficients of the paper's sp4 / sp6.
 void bab_scheme(int integrator, trh::Scheme* s) {
   std::vector<double> a, b;
-  if (integrator == TRH_RK4) {
-    // classical Runge-Kutta: no splitting coefficients; two potential nodes per step (z_i and
-    // z_i + h/2), expressed as node fractions 0 and 1/2
+  if (integrator == TRH_RK4 || integrator == TRH_CONVENTIONAL) {
+    // classical Runge-Kutta and the conventional slice method: no splitting coefficients; two
+    // potential nodes per step (z_i and the midpoint z_i + h/2), as node fractions 0 and 1/2
     s->s = 2;
     s->a[0] = s->a[1] = 0.5;
     for (int i = 0; i <= 2; ++i) s->b[i] = 0.0;
@@ -207,12 +207,14 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
   if (p->n_species < 1 || !p->sf) return fail(TRH_EINVAL, "scattering factors are required");
   if (!(p->z_e < 0)) return fail(TRH_EINVAL, "z_e must be negative");
   if (p->n_steps < 1) return fail(TRH_EINVAL, "n_steps must be >= 1");
-  if (p->integrator != TRH_SP4 && p->integrator != TRH_SP6 && p->integrator != TRH_RK4)
+  if (p->integrator != TRH_SP4 && p->integrator != TRH_SP6 && p->integrator != TRH_RK4 &&
+      p->integrator != TRH_CONVENTIONAL)
     return fail(TRH_EINVAL, "unknown integrator");
   if (p->precision != TRH_FP64 && p->precision != TRH_MIXED)
     return fail(TRH_EINVAL, "unknown precision");
-  if (p->integrator == TRH_RK4 && p->precision != TRH_FP64)
-    return fail(TRH_EUNSUPPORTED, "RK4 runs on the FP64 path only");
+  if ((p->integrator == TRH_RK4 || p->integrator == TRH_CONVENTIONAL) &&
+      p->precision != TRH_FP64)
+    return fail(TRH_EUNSUPPORTED, "RK4 and the conventional method run on the FP64 path only");
   if (p->precision == TRH_MIXED && !trh::mixed_available())
     return fail(TRH_EUNSUPPORTED, "mixed path is not built in this library");
   if (p->precision == TRH_FP64 && p->n_beams > trh::kMaxBeamsWide)
@@ -471,7 +473,8 @@ static trh::IntegrateParams integrate_params(trh_ctx* c, int n_angles, size_t pa
   ip.L = c->L;
   ip.h = c->h;
   ip.threshold = c->threshold;
-  ip.method = c->integrator == TRH_RK4 ? trh::kMethodRK4 : trh::kMethodBAB;
+  ip.method = c->integrator == TRH_RK4 ? trh::kMethodRK4
+             : (c->integrator == TRH_CONVENTIONAL ? trh::kMethodConventional : trh::kMethodBAB);
   return ip;
 }
 
@@ -611,7 +614,8 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, rho, eta);
   int tile = 0;
   const bool wide = c->precision == TRH_FP64 &&
-                    (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4);
+                    (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4 ||
+                     c->integrator == TRH_CONVENTIONAL);
   if (wide) {
     TRH_CUDA(c->d_wide.ensure(pairs * trh::integrate_fp64_wide_state_bytes(c->N, ip.method) /
                               sizeof(double2)));
@@ -714,7 +718,7 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   if (c->n_free + c->n_classes < 1) return fail(TRH_EINVAL, "call trh_set_fit first");
   if (c->N > trh::kMaxBeamsFp64)
     return fail(TRH_EUNSUPPORTED, "the reverse sweep supports N <= %d", trh::kMaxBeamsFp64);
-  if (c->integrator == TRH_RK4)
+  if (c->integrator == TRH_RK4 || c->integrator == TRH_CONVENTIONAL)
     return fail(TRH_EUNSUPPORTED, "the reverse sweep supports the splitting integrators");
   int rc = upload_angles(c, n_angles, theta0, theta1, st);
   if (rc != TRH_OK) return rc;
@@ -1055,7 +1059,8 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
     J.generation = c->generation;
     b->total_pairs += pairs;
     const bool wide = c->precision == TRH_FP64 &&
-                      (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4);
+                      (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4 ||
+                     c->integrator == TRH_CONVENTIONAL);
     const int family = c->precision == TRH_MIXED ? 2 : (wide ? 1 : 0);
     const double cost = (double)c->N * c->N * c->N * c->L * c->scheme.s;
     for (int set = 0; set < c->n_sets; ++set)

@@ -269,6 +269,55 @@ __device__ void wide_rk4_step(WideSmem& S, double2* tbl, const IntegrateParams& 
   }
 }
 
+// out = base + A B for N x N complex matrices in global memory (base may be out itself or null;
+// out must not alias A or B), tile by tile on DMMA.
+template <int TB>
+__device__ void wide_gmm(WideSmem& S, const double2* A, const double2* B, double2* out,
+                         const double2* base, int N) {
+  using T = Tile<TB>;
+  constexpr int TLD = T::LD;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (N + TB - 1) / TB;
+  for (int jb = 0; jb < nb; ++jb)
+    for (int ib = 0; ib < nb; ++ib) {
+      double wr[T::S][4], wi[T::S][4];
+#pragma unroll
+      for (int s = 0; s < T::S; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wr[s][q] = wi[s][q] = 0.0;
+      for (int kb = 0; kb < nb; ++kb) {
+        for (int e = tid; e < TB * TB; e += WT) {
+          const int r = e / TB, k = e - r * TB;
+          const int ar = ib * TB + r, ak = kb * TB + k, br = kb * TB + r, bc = jb * TB + k;
+          double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+          if (ar < N && ak < N) a = A[(size_t)ar * N + ak];
+          if (br < N && bc < N) b = B[(size_t)br * N + bc];
+          S.Ar[r * TLD + k] = a.x;
+          S.Ai[r * TLD + k] = a.y;
+          S.Br[r * TLD + k] = b.x;
+          S.Bi[r * TLD + k] = b.y;
+        }
+        __syncthreads();
+        tile_gemm<TB>(S, wr, wi);
+        __syncthreads();
+      }
+      const int mt = warp % T::MW, nt = warp / T::MW, g = lane >> 2, t = lane & 3;
+#pragma unroll
+      for (int s = 0; s < T::S; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = ib * TB + 16 * mt + g + 8 * (q >> 1);
+          const int col = jb * TB + 8 * T::S * nt + 8 * s + 2 * t + (q & 1);
+          if (row < N && col < N) {
+            const size_t o = (size_t)row * N + col;
+            const double2 b0 = base ? base[o] : make_double2(0.0, 0.0);
+            out[o] = make_double2(b0.x + wr[s][q], b0.y + wi[s][q]);
+          }
+        }
+    }
+  __syncthreads();
+}
+
 // xi of Q (Varah bound); sets S.flag = (xi > threshold).
 __device__ void wide_badness(WideSmem& S, const double2* Q, int N, double threshold) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -378,6 +427,112 @@ __device__ void wide_gauss_jordan(WideSmem& S, double2* X, double2* Y, int N) {
   }
 }
 
+// The conventional multi-slice method (Section 2.2) as the comparison point for Algorithm 1:
+// per slice i, the exponential of h B at the slice midpoint m_i = z_i + h/2 (node 2i+1),
+//   exp(h B) = [[C, Sn], [-M Sn, C]],  C = cos(h sqrt M), Sn = sin(h sqrt M) / sqrt M,
+// both entire functions of M = U(m_i) + Gamma^2 summed as power series in -h^2 M until the terms'
+// bound falls below 1e-18 (instead of the eigendecomposition the paper's conventional code uses;
+// the results agree to rounding), then A^ = S exp(h B) S^{-1} with S = [[Gamma, -iI],
+// [Gamma, iI]] in blocks X, Y, Z, W (Eq. ichimiya1), and the recursive reflection
+// R_i = (Z + W R_{i-1})(X + Y R_{i-1})^{-1}, R_{-1} = 0 (Eqs. ri1, ri2); rho(0) = R_{L-1} e_1.
+// Scratch (5 N x N): R, the series power, C, Sn and -M Sn; X, Y, Z, W reuse them in place.
+template <int TB>
+__device__ void wide_conventional(WideSmem& S, double2* tbl, const IntegrateParams& p, int set,
+                                  double2* Z) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = p.N;
+  const size_t NN = (size_t)N * N;
+  double2 *R = Z, *Pw = Z + NN, *K = Pw + NN, *Cm = K + NN, *Sn = Cm + NN;
+  const double h = p.h, h2 = h * h;
+  for (size_t e = tid; e < NN; e += WT) R[e] = make_double2(0.0, 0.0);
+  // |Gamma_j^2| bound for the series' truncation
+  double gmax = 0.0;
+  for (int j = tid; j < N; j += WT) gmax = fmax(gmax, fabs(S.gam2[j]));
+  for (int i = 0; i < p.L && S.status == kOk; ++i) {
+    load_table(tbl, p, set, 2 * i + 1);
+    double us = 0.0;
+    for (int m = tid; m < p.M; m += WT) us += sqrt(tbl[m].x * tbl[m].x + tbl[m].y * tbl[m].y);
+    us = wsum(us);
+    double gm = gmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if (lane == 0) {
+      S.red0[warp] = us;
+      S.red1[warp] = gm;
+    }
+    for (size_t e = tid; e < NN; e += WT) {
+      const int r = (int)(e / N), c = (int)(e - (size_t)r * N);
+      const double d = (r == c) ? 1.0 : 0.0;
+      Pw[e] = make_double2(d, 0.0);
+      Cm[e] = make_double2(d, 0.0);
+      Sn[e] = make_double2(h * d, 0.0);
+    }
+    __syncthreads();
+    double norm = 0.0;   // bound on || M ||_inf
+    for (int w = 0; w < WT / 32; ++w) norm = fmax(norm, S.red1[w]);
+    {
+      double t = 0.0;
+      for (int w = 0; w < WT / 32; ++w) t += S.red0[w];
+      norm += t;
+    }
+    const double x = h2 * norm;
+    double term = 1.0, fc = 1.0, fs = 1.0;   // x^k / (2k)!, (2k)!, (2k+1)!
+    for (int k = 1; k <= 60; ++k) {
+      wide_stage<TB>(S, tbl, p.lmap, Pw, K, N);      // K = -M Pw
+      fc *= (2.0 * k - 1.0) * (2.0 * k);
+      fs *= (2.0 * k) * (2.0 * k + 1.0);
+      const double ic = 1.0 / fc, is = h / fs;
+      for (size_t e = tid; e < NN; e += WT) {
+        const double2 kv = K[e];
+        const double2 pw = make_double2(h2 * kv.x, h2 * kv.y);   // (-h^2 M)^k
+        Pw[e] = pw;
+        const double2 c = Cm[e], sn = Sn[e];
+        Cm[e] = make_double2(c.x + ic * pw.x, c.y + ic * pw.y);
+        Sn[e] = make_double2(sn.x + is * pw.x, sn.y + is * pw.y);
+      }
+      __syncthreads();
+      term *= x / ((2.0 * k - 1.0) * (2.0 * k));
+      if (term < 1e-18) break;
+    }
+    wide_stage<TB>(S, tbl, p.lmap, Sn, K, N);         // K = -M Sn
+    // blocks of S exp(hB) S^{-1}, in place: X -> Pw, Y -> Cm, Z -> Sn, W -> K
+    for (size_t e = tid; e < NN; e += WT) {
+      const int j = (int)(e / N), k = (int)(e - (size_t)j * N);
+      const double2 c = Cm[e], sn = Sn[e], kv = K[e];   // M Sn = -kv
+      const double gjr = S.Gr[j], gji = S.Gi[j];
+      // (Gamma_j C +- i M Sn) / (2 Gamma_k)
+      const double acr = gjr * c.x - gji * c.y, aci = gjr * c.y + gji * c.x;   // Gamma_j C
+      const double imr = kv.y, imi = -kv.x;                                    // i M Sn = -i kv
+      const double dr = 2.0 * S.Gr[k], di = 2.0 * S.Gi[k], dd = dr * dr + di * di;
+      auto divg = [&](double ar, double ai) {
+        return make_double2((ar * dr + ai * di) / dd, (ai * dr - ar * di) / dd);
+      };
+      const double2 p1 = divg(acr + imr, aci + imi);   // (Gamma C + i M Sn) (2 Gamma)^{-1}
+      const double2 p2 = divg(acr - imr, aci - imi);   // (Gamma C - i M Sn) (2 Gamma)^{-1}
+      // (i/2) Gamma_j Sn
+      const double gsr = gjr * sn.x - gji * sn.y, gsi = gjr * sn.y + gji * sn.x;
+      const double hr = -0.5 * gsi, hi = 0.5 * gsr;
+      const double cr2 = 0.5 * c.x, ci2 = 0.5 * c.y;
+      Pw[e] = make_double2(p1.x + hr + cr2, p1.y + hi + ci2);   // X
+      Cm[e] = make_double2(p1.x - hr - cr2, p1.y - hi - ci2);   // Y
+      Sn[e] = make_double2(p2.x + hr - cr2, p2.y + hi - ci2);   // Z
+      K[e] = make_double2(p2.x - hr + cr2, p2.y - hi + ci2);    // W
+    }
+    __syncthreads();
+    wide_gmm<TB>(S, Cm, R, Pw, Pw, N);   // G = X + Y R
+    wide_gmm<TB>(S, K, R, Sn, Sn, N);    // H = Z + W R
+    wide_gauss_jordan(S, Pw, Sn, N);     // Sn <- H G^{-1}
+    if (S.status != kOk) break;
+    double2* t = R;                      // R_i = H G^{-1}
+    R = Sn;
+    Sn = t;
+  }
+  // rho = R e_1: copy the first column into Sn's storage for the common output code
+  __syncthreads();
+  if (R != Z)
+    for (size_t e = tid; e < NN; e += WT) Z[e] = R[e];
+  __syncthreads();
+}
+
 // Integrates one (set, angle) pair of `p` with its state block Z (Q, P and, for RK4, four more
 // N x N scratch matrices).
 template <int TB>
@@ -411,6 +566,28 @@ __device__ void wide_pair(WideSmem& S, double2* tbl, const IntegrateParams& p, i
     S.Gi[j] = gi;
   }
   __syncthreads();
+  if (p.method == kMethodConventional) {
+    if (S.status == kOk) wide_conventional<TB>(S, tbl, p, set, Z);
+    __syncthreads();
+    const double g1c = sqrt(S.gam2[0]);
+    for (int j = tid; j < N; j += WT) {
+      double2 rho = make_double2(NAN, NAN);
+      double eta = NAN;
+      if (S.status == kOk) {
+        rho = Z[(size_t)j * N];            // R e_1
+        const double g2 = S.gam2[j];
+        eta = (g2 > 0.0) ? (rho.x * rho.x + rho.y * rho.y) * S.sin_t0 * g1c / sqrt(g2) : 0.0;
+      }
+      p.out.rho[pair * N + j] = rho;
+      p.out.eta[pair * N + j] = eta;
+    }
+    if (tid == 0) {
+      p.out.status[pair] = S.status;
+      p.out.n_rhst[pair] = 0;
+    }
+    __syncthreads();
+    return;
+  }
   // initial value [I; i Gamma]
   for (size_t e = tid; e < NN; e += WT) {
     const int r = (int)(e / N), c = (int)(e - (size_t)r * N);
@@ -519,7 +696,7 @@ __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide_items(
 }  // namespace
 
 size_t integrate_fp64_wide_state_bytes(int N, int method) {
-  return (method == kMethodRK4 ? 6 : 2) * (size_t)N * N * sizeof(double2);
+  return (method == kMethodBAB ? 2 : 6) * (size_t)N * N * sizeof(double2);
 }
 
 cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, int tile,
@@ -530,7 +707,7 @@ cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state,
                               : (const void*)k_integrate_fp64_wide<32>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  WideArgs w{p, state, p.method == kMethodRK4 ? 6 : 2};
+  WideArgs w{p, state, p.method == kMethodBAB ? 2 : 6};
   const dim3 grid(p.ang.n_angles, p.n_sets);
   if (tile == 64) k_integrate_fp64_wide<64><<<grid, WT, smem, st>>>(w);
   else k_integrate_fp64_wide<32><<<grid, WT, smem, st>>>(w);

@@ -13,6 +13,7 @@ constexpr int kMaxBeamsWide = 256;   // FP64 path with the state in global memor
 // Integration methods of the kernels (IntegrateParams::method).
 constexpr int kMethodBAB = 0;        // splitting scheme (Scheme), FSAL-merged
 constexpr int kMethodRK4 = 1;        // classical Runge-Kutta (wide FP64 kernel only)
+constexpr int kMethodConventional = 2;  // conventional multi-slice with recursive reflection
 
 // Status words written by kernels (mirrors the TRH_E* codes of trheed.h).
 enum DevStatus : int {

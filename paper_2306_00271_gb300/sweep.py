@@ -1,6 +1,7 @@
 """Step-size sweep: accuracy against time for the integrators (Section 4's time-error study).
 
-For each integrator (sp4 = SRKN_6^b, sp6 = SRKN_11^b, rk4) and precision path, the slab is
+For each method (the conventional multi-slice method of Section 2.2 as the comparison point, and
+Algorithm 1 with sp4 = SRKN_6^b, sp6 = SRKN_11^b, rk4) and precision path, the slab is
 integrated at the step sizes dz of the E-6 series 0.010 ... 0.68 A, and the rocking curve's error
 is measured against a fine reference (sp6, FP64, half the smallest step) with the paper's
 curve error: the maximum over angles of the Euclidean norm of the intensity difference over
@@ -52,8 +53,8 @@ def run(workload: str = "trhepd_n61", n_angles: int = 60, runs=None):
     depth = -base.z_e
     ref_L = int(round(depth / (E6[0] / 2)))
     ref, ref_ms, _, _ = _curve(api, base.with_steps(ref_L), "fp64", "sp6")
-    runs = runs or [("fp64", "sp4"), ("fp64", "sp6"), ("fp64", "rk4"), ("mixed", "sp4"),
-                    ("mixed", "sp6")]
+    runs = runs or [("fp64", "conventional"), ("fp64", "sp4"), ("fp64", "sp6"), ("fp64", "rk4"),
+                    ("mixed", "sp4"), ("mixed", "sp6")]
     rows = []
     for precision, integrator in runs:
         for dz in E6:

@@ -101,3 +101,15 @@ def test_rk4_in_a_batch(api):
     rho_o, eta_o, _, _ = rocking_curve(wl, "rk4")
     _check(rho.cpu().numpy()[0], eta.cpu().numpy()[0], rho_o, eta_o)
     batch.close()
+
+
+@pytest.mark.parametrize("n_beams", [7, 37, 91])
+def test_conventional_method_against_oracle(api, n_beams):
+    """The conventional multi-slice method (Section 2.2, recursive reflection) on the GPU against
+    the oracle's O1 (eigendecomposition route): same slices and midpoints, so they agree to
+    rounding."""
+    wl = W.tiny(n_beams=n_beams, seed=70 + n_beams, n_steps=80, theta0=(0.8, 2.7), depth=8.0)
+    eng = api.Engine(wl, "fp64", "conventional")
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    rho_o, eta_o, _, _ = rocking_curve(wl, "conventional")
+    _check(rho.cpu().numpy()[0], eta.cpu().numpy()[0], rho_o, eta_o)
