@@ -193,6 +193,7 @@ __device__ void gj_invert(Smem& S, float2* T, int n) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int col = tid & 63, rg = tid >> 6;  // 8 row groups
   for (int k = 0; k < n; ++k) {
+    // warp 0: pivot row, then the scaled pivot row, the multipliers and the old row k
     if (warp == 0) {
       float best = -1.0f;
       int bi = k;
@@ -213,40 +214,47 @@ __device__ void gj_invert(Smem& S, float2* T, int n) {
           bi = i2;
         }
       }
+      const int pr = bi;
       if (lane == 0) {
-        S.piv[k] = bi;
+        S.piv[k] = pr;
         if (!(best > 0.0f) || !isfinite(best)) S.status = kSingular;
+      }
+      // any invertible T is a valid RHST (Section 3.2): the reciprocal needs no correction step
+      const float2 a = T[pr * TS + k];
+      const float id = __frcp_rn(a.x * a.x + a.y * a.y);
+      const float2 inv = make_float2(a.x * id, -a.y * id);
+      for (int c = lane; c < n; c += 32) {
+        const float2 t = T[pr * TS + c];
+        S.frow[c] = (c == k) ? inv : make_float2(t.x * inv.x - t.y * inv.y,
+                                                 t.x * inv.y + t.y * inv.x);
+        // row r's multiplier: rows k and pr trade places
+        const int src = (c == k) ? pr : (c == pr ? k : c);
+        S.fcol[c] = (c == k) ? make_float2(0.f, 0.f) : T[src * TS + k];
+        S.oldk[c] = T[k * TS + c];  // old row k, overwritten by the pivot row below
       }
     }
     __syncthreads();
     if (S.status != kOk) return;
     const int pr = S.piv[k];
-    // pivot row (after the interchange) scaled by 1/pivot, and column k (before the update)
-    if (tid < n) {
-      const float2 a = T[pr * TS + k];
-      const float d = a.x * a.x + a.y * a.y;
-      const float2 inv = make_float2(a.x / d, -a.y / d);
-      const float2 t = T[pr * TS + tid];
-      S.frow[tid] = (tid == k) ? inv
-                               : make_float2(t.x * inv.x - t.y * inv.y, t.x * inv.y + t.y * inv.x);
-      // row r's multiplier: rows k and pr trade places
-      const int src = (tid == k) ? pr : (tid == pr ? k : tid);
-      S.fcol[tid] = (tid == k) ? make_float2(0.f, 0.f) : T[src * TS + k];
-      S.oldk[tid] = T[k * TS + tid];  // old row k, overwritten by the pivot row below
-    }
-    __syncthreads();
     if (col < n) {
-      const float2 fr = S.frow[col];
-      // the interchange: old row k moves to pr, old row pr becomes the new pivot row k
-      for (int r = rg; r < n; r += 8) {
-        if (r == k) {
-          T[k * TS + col] = fr;
-        } else {
-          const float2 fc = S.fcol[r];
-          float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? S.oldk[col] : T[r * TS + col]);
-          t.x -= fc.x * fr.x - fc.y * fr.y;
-          t.y -= fc.x * fr.y + fc.y * fr.x;
-          T[r * TS + col] = t;
+      // the interchange: old row k moves to pr, old row pr becomes the new pivot row k; all of
+      // this thread's loads first (its rows and column are its own), then the updates
+      const float2 fr = S.frow[col], ok = S.oldk[col];
+      float2 tv[8], fc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rg + 8 * i;
+        tv[i] = (r < n) ? T[r * TS + col] : make_float2(0.f, 0.f);
+        fc[i] = (r < n) ? S.fcol[r] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rg + 8 * i;
+        if (r < n) {
+          float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? ok : tv[i]);
+          t.x -= fc[i].x * fr.x - fc[i].y * fr.y;
+          t.y -= fc[i].x * fr.y + fc[i].y * fr.x;
+          T[r * TS + col] = (r == k) ? fr : t;
         }
       }
     }
