@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(NT, 1) k_grad_recompute(GradParams g) {
 }
 
 // Adjoint seed from the final state [Q; P] in the Q/P planes; leaves [Qbar; Pbar] there.
-__device__ void adjoint_seed(Smem& S, int N) {
+__device__ __forceinline__ void adjoint_seed(Smem& S, int N) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < N * N; e += NT) {
     const int j = e / N, k = e - j * N, o = j * LD + k;
@@ -162,7 +162,7 @@ __device__ void adjoint_seed(Smem& S, int N) {
 }
 
 // Qbar <- Qbar - c (U^H + Gamma^2) Pbar with U(tau_n) in the U planes.
-__device__ void kick_adjoint(Smem& S, int N, double c) {
+__device__ __forceinline__ void kick_adjoint(Smem& S, int N, double c) {
   double wr[4][4], wi[4][4];
   cgemm<true, true, false, false>(S.Ur, S.Ui, S.Pr, S.Pi, N, wr, wi);
   if (tile_active(N)) {
@@ -184,7 +184,7 @@ __device__ void kick_adjoint(Smem& S, int N, double c) {
 
 // Reverse of the RHST ending step c of the segment: project onto Zbar^H Z = 0, then
 // Zbar <- Zbar Q_pre^{-H}.
-__device__ void rhst_adjoint(Smem& S, int N, const double2* qpre, const double2* x) {
+__device__ __forceinline__ void rhst_adjoint(Smem& S, int N, const double2* qpre, const double2* x) {
   load_mat(S.Ur, S.Ui, x, N);
   __syncthreads();
   double wr[4][4], wi[4][4];

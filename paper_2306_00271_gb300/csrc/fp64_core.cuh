@@ -125,7 +125,7 @@ __device__ __forceinline__ void load_mat(double* Sr, double* Si, const double2* 
 
 // One kick P <- P - h b (U Q + Gamma^2 Q) at the U currently in shared memory, the drift
 // Q <- Q + h a P fused into its epilogue (if do_drift), and the gather of U(next_node) (if >= 0).
-__device__ void kick_drift(Smem& S, const IntegrateParams& p, int set, double coef, double adrift,
+__device__ __forceinline__ void kick_drift(Smem& S, const IntegrateParams& p, int set, double coef, double adrift,
                            bool do_drift, int next_node) {
   const int N = p.N;
   double wr[4][4], wi[4][4];
@@ -178,7 +178,7 @@ __device__ __forceinline__ void warp_argmax(double& val, int& idx) {
 
 // xi = max_i sum_j |q_ij| / min_i (|q_ii| - sum_{j != i} |q_ij|); sets S.flag = (xi > threshold)
 // (a non-positive denominator means xi = infinity).
-__device__ void badness(Smem& S, const IntegrateParams& p) {
+__device__ __forceinline__ void badness(Smem& S, const IntegrateParams& p) {
   const int N = p.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double rowmax = 0.0, minmargin = INFINITY;
@@ -224,7 +224,7 @@ struct Blocks {
 // identity and every other block as B_k B0^{-1}. The forward RHST (Section 3.2) is the case
 // [Q; P]; the reverse sweep uses [Q_pre^H; Qbar; Pbar].
 template <int NB>
-__device__ void gauss_jordan_right(Smem& S, const Blocks<NB>& Z, int N) {
+__device__ __forceinline__ void gauss_jordan_right(Smem& S, const Blocks<NB>& Z, int N) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int R = NB * N;
   for (int k = 0; k < N; ++k) {
@@ -296,7 +296,7 @@ __device__ void gauss_jordan_right(Smem& S, const Blocks<NB>& Z, int N) {
 }
 
 // RHST: Z <- Z Q^{-1}, then Q <- I exactly.
-__device__ void rhst(Smem& S, const IntegrateParams& p) {
+__device__ __forceinline__ void rhst(Smem& S, const IntegrateParams& p) {
   const int N = p.N;
   Blocks<2> Z{{S.Qr, S.Pr}, {S.Qi, S.Pi}};
   gauss_jordan_right<2>(S, Z, N);
@@ -311,7 +311,7 @@ __device__ void rhst(Smem& S, const IntegrateParams& p) {
 
 // Solves A x = y for the N x N complex A in the U planes (destroyed) and y in (yr, yi)
 // (destroyed) by Gaussian elimination with partial pivoting; x lands in (fr, fi).
-__device__ void gauss_solve(Smem& S, int N) {
+__device__ __forceinline__ void gauss_solve(Smem& S, int N) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k < N; ++k) {
     if (warp == 0) {
@@ -407,7 +407,7 @@ __device__ void gauss_solve(Smem& S, int N) {
 // |b0 + k_j|^2, Gamma_j = sqrt(.) or -i sqrt(-.) (the evanescent modes decay away from the slab).
 // Zeroes all six planes, fills gam2 / Gr / Gi and S.sin_t0, and (if init_state) writes the
 // initial value [I; i Gamma] (Algorithm 1's S \ [I; O] times 2 Gamma) into Q, P.
-__device__ void setup_angle(Smem& S, const AngleInputs& ang, int angle, int N, bool init_state) {
+__device__ __forceinline__ void setup_angle(Smem& S, const AngleInputs& ang, int angle, int N, bool init_state) {
   const int tid = threadIdx.x;
   for (int e = tid; e < NP * LD; e += NT) {
     S.Ur[e] = S.Ui[e] = S.Qr[e] = S.Qi[e] = S.Pr[e] = S.Pi[e] = 0.0;

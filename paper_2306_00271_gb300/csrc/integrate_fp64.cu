@@ -22,7 +22,7 @@ using namespace fp64;
 
 // rho = (Gamma Q + i P) x, (Gamma Q - i P) x = e_1; eta of Section 2.1. Uses the U planes as
 // workspace for A = Gamma Q - i P.
-__device__ void assemble(Smem& S, const IntegrateParams& p, size_t pair, double sin_t0) {
+__device__ __forceinline__ void assemble(Smem& S, const IntegrateParams& p, size_t pair, double sin_t0) {
   const int N = p.N;
   const int tid = threadIdx.x;
   for (int e = tid; e < N * N; e += NT) {
@@ -66,7 +66,7 @@ __device__ __forceinline__ void write_checkpoint(const Smem& S, const IntegrateP
 }
 
 // Integrates one (set, angle) pair of `p` and writes rho, eta, status and the RHST count.
-__device__ void integrate_pair(Smem& S, const IntegrateParams& p, int angle, int set) {
+__device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p, int angle, int set) {
   const int tid = threadIdx.x;
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;

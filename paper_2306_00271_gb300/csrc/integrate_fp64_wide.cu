@@ -97,7 +97,7 @@ struct WideArgs {
 // One kick with coefficient hb and (if do_drift) the drift with ha, for the table in shared
 // memory.
 template <int TB>
-__device__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, double2* Q, double2* P,
+__device__ __forceinline__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, double2* Q, double2* P,
                           int N, double hb, double ha, bool do_drift) {
   using T = Tile<TB>;
   constexpr int TLD = T::LD;
@@ -167,7 +167,7 @@ __device__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, doub
   }
 }
 
-__device__ void load_table(double2* tbl, const IntegrateParams& p, int set, int node) {
+__device__ __forceinline__ void load_table(double2* tbl, const IntegrateParams& p, int set, int node) {
   const double2* un = p.u + ((size_t)set * p.n_nodes + node) * p.M;
   for (int m = threadIdx.x; m < p.M; m += WT) tbl[m] = __ldg(un + m);
 }
@@ -175,7 +175,7 @@ __device__ void load_table(double2* tbl, const IntegrateParams& p, int set, int 
 // K = -(U + Gamma^2) X for the table in shared memory (a classical Runge-Kutta stage; Section
 // 3.4 writes the ODE as Z' = B Z, whose lower block is -(U + Gamma^2) Q). X is not modified.
 template <int TB>
-__device__ void wide_stage(WideSmem& S, const double2* tbl, const int* lmap, const double2* X,
+__device__ __forceinline__ void wide_stage(WideSmem& S, const double2* tbl, const int* lmap, const double2* X,
                            double2* K, int N) {
   using T = Tile<TB>;
   constexpr int TLD = T::LD;
@@ -229,7 +229,7 @@ __device__ void wide_stage(WideSmem& S, const double2* tbl, const int* lmap, con
 // M at z_i (node 2i), z_i + h/2 (node 2i+1, stages 2 and 3) and z_i + h (node 2i+2).
 // Scratch after Q, P: X, K, dP (= k_1 + 2 k_2 + ...), dQ (= k_1 + k_2 + ...).
 template <int TB>
-__device__ void wide_rk4_step(WideSmem& S, double2* tbl, const IntegrateParams& p, int set,
+__device__ __forceinline__ void wide_rk4_step(WideSmem& S, double2* tbl, const IntegrateParams& p, int set,
                               int i, double2* Q, double2* P) {
   const int tid = threadIdx.x, N = p.N;
   const size_t NN = (size_t)N * N;
@@ -272,7 +272,7 @@ __device__ void wide_rk4_step(WideSmem& S, double2* tbl, const IntegrateParams& 
 // out = base + A B for N x N complex matrices in global memory (base may be out itself or null;
 // out must not alias A or B), tile by tile on DMMA.
 template <int TB>
-__device__ void wide_gmm(WideSmem& S, const double2* A, const double2* B, double2* out,
+__device__ __forceinline__ void wide_gmm(WideSmem& S, const double2* A, const double2* B, double2* out,
                          const double2* base, int N) {
   using T = Tile<TB>;
   constexpr int TLD = T::LD;
@@ -319,7 +319,7 @@ __device__ void wide_gmm(WideSmem& S, const double2* A, const double2* B, double
 }
 
 // xi of Q (Varah bound); sets S.flag = (xi > threshold).
-__device__ void wide_badness(WideSmem& S, const double2* Q, int N, double threshold) {
+__device__ __forceinline__ void wide_badness(WideSmem& S, const double2* Q, int N, double threshold) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double rowmax = 0.0, minmargin = INFINITY;
   for (int r = warp; r < N; r += WT / 32) {
@@ -355,7 +355,7 @@ __device__ void wide_badness(WideSmem& S, const double2* Q, int N, double thresh
 // [X; Y] <- [X; Y] X^{-1} by Gauss-Jordan elimination with column operations and pivoting along
 // the rows of X (both N x N complex, row-major in global memory): X ends as the identity (up to
 // the discarded pivot columns) and Y as Y X^{-1}.
-__device__ void wide_gauss_jordan(WideSmem& S, double2* X, double2* Y, int N) {
+__device__ __forceinline__ void wide_gauss_jordan(WideSmem& S, double2* X, double2* Y, int N) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k < N; ++k) {
     if (warp == 0) {
@@ -437,7 +437,7 @@ __device__ void wide_gauss_jordan(WideSmem& S, double2* X, double2* Y, int N) {
 // R_i = (Z + W R_{i-1})(X + Y R_{i-1})^{-1}, R_{-1} = 0 (Eqs. ri1, ri2); rho(0) = R_{L-1} e_1.
 // Scratch (5 N x N): R, the series power, C, Sn and -M Sn; X, Y, Z, W reuse them in place.
 template <int TB>
-__device__ void wide_conventional(WideSmem& S, double2* tbl, const IntegrateParams& p, int set,
+__device__ __forceinline__ void wide_conventional(WideSmem& S, double2* tbl, const IntegrateParams& p, int set,
                                   double2* Z) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = p.N;
   const size_t NN = (size_t)N * N;
@@ -536,7 +536,7 @@ __device__ void wide_conventional(WideSmem& S, double2* tbl, const IntegratePara
 // Integrates one (set, angle) pair of `p` with its state block Z (Q, P and, for RK4, four more
 // N x N scratch matrices).
 template <int TB>
-__device__ void wide_pair(WideSmem& S, double2* tbl, const IntegrateParams& p, int angle, int set,
+__device__ __forceinline__ void wide_pair(WideSmem& S, double2* tbl, const IntegrateParams& p, int angle, int set,
                           double2* Z) {
   const int tid = threadIdx.x, N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;

@@ -189,92 +189,78 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 // In-place inverse of the n x n complex FP32 matrix T (row stride TS) by Gauss-Jordan elimination
 // with row pivoting; the row interchanges are undone on the columns in reverse order at the end.
 // Thread t owns column t % 64 and rows t / 64, t / 64 + 8, ... (no index division in the update).
-__device__ __forceinline__ void gj_bar() {  // the 4 eliminating warps only (barrier 1)
-  asm volatile("bar.sync 1, 128;\n" ::: "memory");
-}
-
-__device__ void gj_invert(Smem& S, float2* T, int n) {
+// Inlined so that T and S stay shared-space pointers (shared loads and stores rather than generic).
+__device__ __forceinline__ void gj_invert(Smem& S, float2* T, int n) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // Warps 0-3 eliminate (thread t: column t % 64, rows t / 64, t / 64 + 2, ...) and meet at a
-  // named barrier; the other warps wait at the block barrier below. Few warps keep the
-  // per-step barrier cheap, and the per-step work (one rank-1 update of a 64 x 64 block) is
-  // small enough for them.
-  if (warp < 4) {
-    const int col = tid & 63, rg = tid >> 6;  // 2 row groups
-    for (int k = 0; k < n; ++k) {
-      // warp 0: pivot row, then the scaled pivot row, the multipliers and the old row k
-      if (warp == 0) {
-        float best = -1.0f;
-        int bi = k;
-        for (int r = k + lane; r < n; r += 32) {
-          const float2 a = T[r * TS + k];
-          const float m2 = a.x * a.x + a.y * a.y;
-          if (m2 > best) {
-            best = m2;
-            bi = r;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
-          const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (v2 > best || (v2 == best && i2 < bi)) {
-            best = v2;
-            bi = i2;
-          }
-        }
-        const int pr = bi;
-        if (lane == 0) {
-          S.piv[k] = pr;
-          if (!(best > 0.0f) || !isfinite(best)) S.status = kSingular;
-        }
-        // any invertible T is a valid RHST (Section 3.2): the reciprocal needs no correction
-        const float2 a = T[pr * TS + k];
-        const float id = __frcp_rn(a.x * a.x + a.y * a.y);
-        const float2 inv = make_float2(a.x * id, -a.y * id);
-        for (int c = lane; c < n; c += 32) {
-          const float2 t = T[pr * TS + c];
-          S.frow[c] = (c == k) ? inv : make_float2(t.x * inv.x - t.y * inv.y,
-                                                   t.x * inv.y + t.y * inv.x);
-          // row r's multiplier: rows k and pr trade places
-          const int src = (c == k) ? pr : (c == pr ? k : c);
-          S.fcol[c] = (c == k) ? make_float2(0.f, 0.f) : T[src * TS + k];
-          S.oldk[c] = T[k * TS + c];  // old row k, overwritten by the pivot row below
+  const int col = tid & 63, rg = tid >> 6;  // 8 row groups
+  for (int k = 0; k < n; ++k) {
+    // warp 0: pivot row, then the scaled pivot row, the multipliers and the old row k
+    if (warp == 0) {
+      float best = -1.0f;
+      int bi = k;
+      for (int r = k + lane; r < n; r += 32) {
+        const float2 a = T[r * TS + k];
+        const float m2 = a.x * a.x + a.y * a.y;
+        if (m2 > best) {
+          best = m2;
+          bi = r;
         }
       }
-      gj_bar();
-      if (S.status != kOk) break;
-      const int pr = S.piv[k];
-      if (col < n) {
-        // the interchange: old row k moves to pr, old row pr becomes the new pivot row k;
-        // loads of a chunk of this thread's rows first (its rows and column are its own)
-        const float2 fr = S.frow[col], ok = S.oldk[col];
 #pragma unroll
-        for (int r0 = rg; r0 < 64; r0 += 16) {
-          float2 tv[8], fc[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int r = r0 + 2 * i;
-            tv[i] = (r < n) ? T[r * TS + col] : make_float2(0.f, 0.f);
-            fc[i] = (r < n) ? S.fcol[r] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int r = r0 + 2 * i;
-            if (r < n) {
-              float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? ok : tv[i]);
-              t.x -= fc[i].x * fr.x - fc[i].y * fr.y;
-              t.y -= fc[i].x * fr.y + fc[i].y * fr.x;
-              T[r * TS + col] = (r == k) ? fr : t;
-            }
-          }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > best || (v2 == best && i2 < bi)) {
+          best = v2;
+          bi = i2;
         }
       }
-      gj_bar();
+      const int pr = bi;
+      if (lane == 0) {
+        S.piv[k] = pr;
+        if (!(best > 0.0f) || !isfinite(best)) S.status = kSingular;
+      }
+      // any invertible T is a valid RHST (Section 3.2): the reciprocal needs no correction step
+      const float2 a = T[pr * TS + k];
+      const float id = __frcp_rn(a.x * a.x + a.y * a.y);
+      const float2 inv = make_float2(a.x * id, -a.y * id);
+      for (int c = lane; c < n; c += 32) {
+        const float2 t = T[pr * TS + c];
+        S.frow[c] = (c == k) ? inv : make_float2(t.x * inv.x - t.y * inv.y,
+                                                 t.x * inv.y + t.y * inv.x);
+        // row r's multiplier: rows k and pr trade places
+        const int src = (c == k) ? pr : (c == pr ? k : c);
+        S.fcol[c] = (c == k) ? make_float2(0.f, 0.f) : T[src * TS + k];
+        S.oldk[c] = T[k * TS + c];  // old row k, overwritten by the pivot row below
+      }
     }
+    __syncthreads();
+    if (S.status != kOk) return;
+    const int pr = S.piv[k];
+    if (col < n) {
+      // the interchange: old row k moves to pr, old row pr becomes the new pivot row k; all of
+      // this thread's loads first (its rows and column are its own), then the updates
+      const float2 fr = S.frow[col], ok = S.oldk[col];
+      float2 tv[8], fc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rg + 8 * i;
+        tv[i] = (r < n) ? T[r * TS + col] : make_float2(0.f, 0.f);
+        fc[i] = (r < n) ? S.fcol[r] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rg + 8 * i;
+        if (r < n) {
+          float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? ok : tv[i]);
+          t.x -= fc[i].x * fr.x - fc[i].y * fr.y;
+          t.y -= fc[i].x * fr.y + fc[i].y * fr.x;
+          T[r * TS + col] = (r == k) ? fr : t;
+        }
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (S.status != kOk) return;
   for (int k = n - 1; k >= 0; --k) {
     const int pr = S.piv[k];
     if (pr != k) {
