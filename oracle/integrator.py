@@ -122,8 +122,10 @@ def _magnus2_step(Q, P, z_i, h, gam2, Ufun):
 
 
 def integrate(Gam, gam2, Ufun, z_e: float, L: int, scheme: str = "sp4",
-              threshold: float = 1000.0, rhst: bool = True, Z0=None, one_sided: bool = False):
-    """Algorithm 1's loop: returns (Q, P, n_rhst) at z = 0.
+              threshold: float = 1000.0, rhst: bool = True, Z0=None, one_sided: bool = False,
+              span=None):
+    """Algorithm 1's loop: returns (Q, P, n_rhst) at z = 0 (at z_e + span if ``span`` is given:
+    one bulk period for the bulk-layer treatment of Section 2.2).
 
     Ufun(z) -> (n, n) complex U(z). ``threshold`` is the RHST threshold on xi (xi > threshold
     triggers Z <- Z Q^{-1}); ``rhst=False`` disables the transform altogether. ``one_sided``
@@ -131,7 +133,7 @@ def integrate(Gam, gam2, Ufun, z_e: float, L: int, scheme: str = "sp4",
     at slice boundaries; smooth potentials do not need it).
     """
     n = Gam.shape[0]
-    h = -z_e / L
+    h = (-z_e if span is None else float(span)) / L
     gam2 = np.asarray(gam2, dtype=np.float64)
     if Z0 is None:
         Q = np.eye(n, dtype=np.complex128)
