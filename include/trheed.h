@@ -52,6 +52,7 @@ extern "C" {
 #define TRH_ENOMEM       -5  /* device or host allocation failed                                 */
 #define TRH_ECUDA        -6  /* CUDA runtime error (including: no device)                        */
 #define TRH_EUNSUPPORTED -7  /* valid request this build does not implement                      */
+#define TRH_ENOCONV      -8  /* the bulk boundary condition did not converge in max_periods       */
 
 /* ---- method selection --------------------------------------------------------------------- */
 enum trh_integrator {
@@ -118,6 +119,9 @@ typedef struct trh_stats {
   int wide_tile;          /* tile edge the autotuner chose for the wide FP64 kernel (N > 64) of
                              the last call, 0 if that kernel did not run                         */
   int graph_replay;       /* trh_batch_run: 1 if the work was replayed from the captured graph   */
+  int bulk_periods;       /* bulk periods the last bulk computation needed (largest over angles;
+                             0 without a bulk or when the cached one was reused)                 */
+  double ms_bulk;         /* device time of that bulk computation (0 if none ran)               */
 } trh_stats;
 
 /* Create a context for one beam set and method. Validates and copies `p` (the caller may free
@@ -155,6 +159,27 @@ int trh_set_structure(trh_ctx* ctx, int n_sets, const double* atoms, const doubl
  * TRH_ECUDA. */
 int trh_rocking_curve(trh_ctx* ctx, int n_angles, const double* theta0, const double* theta1,
                       void* rho_out, double* eta_out, void* stream);
+
+/* ---- bulk layer ---------------------------------------------------------------------------
+ * Section 2.2 (end): below the surface region the crystal is an ideal bulk whose reflection
+ * converges quickly with depth; it is computed once, the computation stopping when it has
+ * converged, and reused. Here the bulk is periodic in z with period `period` (A) below z_e; one
+ * period's atoms are given with z relative to the top of the period, in (-period, 0]. Its
+ * boundary condition at z_e is X = P Q^{-1} of the solutions that belong in the bulk (c' = X c),
+ * the fixed point of one period's map (integrate [I; X] over the period with the context's
+ * splitting scheme, `steps_per_period` steps, and normalise), iterated from X = i Gamma until the
+ * largest entry changes by less than `tol` (<= 0 selects 1e-12) relative to the largest entry,
+ * at most `max_periods` times. The potential of a period includes the images of its atoms
+ * within 8 A. Slab integrations then start from [I; X] instead of [I; i Gamma]; the slab's own
+ * atoms (set by trh_create / trh_set_structure) should include the bulk atoms near z_e whose
+ * potential reaches into the slab. X is computed on the binary64 path (N <= 64) once per set of
+ * directions and reused while the directions stay the same (every path, the reverse sweep and
+ * batches use it). n_atoms = 0 removes the bulk.
+ * Errors: TRH_EINVAL, TRH_EUNSUPPORTED (N > 64, RK4 or the conventional integrator); a later call
+ * returns TRH_ENOCONV if some direction did not converge. */
+int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* dw,
+                 const int* species, double period, int steps_per_period, int max_periods,
+                 double tol);
 
 /* ---- reverse analysis ---------------------------------------------------------------------
  * The paper's motivation (Section 1) is the reverse analysis of measured curves: a structure

@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
                       "trheed.h")
 
 TRH_OK, TRH_EINVAL, TRH_EGRAZING, TRH_ESINGULAR = 0, -1, -2, -3
-TRH_ETIMEOUT, TRH_ENOMEM, TRH_ECUDA, TRH_EUNSUPPORTED = -4, -5, -6, -7
+TRH_ETIMEOUT, TRH_ENOMEM, TRH_ECUDA, TRH_EUNSUPPORTED, TRH_ENOCONV = -4, -5, -6, -7, -8
 INTEGRATORS = {"sp4": 0, "sp6": 1, "rk4": 2, "conventional": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
@@ -43,6 +43,7 @@ class TrhStats(C.Structure):
         ("kernels_launched", C.c_int), ("ms_last", C.c_double),
         ("ms_potential", C.c_double), ("ms_integrate", C.c_double),
         ("ms_gradient", C.c_double), ("wide_tile", C.c_int), ("graph_replay", C.c_int),
+        ("bulk_periods", C.c_int), ("ms_bulk", C.c_double),
     ]
 
     def as_dict(self):
@@ -87,6 +88,8 @@ def load():
     lib.trh_rocking_curve_noalloc.argtypes = [C.POINTER(TrhProblem), C.c_int, vp, vp, vp, vp, vp]
     lib.trh_rocking_curve_noalloc.restype = C.c_int
     lib.trh_set_fit.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.c_int]
+    lib.trh_set_bulk.argtypes = [vp, C.c_int, vp, vp, vp, C.c_double, C.c_int, C.c_int,
+                                 C.c_double]
     lib.trh_curve_jacobian.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     lib.trh_rfactor_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.trh_batch_create.argtypes = [C.POINTER(vp)]
@@ -96,7 +99,8 @@ def load():
     lib.trh_batch_destroy.argtypes = [vp]
     lib.trh_batch_destroy.restype = None
     for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query", "trh_set_fit",
-              "trh_curve_jacobian", "trh_rfactor_grad", "trh_batch_create", "trh_batch_add",
+              "trh_curve_jacobian", "trh_rfactor_grad", "trh_set_bulk", "trh_batch_create",
+              "trh_batch_add",
               "trh_batch_run", "trh_batch_query"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
@@ -251,6 +255,18 @@ class Engine:
         _check(self.lib.trh_rocking_curve(self.ctx, A, _ptr(t0), _ptr(t1), _ptr(rho), _ptr(eta),
                                           C.c_void_p(0 if stream is None else stream)))
         return rho, eta
+
+    def set_bulk(self, atoms, dw, species, period: float, steps_per_period: int,
+                 max_periods: int = 500, tol: float = 1e-12):
+        """Ideal bulk below z_e (one period's atoms, z relative to the period top in (-d, 0]);
+        slab integrations then start from the converged bulk boundary condition."""
+        a = np.ascontiguousarray(atoms, dtype=np.float64).reshape(-1, 3)
+        d = np.ascontiguousarray(dw, dtype=np.float64).reshape(-1)
+        sp = np.ascontiguousarray(species, dtype=np.int32).reshape(-1)
+        self._bulk = (a, d, sp)
+        _check(self.lib.trh_set_bulk(self.ctx, a.shape[0], _ptr(a), _ptr(d), _ptr(sp),
+                                     float(period), int(steps_per_period), int(max_periods),
+                                     float(tol)))
 
     def set_fit(self, free_atoms, dw_class=None, ckpt_every: int = 64):
         """Fit parameters for curve_jacobian / rfactor_grad: z of the atoms ``free_atoms`` and

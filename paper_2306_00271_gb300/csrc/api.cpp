@@ -139,6 +139,16 @@ struct trh_ctx {
   std::vector<double> atoms, dw;  // [n_sets][n_atoms][3], [n_sets][n_atoms]
   bool tables_dirty = true;
   unsigned long long generation = 0;  // bumped whenever device tables may move (batch plans)
+  // bulk layer (trh_set_bulk): one period's atoms (z relative to the period top), its table and
+  // the converged boundary condition X for the directions `bulk_t0/t1`
+  int bulk_n = 0, bulk_steps = 0, bulk_max = 0;
+  double bulk_period = 0, bulk_tol = 0;
+  std::vector<double> bulk_atoms, bulk_dw, bulk_t0, bulk_t1;
+  std::vector<int> bulk_species;
+  bool bulk_dirty = false;
+  DevBuf<double2> d_bulk_u, d_bulk_F, d_xbulk;
+  DevBuf<double> d_bulk_atoms, d_bulk_dw, d_bulk_nodes;
+  DevBuf<int> d_bulk_species, d_bulk_stat;
   // device
   DevBuf<double2> d_kvec, d_g, d_u, d_F, d_rho;
   DevBuf<double> d_atoms, d_dw, d_sf, d_nodes, d_theta, d_eta;
@@ -173,6 +183,7 @@ const char* trh_strerror(int status) {
     case TRH_ENOMEM: return "out of memory";
     case TRH_ECUDA: return "CUDA error";
     case TRH_EUNSUPPORTED: return "not supported by this build";
+    case TRH_ENOCONV: return "bulk boundary condition did not converge";
     default: return "unknown status";
   }
 }
@@ -484,6 +495,7 @@ static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParam
   mp.ang = ip.ang;
   mp.out = ip.out;
   mp.img = c->d_img.p;
+  mp.p0 = ip.p0;
   mp.N = c->N;
   mp.n_nodes = c->n_nodes;
   mp.n_sets = c->n_sets;
@@ -587,6 +599,153 @@ static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* s
   return TRH_OK;
 }
 
+int trh_set_bulk(trh_ctx* c, int n_atoms, const double* atoms, const double* dw,
+                 const int* species, double period, int steps_per_period, int max_periods,
+                 double tol) {
+  if (!c) return fail(TRH_EINVAL, "ctx is NULL");
+  if (n_atoms == 0) {
+    c->bulk_n = 0;
+    return TRH_OK;
+  }
+  if (n_atoms < 0 || !atoms || !dw || !species) return fail(TRH_EINVAL, "bad bulk atoms");
+  if (!(period > 0) || steps_per_period < 1 || max_periods < 2)
+    return fail(TRH_EINVAL, "need period > 0, steps_per_period >= 1, max_periods >= 2");
+  if (c->N > trh::kMaxBeamsFp64)
+    return fail(TRH_EUNSUPPORTED, "the bulk boundary condition supports N <= %d",
+                trh::kMaxBeamsFp64);
+  if (c->integrator == TRH_RK4 || c->integrator == TRH_CONVENTIONAL)
+    return fail(TRH_EUNSUPPORTED, "the bulk boundary condition needs a splitting integrator");
+  for (int a = 0; a < n_atoms; ++a) {
+    const double z = atoms[3 * a + 2];
+    if (!(z <= 0 && z > -period)) return fail(TRH_EINVAL, "bulk atom %d: z outside (-d, 0]", a);
+    if (!(dw[a] >= 0)) return fail(TRH_EINVAL, "bulk dw[%d] < 0", a);
+    if (species[a] < 0 || species[a] >= c->n_species)
+      return fail(TRH_EINVAL, "bulk species[%d] out of range", a);
+  }
+  c->bulk_n = n_atoms;
+  c->bulk_atoms.assign(atoms, atoms + 3 * n_atoms);
+  c->bulk_dw.assign(dw, dw + n_atoms);
+  c->bulk_species.assign(species, species + n_atoms);
+  c->bulk_period = period;
+  c->bulk_steps = steps_per_period;
+  c->bulk_max = max_periods;
+  c->bulk_tol = tol > 0 ? tol : 1e-12;
+  c->bulk_dirty = true;
+  c->generation++;
+  return TRH_OK;
+}
+
+// The bulk boundary condition for these directions (device X in d_xbulk), computed unless the
+// cached one matches. Sets *bulk_p0 (nullptr without a bulk).
+static int bulk_prepare(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
+                        const double* dev_t0, const double* dev_t1, cudaStream_t st,
+                        int* launched, const double2** bulk_p0) {
+  *bulk_p0 = nullptr;
+  c->stats.bulk_periods = 0;
+  c->stats.ms_bulk = 0.0;
+  if (c->bulk_n == 0) return TRH_OK;
+  std::vector<double> t0(n_angles), t1(n_angles);
+  TRH_CUDA(cudaMemcpyAsync(t0.data(), theta0, n_angles * 8, cudaMemcpyDefault, st));
+  TRH_CUDA(cudaMemcpyAsync(t1.data(), theta1, n_angles * 8, cudaMemcpyDefault, st));
+  TRH_CUDA(cudaStreamSynchronize(st));
+  if (!c->bulk_dirty && t0 == c->bulk_t0 && t1 == c->bulk_t1) {
+    *bulk_p0 = c->d_xbulk.p;
+    return TRH_OK;
+  }
+  const int s = c->scheme.s, Lb = c->bulk_steps;
+  const double d = c->bulk_period, hb = d / Lb;
+  // images of the period's atoms within 8 A, one period's kick positions below z_e
+  const int kmax = (int)std::ceil((8.0 + d) / d);
+  std::vector<double> at, dwv;
+  std::vector<int> sp;
+  for (int k = -kmax; k <= kmax; ++k)
+    for (int a = 0; a < c->bulk_n; ++a) {
+      at.push_back(c->bulk_atoms[3 * a]);
+      at.push_back(c->bulk_atoms[3 * a + 1]);
+      at.push_back(c->z_e + c->bulk_atoms[3 * a + 2] + k * d);
+      dwv.push_back(c->bulk_dw[a]);
+      sp.push_back(c->bulk_species[a]);
+    }
+  const int n_img = (int)dwv.size();
+  const int n_nodes = s * Lb + 1;
+  std::vector<double> cr(s, 0.0), nz(n_nodes);
+  for (int r = 1; r < s; ++r) cr[r] = cr[r - 1] + c->scheme.a[r - 1];
+  for (int i = 0; i < Lb; ++i)
+    for (int r = 0; r < s; ++r) nz[(size_t)s * i + r] = c->z_e - d + (i + cr[r]) * hb;
+  nz[(size_t)s * Lb] = c->z_e;
+  TRH_CUDA(c->d_bulk_atoms.ensure(at.size()));
+  TRH_CUDA(c->d_bulk_dw.ensure(n_img));
+  TRH_CUDA(c->d_bulk_species.ensure(n_img));
+  TRH_CUDA(c->d_bulk_nodes.ensure(n_nodes));
+  TRH_CUDA(c->d_bulk_u.ensure((size_t)n_nodes * c->M));
+  TRH_CUDA(c->d_bulk_F.ensure((size_t)c->M * 4 * n_img));
+  const double2* old_x = c->d_xbulk.p;
+  TRH_CUDA(c->d_xbulk.ensure((size_t)n_angles * c->N * c->N));
+  if (c->d_xbulk.p != old_x) c->generation++;   // batch plans hold the old pointer
+  TRH_CUDA(c->d_bulk_stat.ensure(2 * (size_t)n_angles));
+  TRH_CUDA(cudaMemcpyAsync(c->d_bulk_atoms.p, at.data(), at.size() * 8, cudaMemcpyHostToDevice, st));
+  TRH_CUDA(cudaMemcpyAsync(c->d_bulk_dw.p, dwv.data(), n_img * 8, cudaMemcpyHostToDevice, st));
+  TRH_CUDA(cudaMemcpyAsync(c->d_bulk_species.p, sp.data(), n_img * 4, cudaMemcpyHostToDevice, st));
+  TRH_CUDA(cudaMemcpyAsync(c->d_bulk_nodes.p, nz.data(), n_nodes * 8, cudaMemcpyHostToDevice, st));
+  TRH_CUDA(cudaEventRecord(c->ev[4], st));
+  trh::PotentialParams pp{};
+  pp.g = c->d_g.p;
+  pp.atoms = c->d_bulk_atoms.p;
+  pp.dw = c->d_bulk_dw.p;
+  pp.species = c->d_bulk_species.p;
+  pp.sf = c->d_sf.p;
+  pp.node_z = c->d_bulk_nodes.p;
+  pp.pref = potential_prefactor(c);
+  pp.M = c->M;
+  pp.n_atoms = n_img;
+  pp.n_nodes = n_nodes;
+  pp.n_sets = 1;
+  pp.F = c->d_bulk_F.p;
+  pp.u = c->d_bulk_u.p;
+  pp.u32 = nullptr;
+  TRH_CUDA(trh::launch_potential(pp, st, launched));
+  trh::IntegrateParams bp{};
+  bp.sch = c->scheme;
+  bp.ang.theta0 = dev_t0;
+  bp.ang.theta1 = dev_t1;
+  bp.ang.kvec = c->d_kvec.p;
+  bp.ang.gamma = c->gamma;
+  bp.ang.phi_a1 = c->phi_a1;
+  bp.ang.n_angles = n_angles;
+  bp.out.status = c->d_bulk_stat.p;
+  bp.u = c->d_bulk_u.p;
+  bp.lmap = c->d_lmap.p;
+  bp.N = c->N;
+  bp.M = c->M;
+  bp.n_nodes = n_nodes;
+  bp.n_sets = 1;
+  bp.L = Lb;
+  bp.h = hb;
+  bp.threshold = c->threshold;
+  bp.method = trh::kMethodBAB;
+  TRH_CUDA(trh::launch_bulk_fp64(bp, c->d_xbulk.p, c->d_bulk_stat.p + n_angles, c->bulk_max,
+                                 c->bulk_tol, st, launched));
+  TRH_CUDA(cudaEventRecord(c->ev[5], st));
+  std::vector<int> hs(2 * (size_t)n_angles);
+  TRH_CUDA(cudaMemcpyAsync(hs.data(), c->d_bulk_stat.p, hs.size() * 4, cudaMemcpyDeviceToHost, st));
+  TRH_CUDA(cudaStreamSynchronize(st));
+  int worst = TRH_OK, periods = 0;
+  for (int a = 0; a < n_angles; ++a) {
+    if (hs[a] != 0 && worst == TRH_OK) worst = hs[a];
+    periods = std::max(periods, hs[n_angles + a]);
+  }
+  c->stats.bulk_periods = periods;
+  c->stats.ms_bulk = elapsed_ms(c->ev[4], c->ev[5]);
+  if (worst != TRH_OK)
+    return fail(worst, "bulk boundary condition: %s (max_periods %d)", trh_strerror(worst),
+                c->bulk_max);
+  c->bulk_t0 = t0;
+  c->bulk_t1 = t1;
+  c->bulk_dirty = false;
+  *bulk_p0 = c->d_xbulk.p;
+  return TRH_OK;
+}
+
 int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const double* theta1,
                       void* rho_out, double* eta_out, void* stream) {
   const auto t_start = std::chrono::steady_clock::now();
@@ -611,7 +770,12 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
     eta = c->d_eta.p;
   }
   TRH_CUDA(c->d_status.ensure(2 * pairs));
+  const double2* bulk_p0 = nullptr;
+  rc = bulk_prepare(c, n_angles, theta0, theta1, c->d_theta.p, c->d_theta.p + n_angles, st,
+                    &launched, &bulk_p0);
+  if (rc != TRH_OK) return rc;
   trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, rho, eta);
+  ip.p0 = bulk_p0;
   int tile = 0;
   const bool wide = c->precision == TRH_FP64 &&
                     (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4 ||
@@ -750,7 +914,12 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
         TRH_CUDA(cudaEventCreateWithFlags(&c->gev[k][b], cudaEventDisableTiming));
   }
 
+  const double2* bulk_p0 = nullptr;
+  rc = bulk_prepare(c, n_angles, theta0, theta1, c->d_theta.p, c->d_theta.p + n_angles, st,
+                    launched, &bulk_p0);
+  if (rc != TRH_OK) return rc;
   trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, c->d_rho.p, c->d_eta.p);
+  ip.p0 = bulk_p0;
   ip.ckpt = c->d_ckpt.p;
   ip.ckpt_every = C;
   ip.n_ckpt = n_seg + 1;
@@ -948,6 +1117,14 @@ void trh_destroy(trh_ctx* c) {
   c->d_status.release();
   c->d_img.release();
   c->d_wide.release();
+  c->d_bulk_u.release();
+  c->d_bulk_F.release();
+  c->d_xbulk.release();
+  c->d_bulk_atoms.release();
+  c->d_bulk_dw.release();
+  c->d_bulk_nodes.release();
+  c->d_bulk_species.release();
+  c->d_bulk_stat.release();
   c->d_active.release();
   c->d_free_active.release();
   c->d_class_active.release();
@@ -1055,6 +1232,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
     trh::IntegrateParams ip = integrate_params(c, J.n_angles, pairs, J.rho, J.eta);
     ip.ang.theta0 = J.theta0;
     ip.ang.theta1 = J.theta1;
+    ip.p0 = c->bulk_n > 0 ? c->d_xbulk.p : nullptr;
     b->params.push_back(ip);
     J.generation = c->generation;
     b->total_pairs += pairs;
@@ -1152,12 +1330,22 @@ int trh_batch_run(trh_batch* b, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   int launched = 0;
   bool stale = !b->prepared;
-  for (auto& J : b->jobs) {
+  for (size_t j = 0; j < b->jobs.size(); ++j) {
+    auto& J = b->jobs[j];
     if (!J.c->ev[0])
       for (int i = 0; i < 6; ++i) TRH_CUDA(cudaEventCreate(&J.c->ev[i]));
     bool rebuilt = false;
     int rc = build_tables(J.c, st, &launched, &rebuilt);
     if (rc != TRH_OK) return rc;
+    if (J.c->bulk_n > 0) {
+      for (size_t i = 0; i < j; ++i)
+        if (b->jobs[i].c == J.c)
+          return fail(TRH_EINVAL, "a context with a bulk may appear in one job of a batch");
+      const double2* p0 = nullptr;
+      rc = bulk_prepare(J.c, J.n_angles, J.theta0, J.theta1, J.theta0, J.theta1, st, &launched,
+                        &p0);
+      if (rc != TRH_OK) return rc;
+    }
     if (J.c->generation != J.generation) stale = true;
   }
   if (stale) {

@@ -406,8 +406,10 @@ __device__ __forceinline__ void gauss_solve(Smem& S, int N) {
 // Row A1 for one angle: b0 = gamma cos(theta0) (cos phi, sin phi), Gamma_j^2 = gamma^2 -
 // |b0 + k_j|^2, Gamma_j = sqrt(.) or -i sqrt(-.) (the evanescent modes decay away from the slab).
 // Zeroes all six planes, fills gam2 / Gr / Gi and S.sin_t0, and (if init_state) writes the
-// initial value [I; i Gamma] (Algorithm 1's S \ [I; O] times 2 Gamma) into Q, P.
-__device__ __forceinline__ void setup_angle(Smem& S, const AngleInputs& ang, int angle, int N, bool init_state) {
+// initial value into Q, P: [I; i Gamma] (Algorithm 1's S \ [I; O] times 2 Gamma), or [I; X]
+// when a bulk boundary condition X (this angle's N x N matrix) is given.
+__device__ __forceinline__ void setup_angle(Smem& S, const AngleInputs& ang, int angle, int N,
+                                            bool init_state, const double2* x0 = nullptr) {
   const int tid = threadIdx.x;
   for (int e = tid; e < NP * LD; e += NT) {
     S.Ur[e] = S.Ui[e] = S.Qr[e] = S.Qi[e] = S.Pr[e] = S.Pi[e] = 0.0;
@@ -432,14 +434,22 @@ __device__ __forceinline__ void setup_angle(Smem& S, const AngleInputs& ang, int
       if (fabs(g2) < 1e-12 * ang.gamma * ang.gamma) S.status = kGrazing;
       if (init_state) {
         S.Qr[tid * LD + tid] = 1.0;
-        S.Pr[tid * LD + tid] = -gi;
-        S.Pi[tid * LD + tid] = gr;
+        if (!x0) {
+          S.Pr[tid * LD + tid] = -gi;
+          S.Pi[tid * LD + tid] = gr;
+        }
       }
     }
     S.gam2[tid] = g2;
     S.Gr[tid] = gr;
     S.Gi[tid] = gi;
   }
+  if (init_state && x0)
+    for (int e = tid; e < N * N; e += NT) {
+      const int j = e / N, k = e - j * N;
+      S.Pr[j * LD + k] = x0[e].x;
+      S.Pi[j * LD + k] = x0[e].y;
+    }
   __syncthreads();
 }
 

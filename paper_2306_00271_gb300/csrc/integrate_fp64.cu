@@ -71,7 +71,7 @@ __device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
 
-  setup_angle(S, p.ang, angle, N, true);
+  setup_angle(S, p.ang, angle, N, true, p.p0 ? p.p0 + (size_t)angle * N * N : nullptr);
   const double sin_t0 = S.sin_t0;
   load_u(S, p, set, 0);
   __syncthreads();
@@ -143,7 +143,83 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_fp64_items(const IntegrateP
   }
 }
 
+// Bulk boundary condition (Section 2.2, end: the bulk layer's reflection converges quickly, is
+// computed once and reused). In the economical form it is X = P Q^{-1} at z_e of the solutions
+// that belong in the semi-infinite bulk, the fixed point of one period's map F(X) (integrate
+// [I; X] over the period with the splitting scheme, normalise by the RHST). One CTA per angle
+// iterates F from X = i Gamma (no wave at a deep bottom) and stops when X changes by less than
+// tol relative to its largest entry.
+__global__ void __launch_bounds__(NT, 1) k_bulk_fp64(IntegrateParams p, double2* X, int* periods,
+                                                     int max_periods, double tol) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const int angle = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = p.N;
+  const int s = p.sch.s;
+  double2* Xg = X + (size_t)angle * N * N;
+  setup_angle(S, p.ang, angle, N, true);
+  int k = 0;
+  bool done = false;
+  while (!done && S.status == kOk && k < max_periods) {
+    ++k;
+    load_u(S, p, 0, 0);
+    __syncthreads();
+    for (int i = 0; i < p.L && S.status == kOk; ++i) {
+      for (int r = 0; r < s; ++r) {
+        const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
+        kick_drift(S, p, 0, coef, p.sch.a[r], true, s * i + r + 1);
+      }
+      badness(S, p);
+      if (S.flag) rhst(S, p);
+    }
+    if (S.status != kOk) break;
+    kick_drift(S, p, 0, p.sch.b[s], 0.0, false, -1);
+    rhst(S, p);                                   // normalise: Q = I, P = F(X)
+    if (S.status != kOk) break;
+    double dmax = 0.0, xmax = 0.0;
+    for (int e = tid; e < N * N; e += NT) {
+      const int j = e / N, c = e - j * N;
+      const double2 xn = make_double2(S.Pr[j * LD + c], S.Pi[j * LD + c]);
+      const double2 xo = Xg[e];
+      dmax = fmax(dmax, hypot(xn.x - xo.x, xn.y - xo.y));
+      xmax = fmax(xmax, hypot(xn.x, xn.y));
+      Xg[e] = xn;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if (lane == 0) {
+      S.red0[warp] = dmax;
+      S.red1[warp] = xmax;
+    }
+    __syncthreads();
+    double dm = 0.0, xm = 0.0;
+    for (int w = 0; w < NT / 32; ++w) {
+      dm = fmax(dm, S.red0[w]);
+      xm = fmax(xm, S.red1[w]);
+    }
+    done = (k > 1) && (dm <= tol * xm);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    periods[angle] = k;
+    p.out.status[angle] = (S.status != kOk) ? S.status : (done ? kOk : kNoConvergence);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bulk_fp64(const IntegrateParams& p, double2* X, int* periods, int max_periods,
+                             double tol, cudaStream_t st, int* n_launched) {
+  const size_t smem = sizeof(Smem);
+  cudaError_t e = cudaFuncSetAttribute(k_bulk_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_bulk_fp64<<<p.ang.n_angles, NT, smem, st>>>(p, X, periods, max_periods, tol);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
 
 size_t integrate_fp64_smem_bytes() { return sizeof(Smem); }
 

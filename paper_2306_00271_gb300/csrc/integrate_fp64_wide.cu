@@ -588,11 +588,12 @@ __device__ __forceinline__ void wide_pair(WideSmem& S, double2* tbl, const Integ
     __syncthreads();
     return;
   }
-  // initial value [I; i Gamma]
+  // initial value [I; i Gamma], or [I; X] with a bulk boundary condition X
+  const double2* x0 = p.p0 ? p.p0 + (size_t)angle * NN : nullptr;
   for (size_t e = tid; e < NN; e += WT) {
     const int r = (int)(e / N), c = (int)(e - (size_t)r * N);
     Q[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
-    P[e] = (r == c) ? make_double2(-S.Gi[r], S.Gr[r]) : make_double2(0.0, 0.0);
+    P[e] = x0 ? x0[e] : ((r == c) ? make_double2(-S.Gi[r], S.Gr[r]) : make_double2(0.0, 0.0));
   }
   __syncthreads();
   const int s = p.sch.s;

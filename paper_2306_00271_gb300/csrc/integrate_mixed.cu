@@ -394,18 +394,23 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   const double g2d = (j < N) ? S.gam2[j] : 0.0;
   const float g2h = (float)g2d, g2l = (float)(g2d - (double)g2h);
 
-  // initial value [I; i Gamma]
+  // initial value [I; i Gamma], or [I; X] with a bulk boundary condition X
   float Qh[CPT], Ql[CPT], Ph[CPT], Pl[CPT];
   {
     const double pv = (j < N) ? (part ? S.Gr[j] : -S.Gi[j]) : 0.0;
-    const float pvh = (float)pv, pvl = (float)(pv - (double)pvh);
+    const double2* x0 = p.p0 ? p.p0 + (size_t)angle * N * N : nullptr;
 #pragma unroll
     for (int i = 0; i < CPT; ++i) {
       const bool dg = (j < N) && (c0 + i == j);
+      double v = dg ? pv : 0.0;
+      if (x0 && j < N && c0 + i < N) {
+        const double2 xv = x0[j * N + c0 + i];
+        v = part ? xv.y : xv.x;
+      }
       Qh[i] = (dg && part == 0) ? 1.0f : 0.0f;
       Ql[i] = 0.0f;
-      Ph[i] = dg ? pvh : 0.0f;
-      Pl[i] = dg ? pvl : 0.0f;
+      Ph[i] = (float)v;
+      Pl[i] = (float)(v - (double)Ph[i]);
     }
   }
   if (tid == 0) S.ovf = 0;

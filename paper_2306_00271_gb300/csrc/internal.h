@@ -17,7 +17,7 @@ constexpr int kMethodConventional = 2;  // conventional multi-slice with recursi
 
 // Status words written by kernels (mirrors the TRH_E* codes of trheed.h).
 enum DevStatus : int {
-  kOk = 0, kSingular = -3, kGrazing = -2, kTimeout = -4
+  kOk = 0, kSingular = -3, kGrazing = -2, kTimeout = -4, kNoConvergence = -8
 };
 
 // A BAB splitting scheme after FSAL merging: per step, s kicks and s drifts; the first kick of
@@ -55,6 +55,9 @@ struct IntegrateParams {
   double h;
   double threshold;
   int method;                  // kMethodBAB or kMethodRK4 (nodes z_i, z_i + h/2 per step)
+  // Optional initial state [I; X] at z_e instead of [I; i Gamma] (the converged bulk boundary
+  // condition, one X per angle): [n_angles][N][N] complex, or nullptr.
+  const double2* p0;
   // Optional checkpoints for the reverse sweep (nullptr: none). Slot c < n_ckpt - 1 holds the
   // state [Q; P] at the start of step c * ckpt_every, slot n_ckpt - 1 the final state;
   // layout [n_sets][n_angles][n_ckpt][2][N][N] complex.
@@ -90,6 +93,7 @@ struct MixedParams {
   AngleInputs ang;
   Outputs out;
   const unsigned char* img;    // BF16 images of U(tau) per node
+  const double2* p0;           // optional initial P ([n_angles][N][N]; Q = I), or nullptr
   int N, n_nodes, n_sets, L;
   int n_mma;                   // UMMA N: N rounded up to 16
   int k_slices;                // UMMA K slices of 16: ceil(2N / 16)
@@ -159,6 +163,12 @@ size_t mixed_image_bytes_per_node();
 void set_last_error(const char* msg);
 cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int* n_launched);
 size_t integrate_fp64_smem_bytes();
+// Bulk boundary condition (integrate_fp64.cu): per angle the fixed point X of one bulk period's
+// map, iterated from i Gamma until the largest change is below tol times the largest entry.
+// `p` describes one period (its table, L steps); X is [n_angles][N][N], periods [n_angles];
+// p.out.status receives kNoConvergence when max_periods were not enough.
+cudaError_t launch_bulk_fp64(const IntegrateParams& p, double2* X, int* periods, int max_periods,
+                             double tol, cudaStream_t st, int* n_launched);
 // Wide beam sets and RK4 on the FP64 path (integrate_fp64_wide.cu); `state` holds 2 N^2 (6 N^2
 // for RK4) complex128 per (set, angle) pair (integrate_fp64_wide_state_bytes).
 cudaError_t launch_integrate_fp64_wide(const IntegrateParams& p, double2* state, int tile,
