@@ -173,6 +173,26 @@ __device__ __forceinline__ void write_b_exact(Smem& S, const float (&qh)[CPT], i
   digits_b(S, qh, m, c0, qd, lane, par, par);
 }
 
+// Two 32x32b.x8 loads, one wait.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, float (&va)[8], uint32_t tb,
+                                           float (&vb)[8]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(r[8 + i]);
+  }
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
   asm volatile(
@@ -284,8 +304,7 @@ __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32
   for (int i = 0; i < CPT; ++i) oh[i] = ol[i] = 0.0f;
   for (int kc = 0; kc < n; kc += 8) {
     float zh[8], zl[8], ph[8], pl[8];
-    tmem_ld8(t_lane + col_h + kc, zh);
-    tmem_ld8(t_lane + col_l + kc, zl);
+    tmem_ld8x2(t_lane + col_h + kc, zh, t_lane + col_l + kc, zl);
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
       ph[kk] = __shfl_xor_sync(0xffffffffu, zh[kk], 1);
@@ -489,12 +508,15 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       // acc = D_0 + 2^-8 (D_1 + 2^-8 (D_2 + 2^-8 D_3)), folded as the accumulators arrive
       constexpr float kQ = 0.00390625f;  // 2^-8
       float acc[CPT], dt[CPT];
-      tmem_ld16(t_lane + TM_D3 + c0, acc);
+      tmem_ld16x2(t_lane + TM_D3 + c0, acc, t_lane + TM_D2 + c0, dt);
 #pragma unroll
-      for (int o = 2; o >= 0; --o) {
-        tmem_ld16(t_lane + (o == 2 ? TM_D2 : (o == 1 ? TM_D1 : TM_D0)) + c0, dt);
+      for (int c = 0; c < CPT; ++c) acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
+      {
+        float d1[CPT];
+        tmem_ld16x2(t_lane + TM_D1 + c0, d1, t_lane + TM_D0 + c0, dt);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
+        for (int c = 0; c < CPT; ++c)
+          acc[c] = __fadd_rn(dt[c], __fmul_rn(__fadd_rn(d1[c], __fmul_rn(acc[c], kQ)), kQ));
       }
       const float hbh = p.kick_hi[kidx], hbl = p.kick_lo[kidx];
       float cgh, cgl;  // hb * Gamma_j^2 as a float pair
