@@ -194,8 +194,11 @@ int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* d
  * recomputes one segment at a time. Device scratch per (set, angle) pair, in bytes:
  *   16 N^2 (2 (L / C + 1) + 2 (s C + 1) + 2 C + 2) + 4 C,   C = ckpt_every, s = kicks per step,
  * about 53 MB at N = 61, L = 2000, C = 64 (sp4).
- * Both calls always integrate on the binary64 path (the kernels of TRH_FP64), whatever the
- * context's precision. */
+ * On a TRH_FP64 context everything runs on the binary64 path. On a TRH_MIXED context the forward
+ * pass (curve, R and the checkpoints, binary64 values of its double-float state) runs on the
+ * mixed path and every segment is recomputed on the binary64 path from its checkpoint, so the
+ * reverse map differentiates the trajectory it recomputes; the gradient then carries the mixed
+ * path's ~1e-8 relative error. */
 
 /* Declare the fit parameters: the z coordinates of atoms free_atoms[0..n_free-1] (distinct
  * indices into the context's atoms) and n_classes Debye-Waller classes, dw_class[a] in

@@ -496,6 +496,9 @@ static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParam
   mp.out = ip.out;
   mp.img = c->d_img.p;
   mp.p0 = ip.p0;
+  mp.ckpt = ip.ckpt;
+  mp.ckpt_every = ip.ckpt_every;
+  mp.n_ckpt = ip.n_ckpt;
   mp.N = c->N;
   mp.n_nodes = c->n_nodes;
   mp.n_sets = c->n_sets;
@@ -924,7 +927,14 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   ip.ckpt_every = C;
   ip.n_ckpt = n_seg + 1;
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
-  TRH_CUDA(trh::launch_integrate_fp64(ip, st, launched));
+  if (c->precision == TRH_MIXED) {
+    // mixed forward: curve and checkpoints from the double-float state; every segment is then
+    // recomputed on the binary64 path from its checkpoint, so the reverse map stays consistent
+    // with the trajectory it differentiates
+    TRH_CUDA(trh::launch_integrate_mixed(mixed_params(c, ip), st, launched));
+  } else {
+    TRH_CUDA(trh::launch_integrate_fp64(ip, st, launched));
+  }
   TRH_CUDA(cudaEventRecord(c->ev[3], st));
 
   trh::GradParams g{};

@@ -452,9 +452,23 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   int abort = (S.status != kOk);
   int kick_no = 0;
 
+  // [Q; P] as binary64 (hi + lo) into checkpoint slot `slot` (for the reverse sweep)
+  auto checkpoint = [&](int slot) {
+    if (j >= N) return;
+    const size_t NN = (size_t)N * N;
+    double2* dst = p.ckpt + ((size_t)pair * p.n_ckpt + slot) * 2 * NN;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (c0 + c < N) {
+        reinterpret_cast<double*>(&dst[(size_t)j * N + c0 + c])[part] = (double)Qh[c] + (double)Ql[c];
+        reinterpret_cast<double*>(&dst[NN + (size_t)j * N + c0 + c])[part] =
+            (double)Ph[c] + (double)Pl[c];
+      }
+  };
   for (int i = 0; i <= p.L && !abort; ++i) {
     const bool last = (i == p.L);
     const int nk = last ? 1 : s;
+    if (p.ckpt && !last && i % p.ckpt_every == 0) checkpoint(i / p.ckpt_every);
     for (int r = 0; r < nk; ++r, ++kick_no) {
       const int kidx = last ? s + 1 : (r > 0 ? r : (i == 0 ? 0 : s));
       const int next = last ? -1 : s * i + r + 1;
@@ -572,7 +586,10 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
         __syncthreads();
       }
     }
-    if (abort || last) break;
+    if (abort || last) {
+      if (!abort && p.ckpt) checkpoint(p.n_ckpt - 1);   // final state: seeds the reverse sweep
+      break;
+    }
 
     // badness xi of Q (FP32 Varah bound) after the step
     {

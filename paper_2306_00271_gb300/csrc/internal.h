@@ -94,6 +94,8 @@ struct MixedParams {
   Outputs out;
   const unsigned char* img;    // BF16 images of U(tau) per node
   const double2* p0;           // optional initial P ([n_angles][N][N]; Q = I), or nullptr
+  double2* ckpt;               // optional checkpoints as in IntegrateParams (binary64 values of
+  int ckpt_every, n_ckpt;      // the double-float state), or nullptr
   int N, n_nodes, n_sets, L;
   int n_mma;                   // UMMA N: N rounded up to 16
   int k_slices;                // UMMA K slices of 16: ceil(2N / 16)

@@ -136,3 +136,28 @@ def test_fit_argument_errors(api):
         with pytest.raises(api.TrhError) as e:
             eng.set_fit(free, cls)
         assert e.value.code == api.TRH_EINVAL
+
+
+def test_mixed_forward_gradient(api):
+    """A mixed-precision context: forward and checkpoints on the mixed path, segments recomputed
+    in binary64; small size against the oracle's central differences and full size against the
+    golden gradient, both within the 1e-5 bar."""
+    wl = _small()
+    free, cls = np.array([1, 3]), np.array([0, 0, 1, 1])
+    target = np.array([0.05, 0.02, 0.01, 0.004])
+    eng = api.Engine(wl, "mixed", "sp4")
+    eng.set_fit(free, cls, ckpt_every=50)
+    R, gz, gb = eng.rfactor_grad(wl.theta0, wl.theta1, target)
+    fd = G.fd_gradient(wl, free, cls, target)
+    g = np.concatenate([gz.cpu().numpy()[0], gb.cpu().numpy()[0]])
+    assert float(R[0]) == pytest.approx(fd["R"], rel=1e-6)
+    assert _rel(g, fd["grad"]) <= TOL, _rel(g, fd["grad"])
+    gold = np.load(GOLDEN)
+    fp = W.rfactor_fit()
+    eng = api.Engine(fp.workload, "mixed", "sp4")
+    eng.set_fit(fp.free_atoms, fp.dw_class, ckpt_every=64)
+    R, gz, gb = eng.rfactor_grad(fp.workload.theta0, fp.workload.theta1, gold["target"])
+    g = np.concatenate([gz.cpu().numpy()[0], gb.cpu().numpy()[0]])
+    assert _rel(g, gold["grad"]) <= TOL, _rel(g, gold["grad"])
+    st = eng.stats()
+    assert st["ms_integrate"] < 1000.0      # the forward ran on the mixed path
