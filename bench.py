@@ -104,6 +104,65 @@ def cpu_baseline(wl, n_angles: int):
                       f"{dt:.1f} s wall"}
 
 
+def oracle_timings(cores: int):
+    """The oracle's other timings on the host cores: O1 (conventional, eigendecomposition route)
+    on the same 61-beam sample at 2000 slices, and O1 / O2 on the 11-beam RHEED workload
+    (1 angle, 400 slices)."""
+    from oracle.curve import rocking_curve, rocking_curve_parallel
+    out = {}
+    wl = W.trhepd_n61()
+    idx = list(np.linspace(0, 59, cores).round().astype(int))
+    t = time.perf_counter()
+    rocking_curve_parallel(wl, "conventional", angles=idx, processes=cores)
+    dt = time.perf_counter() - t
+    out["o1_trhepd_n61"] = {"value": len(idx) / dt, "unit": UNIT,
+                            "sample": f"{len(idx)} angles, 2000 slices, {cores} processes"}
+    row = W.rheed_row()
+    for name, method in (("o2_rheed_row", "sp4"), ("o1_rheed_row", "conventional")):
+        t = time.perf_counter()
+        rocking_curve(row, method)
+        out[name] = {"value": 1e6 * (time.perf_counter() - t), "unit": "us per curve",
+                     "sample": "1 angle, 400 slices, 1 process"}
+    return out
+
+
+def rheed_row_latency():
+    """Device time of one 11-beam RHEED curve (1 angle, 400 slices) per path: the small,
+    latency-bound case, reported in microseconds."""
+    from paper_2306_00271_gb300 import api
+    wl = W.rheed_row()
+    out = {}
+    for path in ("fp64", "mixed"):
+        eng = api.Engine(wl, path, "sp4")
+        eng.rocking_curve(wl.theta0, wl.theta1)
+        ms = []
+        for _ in range(5):
+            eng.rocking_curve(wl.theta0, wl.theta1)
+            ms.append(eng.stats()["ms_integrate"])
+        out[path] = {"value": 1e3 * float(np.median(ms)), "unit": "us per curve (integration)"}
+        eng.close()
+    return out
+
+
+def run_large_sample(slices: int = 30):
+    """The 255-beam recipe (one structure, 120 angles) on the FP64 path at a few slices: time per
+    slice, extrapolated to its 3000 slices and 64 structures (FP64 only; the mixed path and the
+    reverse sweep take N <= 64)."""
+    import torch
+    from paper_2306_00271_gb300 import api
+    wl = W.large_n255(1)[0].with_steps(slices)
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.rocking_curve(wl.theta0, wl.theta1)
+    ms = eng.stats()["ms_integrate"]
+    tile = eng.stats()["wide_tile"]
+    eng.close()
+    per_slice = ms / slices
+    return {"value": 120 / (ms / 1e3), "unit": "angles/s", "slices": slices, "ms": ms,
+            "wide_tile": tile,
+            "extrapolated_full_forward_s": per_slice * 3000 * 64 / 1e3,
+            "note": "FP64 wide kernel, 120 angles on 120 SMs; full recipe = 3000 slices x 64 sets"}
+
+
 # DRAM bytes per kick node of the integration kernels, from one ncu capture each (dram__bytes_read
 # + dram__bytes_write of a small case, divided by its node count; the traffic of both kernels is
 # proportional to the node count). Summaries: profiles/k_integrate_mixed_trhepd_n61_L400.md and
@@ -195,7 +254,7 @@ def run_ours(args):
     return wl, results, ws, rank
 
 
-def run_gradient(local: int, slices: int = 0, warmup: int = 1):
+def run_gradient(local: int, slices: int = 0, warmup: int = 1, path: str = "fp64"):
     """One R-factor gradient at the differentiation workload (N = 61, 2000 slices, 60 angles,
     12 free z + 6 Debye-Waller classes, checkpoints every 64 steps), FP64 reverse sweep. The
     target curve is this library's own FP64 curve at the hidden true structure."""
@@ -205,7 +264,7 @@ def run_gradient(local: int, slices: int = 0, warmup: int = 1):
     if slices:
         fp = replace(fp, workload=fp.workload.with_steps(slices))
     wl = fp.workload
-    eng = api.Engine(wl, "fp64", "sp4")
+    eng = api.Engine(wl, path, "sp4")
     truth = W.fit_structure(fp, fp.z_true, fp.b_true)
     eng.set_structures(truth.atoms[None], truth.dw[None])
     _, eta_t = eng.rocking_curve(wl.theta0, wl.theta1)
@@ -225,7 +284,8 @@ def run_gradient(local: int, slices: int = 0, warmup: int = 1):
     st = eng.stats()
     eng.close()
     return {"metric": f"R-factor gradients/s (N=61, L={wl.n_steps}, 60 angles, 18 parameters, "
-                      "FP64 reverse sweep, checkpoints every 64 steps)",
+                      f"{'mixed' if path == 'mixed' else 'FP64'} forward, FP64 reverse sweep, "
+                      "checkpoints every 64 steps)",
             "value": 1000.0 / ms, "unit": "gradients/s", "ms_per_gradient": ms,
             "ms_forward": st["ms_integrate"], "ms_reverse": st["ms_gradient"],
             "kernels_launched": st["kernels_launched"], "R": float(R[0])}
@@ -371,12 +431,17 @@ def main():
         out["mixed_vs_fp64_curve_error"] = curve_error(res["mixed"]["eta"], res["fp64"]["eta"])
     if not args.no_grad:
         out["gradient"] = run_gradient(int(os.environ.get("LOCAL_RANK", "0")), args.slices)
+        out["gradient_mixed_forward"] = run_gradient(int(os.environ.get("LOCAL_RANK", "0")),
+                                                     args.slices, path="mixed")
     if not args.no_batch:
         out["batches"] = run_batches(args.slices)
+        out["large_n255_sample"] = run_large_sample()
+        out["rheed_row_latency"] = rheed_row_latency()
     if ws == 1 and not args.no_cpu:
         n = args.cpu_angles or min(60, max(8, len(os.sched_getaffinity(0))))
         try:
             out["cpu_baseline"] = cpu_baseline(wl, n)
+            out["oracle_timings"] = oracle_timings(len(os.sched_getaffinity(0)))
         except Exception as e:  # pragma: no cover
             out["cpu_baseline"] = {"error": str(e)}
     print(json.dumps(out))
