@@ -27,7 +27,8 @@
 // kick P <- P - hb W - (hb Gamma^2) Q and the drift Q <- Q + ha P are exact to that precision.
 //
 // Per kick: every thread waits for the bulk copy of U(tau)'s digit image (128 KB + row scales, TMA
-// engine); thread 0 issues 10 x 8 tcgen05.mma (128 x n x 16) into the four accumulators and
+// engine); thread 0 issues 4 x 8 tcgen05.mma (128 x (64 (3 - a) + n) x 16 for digit a of A, which
+// meets all the digits of B it pairs with in one instruction) into the four accumulators and
 // commits to an mbarrier; the next image is fetched as soon as the MMAs are done, overlapping the
 // epilogue. The epilogue (16 warps; warp w reads TMEM lanes 32(w%4).. and columns 16(w/4)..)
 // applies the kick and the drift, takes the exact column maxima of the new Q (warp reductions,
@@ -64,7 +65,7 @@ constexpr int B_TERM = (NC / 8) * B_SBO;
 constexpr int TS = NC + 1;                   // row stride (float2) of T = Q^{-1} in the B region:
                                              // column walks hit 16 distinct bank pairs per phase
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t TM_D0 = 0, TM_D1 = 64, TM_D2 = 128, TM_D3 = 192;
+constexpr uint32_t TM_D3 = 0, TM_D2 = 64, TM_D1 = 128, TM_D0 = 192;  // D_o at 64 (3 - o)
 constexpr uint32_t TM_QH = 256, TM_QL = 320, TM_PH = 384, TM_PL = 448;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 constexpr double kPi = 3.14159265358979323846;
@@ -160,7 +161,8 @@ __device__ __forceinline__ bool digits_b(Smem& S, const float (&qh)[CPT], int m,
     digits4(qh[i], inv, b);
     const int off = (c >> 3) * B_SBO + (m >> 3) * B_LBO + (c & 7) * 16 + (m & 7) * 2;
 #pragma unroll
-    for (int t = 0; t < NDIG; ++t) *reinterpret_cast<uint16_t*>(S.B + t * B_TERM + off) = b[t];
+    for (int t = 0; t < NDIG; ++t)  // digit t in plane position 3 - t
+      *reinterpret_cast<uint16_t*>(S.B + (NDIG - 1 - t) * B_TERM + off) = b[t];
   }
   return ovf;
 }
@@ -447,7 +449,6 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   tc_fence_after();
 
   const int s = p.sch.s;
-  const uint32_t idesc = idesc_bf16_f32(MT, p.n_mma);
   const uint32_t a_base = smem_u32(S.A), b_base = smem_u32(S.B);
   int abort = (S.status != kOk);
   int kick_no = 0;
@@ -484,25 +485,23 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       if (tid == 0) {
         if (!to) {
           tc_fence_after();
-          // orders 0..3 of the digit products, each in its own accumulator. Descriptors are built
-          // once; the 14-bit start-address field (bits 0-13, in 16-byte units) is advanced
+          // digit a of A against the digit planes b = 3-a, ..., 0 of B, which lie contiguous from
+          // plane position a (plane b is stored at position 3-b): one MMA of N = 64 (3-a) + n
+          // columns puts the product of order a+b into the accumulator at TMEM column 64 (3-a-b),
+          // so every group writes from column 0 and the first MMA clears all four. Descriptors are
+          // built once; the 14-bit start-address field (bits 0-13, in 16-byte units) is advanced
           // directly (shared addresses stay below 256 KB, so it never carries).
-          constexpr int kTa[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-          constexpr int kTb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-          constexpr int kOrd[10] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
-          constexpr bool kFirst[10] = {true, true, false, true, false, false,
-                                       true, false, false, false};
           const uint64_t a0 = smem_desc(a_base, A_LBO, A_SBO);
           const uint64_t b0 = smem_desc(b_base, B_LBO, B_SBO);
 #pragma unroll
-          for (int t = 0; t < 10; ++t) {
-            const uint64_t at = a0 + (uint64_t)((kTa[t] * A_TERM) >> 4);
-            const uint64_t bt = b0 + (uint64_t)((kTb[t] * B_TERM) >> 4);
-            const uint32_t dt = tmem + TM_D0 + 64u * kOrd[t];
+          for (int a = 0; a < NDIG; ++a) {
+            const uint64_t at = a0 + (uint64_t)((a * A_TERM) >> 4);
+            const uint64_t bt = b0 + (uint64_t)((a * B_TERM) >> 4);
+            const uint32_t id = idesc_bf16_f32(MT, NC * (NDIG - 1 - a) + p.n_mma);
 #pragma unroll
             for (int ks = 0; ks < KS; ++ks)
-              mma_bf16(dt, at + (uint64_t)(ks * ((2 * A_LBO) >> 4)),
-                       bt + (uint64_t)(ks * ((2 * B_LBO) >> 4)), idesc, !(kFirst[t] && ks == 0));
+              mma_bf16(tmem, at + (uint64_t)(ks * ((2 * A_LBO) >> 4)),
+                       bt + (uint64_t)(ks * ((2 * B_LBO) >> 4)), id, !(a == 0 && ks == 0));
           }
         }
         mma_commit(&S.bar_mma);
