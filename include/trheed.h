@@ -67,8 +67,9 @@ enum trh_integrator {
 
 enum trh_precision {
   TRH_FP64  = 0, /* every product, update and solve in IEEE binary64                            */
-  TRH_MIXED = 1  /* U*Q products on the BF16 tensor cores as a 3-term split with FP32
-                    accumulation; state, RHST and final solve in higher precision (see
+  TRH_MIXED = 1  /* U*Q products on the BF16 tensor cores as fixed-point digit products (four
+                    8-bit digits per operand, FP32 accumulators that never round); state as
+                    FP32 pairs, RHST in FP32 plus double-float, final solve in binary64 (see
                     trh_rocking_curve)                                                           */
 };
 
@@ -122,14 +123,17 @@ typedef struct trh_stats {
   int bulk_periods;       /* bulk periods the last bulk computation needed (largest over angles;
                              0 without a bulk or when the cached one was reused)                 */
   double ms_bulk;         /* device time of that bulk computation (0 if none ran)               */
+  int column_split;       /* mixed path: 1 if the last call ran two CTAs per (set, angle) pair
+                             (trh_set_column_split), else 0                                    */
 } trh_stats;
 
 /* Create a context for one beam set and method. Validates and copies `p` (the caller may free
  * its arrays afterwards), allocates device tables for one parameter set (the default structure
  * p->atoms, p->dw) and builds the host-side geometry (reciprocal rods, difference map U_jk ->
  * u_{g_j - g_k}, kick positions of the integrator).
- * Errors: TRH_EINVAL (see field comments; N > 64 on the FP64 path and N > 64 on the mixed path
- * are TRH_EUNSUPPORTED in this build), TRH_ENOMEM, TRH_ECUDA. On error *out is NULL. */
+ * Errors: TRH_EINVAL (see field comments), TRH_EUNSUPPORTED (N > 256 on the FP64 path, N > 64
+ * on the mixed path, RK4 or the conventional method on the mixed path), TRH_ENOMEM, TRH_ECUDA.
+ * On error *out is NULL. */
 int trh_create(trh_ctx** out, const trh_problem* p);
 
 /* Replace the context's parameter sets: n_sets structures sharing the beam set, species table
@@ -180,6 +184,21 @@ int trh_rocking_curve(trh_ctx* ctx, int n_angles, const double* theta0, const do
 int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* dw,
                  const int* species, double period, int steps_per_period, int max_periods,
                  double tol);
+
+/* ---- mixed path: CTAs per (set, angle) pair ------------------------------------------------
+ * The kick and the drift act column by column (W_c = U Q_c, Section 3.4), so on the mixed path
+ * the columns of one pair can be shared by the two CTAs of a thread-block cluster, 32 each. They
+ * exchange the Varah row sums once per step, the column halves of Q and P at every RHST
+ * (Section 3.2: each CTA inverts the whole Q and transforms its own columns) and at the end
+ * (CTA 0 assembles rho). This shortens a pair's critical path but takes two SMs per pair:
+ * TRH_SPLIT_AUTO (the default) uses it when N > 32 and the call has at most (SM count / 2)
+ * pairs, TRH_SPLIT_OFF never, TRH_SPLIT_ON whenever N > 32. Results are identical either way:
+ * every column sees the same arithmetic, and the row sums are added in the same fixed order, so
+ * the RHST decisions coincide. Batches (trh_batch_*) always run one CTA per pair. A wait for the
+ * other CTA that runs out (about 2 s) ends the pair with TRH_ETIMEOUT.
+ * Errors: TRH_EINVAL (mode not one of the three). */
+enum trh_split_mode { TRH_SPLIT_AUTO = 0, TRH_SPLIT_OFF = 1, TRH_SPLIT_ON = 2 };
+int trh_set_column_split(trh_ctx* ctx, int mode);
 
 /* ---- reverse analysis ---------------------------------------------------------------------
  * The paper's motivation (Section 1) is the reverse analysis of measured curves: a structure

@@ -21,6 +21,7 @@ TRH_OK, TRH_EINVAL, TRH_EGRAZING, TRH_ESINGULAR = 0, -1, -2, -3
 TRH_ETIMEOUT, TRH_ENOMEM, TRH_ECUDA, TRH_EUNSUPPORTED, TRH_ENOCONV = -4, -5, -6, -7, -8
 INTEGRATORS = {"sp4": 0, "sp6": 1, "rk4": 2, "conventional": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+SPLIT_MODES = {"auto": 0, "off": 1, "on": 2}
 
 
 class TrhProblem(C.Structure):
@@ -43,7 +44,7 @@ class TrhStats(C.Structure):
         ("kernels_launched", C.c_int), ("ms_last", C.c_double),
         ("ms_potential", C.c_double), ("ms_integrate", C.c_double),
         ("ms_gradient", C.c_double), ("wide_tile", C.c_int), ("graph_replay", C.c_int),
-        ("bulk_periods", C.c_int), ("ms_bulk", C.c_double),
+        ("bulk_periods", C.c_int), ("ms_bulk", C.c_double), ("column_split", C.c_int),
     ]
 
     def as_dict(self):
@@ -90,6 +91,7 @@ def load():
     lib.trh_set_fit.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.c_int]
     lib.trh_set_bulk.argtypes = [vp, C.c_int, vp, vp, vp, C.c_double, C.c_int, C.c_int,
                                  C.c_double]
+    lib.trh_set_column_split.argtypes = [vp, C.c_int]
     lib.trh_curve_jacobian.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     lib.trh_rfactor_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.trh_batch_create.argtypes = [C.POINTER(vp)]
@@ -99,7 +101,7 @@ def load():
     lib.trh_batch_destroy.argtypes = [vp]
     lib.trh_batch_destroy.restype = None
     for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query", "trh_set_fit",
-              "trh_curve_jacobian", "trh_rfactor_grad", "trh_set_bulk", "trh_batch_create",
+              "trh_curve_jacobian", "trh_rfactor_grad", "trh_set_bulk", "trh_set_column_split", "trh_batch_create",
               "trh_batch_add",
               "trh_batch_run", "trh_batch_query"):
         getattr(lib, f).restype = C.c_int
@@ -267,6 +269,11 @@ class Engine:
         _check(self.lib.trh_set_bulk(self.ctx, a.shape[0], _ptr(a), _ptr(d), _ptr(sp),
                                      float(period), int(steps_per_period), int(max_periods),
                                      float(tol)))
+
+    def set_column_split(self, mode: str = "auto"):
+        """Mixed path: two CTAs per (set, angle) pair ("on"), one ("off"), or two when the
+        call's pairs fit on half the SMs ("auto", the default). Results are identical."""
+        _check(self.lib.trh_set_column_split(self.ctx, SPLIT_MODES[mode]))
 
     def set_fit(self, free_atoms, dw_class=None, ckpt_every: int = 64):
         """Fit parameters for curve_jacobian / rfactor_grad: z of the atoms ``free_atoms`` and

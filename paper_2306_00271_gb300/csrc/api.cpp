@@ -155,6 +155,7 @@ struct trh_ctx {
   DevBuf<int> d_species, d_lmap, d_status;
   DevBuf<unsigned char> d_img;
   DevBuf<double2> d_wide;         // state of the wide FP64 kernel (N > 64)
+  int split_mode = TRH_SPLIT_AUTO;  // mixed path: two CTAs per pair (trh_set_column_split)
   std::vector<int> h_status;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   trh_stats stats{};
@@ -489,6 +490,19 @@ static trh::IntegrateParams integrate_params(trh_ctx* c, int n_angles, size_t pa
   return ip;
 }
 
+// Mixed path: whether a call of `pairs` (set, angle) pairs runs with two CTAs per pair. The
+// split halves every CTA's kick work but needs twice the SMs, so AUTO takes it when one wave of
+// two-CTA clusters still fits on the device; 32 beams or fewer leave the second CTA no column.
+static bool use_split(const trh_ctx* c, size_t pairs) {
+  if (c->precision != TRH_MIXED || c->N <= 32 || c->split_mode == TRH_SPLIT_OFF) return false;
+  if (c->split_mode == TRH_SPLIT_ON) return true;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  return 2 * pairs <= (size_t)sms;
+}
+
 static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParams& ip) {
   trh::MixedParams mp{};
   mp.sch = ip.sch;
@@ -599,6 +613,16 @@ static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* s
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_wide_tile[2 * c->N + ip.method] = best_tile;
   *tile = best_tile;
+  return TRH_OK;
+}
+
+int trh_set_column_split(trh_ctx* c, int mode) {
+  if (!c) return TRH_EINVAL;
+  if (mode != TRH_SPLIT_AUTO && mode != TRH_SPLIT_OFF && mode != TRH_SPLIT_ON) {
+    trh::set_last_error("trh_set_column_split: mode must be TRH_SPLIT_AUTO, _OFF or _ON");
+    return TRH_EINVAL;
+  }
+  c->split_mode = mode;
   return TRH_OK;
 }
 
@@ -789,10 +813,11 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
     rc = tune_wide_tile(c, ip, c->d_wide.p, st, &tile);
     if (rc != TRH_OK) return rc;
   }
+  const bool split = use_split(c, pairs);
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
     trh::MixedParams mp = mixed_params(c, ip);
-    TRH_CUDA(trh::launch_integrate_mixed(mp, st, &launched));
+    TRH_CUDA(trh::launch_integrate_mixed(mp, split, st, &launched));
   } else if (!wide) {
     TRH_CUDA(trh::launch_integrate_fp64(ip, st, &launched));
   } else {
@@ -813,6 +838,7 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
   S.ms_gradient = 0.0;
   S.wide_tile = tile;
+  S.column_split = split ? 1 : 0;
   S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
                   .count();
   if (S.n_bad) return bad_pairs_error(c);
@@ -926,12 +952,16 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   ip.ckpt = c->d_ckpt.p;
   ip.ckpt_every = C;
   ip.n_ckpt = n_seg + 1;
+  bool split = false;
+  c->stats.column_split = 0;
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
     // mixed forward: curve and checkpoints from the double-float state; every segment is then
     // recomputed on the binary64 path from its checkpoint, so the reverse map stays consistent
     // with the trajectory it differentiates
-    TRH_CUDA(trh::launch_integrate_mixed(mixed_params(c, ip), st, launched));
+    split = use_split(c, pairs);
+    TRH_CUDA(trh::launch_integrate_mixed(mixed_params(c, ip), split, st, launched));
+    c->stats.column_split = split ? 1 : 0;
   } else {
     TRH_CUDA(trh::launch_integrate_fp64(ip, st, launched));
   }

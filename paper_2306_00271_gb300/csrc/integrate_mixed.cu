@@ -50,7 +50,6 @@ namespace {
 using namespace umma;
 
 constexpr int NT = 512;
-constexpr int CPT = 16;                      // columns per thread
 constexpr int MT = 128;
 constexpr int KT = 128;
 constexpr int NC = 64;
@@ -65,11 +64,25 @@ constexpr int B_TERM = (NC / 8) * B_SBO;
 constexpr int TS = NC + 1;                   // row stride (float2) of T = Q^{-1} in the B region:
                                              // column walks hit 16 distinct bank pairs per phase
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t TM_D3 = 0, TM_D2 = 64, TM_D1 = 128, TM_D0 = 192;  // D_o at 64 (3 - o)
-constexpr uint32_t TM_QH = 256, TM_QL = 320, TM_PH = 384, TM_PL = 448;
+constexpr uint32_t TM_QH = 256, TM_QL = 320, TM_PH = 384, TM_PL = 448;  // full rows, RHST
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 constexpr double kPi = 3.14159265358979323846;
 constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23: x + M - M rounds x to an integer
+
+// Columns per thread (CP) and per CTA (NCOL): one CTA covers all 64 columns with 16 per thread,
+// or each CTA of a two-CTA cluster covers 32 columns with 8 per thread (column split). The
+// accumulator of digit order o sits at TMEM column NCOL (3 - o); B digit planes are NCOL wide.
+template <int CP>
+struct ColCfg {
+  static constexpr int NCOL = 4 * CP;
+  static constexpr int BT = (NCOL / 8) * B_SBO;  // one digit plane of B
+};
+// Column split: the exchange buffer (the other CTA's 32 columns of a double-float matrix, hi
+// then lo, [column][row]) lies in the B region after this CTA's four 32-column digit planes.
+constexpr int XB_OFF = NDIG * ColCfg<8>::BT;
+constexpr int XB_LO = 32 * MT;                   // floats from hi to lo
+static_assert(XB_OFF + 2 * XB_LO * 4 <= NDIG * B_TERM, "exchange buffer exceeds the B region");
+static_assert(NC * TS * 8 <= XB_OFF, "T overlaps the exchange buffer");
 
 struct __align__(128) Smem {
   unsigned char A[A_DIGITS];    // U(tau) digit planes; FP64 LU workspace at the end
@@ -78,18 +91,26 @@ struct __align__(128) Smem {
   float gamma[2][NC];           // column scales of B, by kick parity
   uint4 colmax[2][NC];          // per-quadrant column maxima of Q (float bits of |Q|), by parity
   int ovf;                      // a digit outgrew its scale (set before the end-of-kick barrier)
+  int ovfc[NC];                 // ... in that column
   int drained;                  // a pending image copy was waited for at the end of a pair
   uint64_t bar_tma, bar_mma;
+  uint64_t bar_x[2];            // column split: arrivals of the other CTA, alternating
   uint32_t tmem_base;
   int status, flag, n_rhst;
+  int xstatus;                  // column split: the other CTA's status at the end of a pair
   int piv[NC];
-  float rowsum[4][NC], diag[NC];
+  float rs8[8][NC];             // row sums of |Q_jk| over the 8-column groups k (Varah bound)
+  float xrow[2][2][NC];         // [step parity][CTA or column half] row sums of its 32 columns
+  float xdiag[2][NC];           // [step parity] |Q_jj|
   float redf[4];
   double gam2[NC], Gr[NC], Gi[NC];
   float2 frow[NC], fcol[NC], oldk[NC];
   double2 xv[NC], rv[NC];
   double psum[4][MT];
 };
+
+static_assert(sizeof(Smem) + sizeof(MixedParams) + 16 + 1024 <= 232448,
+              "shared memory above the 227 KB a CTA may use");
 
 // Error-free transformations. The explicit _rn intrinsics are never contracted into FMAs: a
 // contraction would make the rounded sum differ from the one the error term assumes.
@@ -134,45 +155,54 @@ __device__ __forceinline__ void digits4(float x, float inv_scale, uint16_t (&b)[
 }
 
 // Column maxima of this warp's 32 rows of |Qh|, one lane per column, into colmax[par][c][qd].
-__device__ __forceinline__ void column_maxima(Smem& S, const float (&qh)[CPT], int c0, int qd,
+template <int CP>
+__device__ __forceinline__ void column_maxima(Smem& S, const float (&qh)[CP], int c0, int qd,
                                               int lane, int par) {
 #pragma unroll
-  for (int i = 0; i < CPT; ++i) {
+  for (int i = 0; i < CP; ++i) {
     const uint32_t mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(qh[i])));
     if (lane == i) reinterpret_cast<uint32_t*>(&S.colmax[par][c0 + i])[qd] = mx;
   }
 }
 
-// Digits of B from qh with the column scales taken from colmax[spar]; the scales are published
-// in gamma[gpar] for the epilogue that reads the product. Returns true if some |x| / scale > 2
-// (the fixed-point format tolerates |d0| <= 256: every accumulator stays below 2^24).
-__device__ __forceinline__ bool digits_b(Smem& S, const float (&qh)[CPT], int m, int c0, int qd,
-                                         int lane, int spar, int gpar) {
-  bool ovf = false;
+// Digits of B from qh with the column scales taken from colmax[spar], for the columns c0 + i
+// with bit i of `cols` set; the scales are published in gamma[gpar] for the epilogue that reads
+// the product. Returns the mask of those columns where some |x| / scale > 2 (the fixed-point
+// format tolerates |d0| <= 256: every accumulator stays below 2^24). Column c is column
+// c % NCOL of this CTA's B planes.
+template <int CP>
+__device__ __forceinline__ uint32_t digits_b(Smem& S, const float (&qh)[CP], int m, int c0,
+                                             int qd, int lane, int spar, int gpar,
+                                             uint32_t cols = ~0u) {
+  constexpr int NCOL = ColCfg<CP>::NCOL, BT = ColCfg<CP>::BT;
+  uint32_t ovf = 0;
 #pragma unroll
-  for (int i = 0; i < CPT; ++i) {
+  for (int i = 0; i < CP; ++i) {
+    if (!((cols >> i) & 1u)) continue;
     const int c = c0 + i;
     const uint4 q4 = S.colmax[spar][c];
     const float g = pow2_ceil(__uint_as_float(max(max(q4.x, q4.y), max(q4.z, q4.w))));
     if (qd == 0 && lane == i) S.gamma[gpar][c] = g;
     const float inv = pow2_inv(g);
-    ovf |= fabsf(qh[i]) * inv > 2.0f;
+    if (fabsf(qh[i]) * inv > 2.0f) ovf |= 1u << i;
     uint16_t b[NDIG];
     digits4(qh[i], inv, b);
-    const int off = (c >> 3) * B_SBO + (m >> 3) * B_LBO + (c & 7) * 16 + (m & 7) * 2;
+    const int cl = c & (NCOL - 1);
+    const int off = (cl >> 3) * B_SBO + (m >> 3) * B_LBO + (cl & 7) * 16 + (m & 7) * 2;
 #pragma unroll
     for (int t = 0; t < NDIG; ++t)  // digit t in plane position 3 - t
-      *reinterpret_cast<uint16_t*>(S.B + (NDIG - 1 - t) * B_TERM + off) = b[t];
+      *reinterpret_cast<uint16_t*>(S.B + (NDIG - 1 - t) * BT + off) = b[t];
   }
   return ovf;
 }
 
 // Exact variant: maxima of qh itself (one block barrier), digits, scales into gamma[par].
-__device__ __forceinline__ void write_b_exact(Smem& S, const float (&qh)[CPT], int m, int c0,
+template <int CP>
+__device__ __forceinline__ void write_b_exact(Smem& S, const float (&qh)[CP], int m, int c0,
                                               int qd, int lane, int par) {
-  column_maxima(S, qh, c0, qd, lane, par);
+  column_maxima<CP>(S, qh, c0, qd, lane, par);
   __syncthreads();
-  digits_b(S, qh, m, c0, qd, lane, par, par);
+  digits_b<CP>(S, qh, m, c0, qd, lane, par, par);
 }
 
 // Two 32x32b.x8 loads, one wait.
@@ -206,6 +236,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
       : "memory");
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CP>
+__device__ __forceinline__ void tmem_ldx2(uint32_t ta, float (&va)[CP], uint32_t tb,
+                                          float (&vb)[CP]) {
+  if constexpr (CP == 16) tmem_ld16x2(ta, va, tb, vb);
+  else tmem_ld8x2(ta, va, tb, vb);
+}
+template <int CP>
+__device__ __forceinline__ void tmem_stx(uint32_t ta, const float (&v)[CP]) {
+  if constexpr (CP == 16) tmem_st16(ta, v);
+  else tmem_st8(ta, v);
 }
 
 // In-place inverse of the n x n complex FP32 matrix T (row stride TS) by Gauss-Jordan elimination
@@ -296,14 +338,15 @@ __device__ __forceinline__ void gj_invert(Smem& S, float2* T, int n) {
   }
 }
 
-// out = Z T for this thread's part of row j and its CPT columns, Z read from TMEM (hi at col_h,
-// lo at col_l) in double-float, T (FP32) from shared memory; products are exact (FMA residual)
-// and summed with error-free additions.
+// out = Z T for this thread's part of row j and its CP columns c0.., Z read from TMEM (full rows,
+// hi at col_h, lo at col_l) in double-float, T (FP32) from shared memory; products are exact
+// (FMA residual) and summed with error-free additions.
+template <int CP>
 __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32_t col_h,
                                         uint32_t col_l, int part, int c0, int n,
-                                        float (&oh)[CPT], float (&ol)[CPT]) {
+                                        float (&oh)[CP], float (&ol)[CP]) {
 #pragma unroll
-  for (int i = 0; i < CPT; ++i) oh[i] = ol[i] = 0.0f;
+  for (int i = 0; i < CP; ++i) oh[i] = ol[i] = 0.0f;
   for (int kc = 0; kc < n; kc += 8) {
     float zh[8], zl[8], ph[8], pl[8];
     tmem_ld8x2(t_lane + col_h + kc, zh, t_lane + col_l + kc, zl);
@@ -321,7 +364,7 @@ __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32
       const float x2h = part ? zih : -zih, x2l = part ? zil : -zil;
       const float2* Trow = T + (kc + kk) * TS + c0;
 #pragma unroll
-      for (int i = 0; i < CPT; ++i) {
+      for (int i = 0; i < CP; ++i) {
         const float2 t = Trow[i];
         const float y1 = part ? t.y : t.x;
         const float y2 = part ? t.x : t.y;
@@ -340,7 +383,7 @@ __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32
     }
   }
 #pragma unroll
-  for (int i = 0; i < CPT; ++i) {
+  for (int i = 0; i < CP; ++i) {
     float s, e;
     quick_two_sum(oh[i], ol[i], s, e);
     const bool live = (c0 + i) < n;
@@ -356,6 +399,8 @@ __device__ __forceinline__ uint32_t mixed_prologue(Smem& S) {
   if (threadIdx.x == 0) {
     mbar_init(&S.bar_tma, 1);
     mbar_init(&S.bar_mma, 1);
+    mbar_init(&S.bar_x[0], 1);
+    mbar_init(&S.bar_x[1], 1);
     mbar_fence_init();
   }
   if ((threadIdx.x >> 5) == 0) tmem_alloc(&S.tmem_base, TMEM_COLS);
@@ -372,15 +417,108 @@ __device__ __forceinline__ void mixed_epilogue(Smem& S, uint32_t tmem) {
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// rho and eta of one pair from the final Q and P (double-float pairs; this thread's part of row j
+// and the 16 columns 16 cq ..), in FP64: A0 = Gamma Q - i P, x = A0^{-1} e_1 with one step of
+// iterative refinement, rho = B0 x with B0 = Gamma Q + i P (Eq. vrhocomp), eta (Section 2.1).
+__device__ __forceinline__ void mixed_assemble(Smem& S, const MixedParams& p, size_t pair,
+                                               double sin_t0, const float (&Qh)[16],
+                                               const float (&Ql)[16], const float (&Ph)[16],
+                                               const float (&Pl)[16]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cq = warp >> 2, m = 32 * (warp & 3) + lane;
+  const int j = m >> 1, part = m & 1;
+  const int c0 = 16 * cq;
+  const int N = p.N;
+  const double gr = (j < N) ? S.Gr[j] : 0.0, gi = (j < N) ? S.Gi[j] : 0.0;
+  double2* LU = reinterpret_cast<double2*>(S.A);
+  // sign = -1: A0 = Gamma Q - i P ; sign = +1: B0 = Gamma Q + i P (complex entry of (j, c0+c))
+  auto entry = [&](int c, double sign) {
+    const double qv = (double)Qh[c] + (double)Ql[c];
+    const double pv = (double)Ph[c] + (double)Pl[c];
+    const double qo = __shfl_xor_sync(0xffffffffu, qv, 1);
+    const double po = __shfl_xor_sync(0xffffffffu, pv, 1);
+    const double qr = part ? qo : qv, qi = part ? qv : qo;
+    const double pr = part ? po : pv, pi = part ? pv : po;
+    return make_double2(gr * qr - gi * qi - sign * pi, gr * qi + gi * qr + sign * pr);
+  };
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const double2 a = entry(c, -1.0);
+    if (j < N && c0 + c < N)
+      reinterpret_cast<double*>(&LU[j * NC + c0 + c])[part] = part ? a.y : a.x;
+  }
+  __syncthreads();
+  dense::lu_factor(LU, NC, N, S.piv, &S.status, nullptr, nullptr);
+  if (S.status != kOk) return;
+  if (warp == 0) {
+    for (int k = lane; k < N; k += 32) S.xv[k] = make_double2(k == 0 ? 1.0 : 0.0, 0.0);
+    __syncwarp();
+    dense::lu_solve_warp(LU, NC, N, S.piv, S.xv);
+  }
+  __syncthreads();
+  // pass 0: residual r = e_1 - A0 x and one correction; pass 1: rho = B0 x
+  for (int pass = 0; pass < 2; ++pass) {
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const double2 a = entry(c, pass == 0 ? -1.0 : 1.0);
+      if (c0 + c < N) {
+        const double2 x = S.xv[c0 + c];
+        acc += part ? (a.x * x.y + a.y * x.x) : (a.x * x.x - a.y * x.y);
+      }
+    }
+    S.psum[cq][m] = acc;
+    __syncthreads();
+    if (pass == 0) {
+      if (tid < N) {
+        const double re = (S.psum[0][2 * tid] + S.psum[1][2 * tid]) +
+                          (S.psum[2][2 * tid] + S.psum[3][2 * tid]);
+        const double im = (S.psum[0][2 * tid + 1] + S.psum[1][2 * tid + 1]) +
+                          (S.psum[2][2 * tid + 1] + S.psum[3][2 * tid + 1]);
+        S.rv[tid] = make_double2((tid == 0 ? 1.0 : 0.0) - re, -im);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        dense::lu_solve_warp(LU, NC, N, S.piv, S.rv);
+        for (int k = lane; k < N; k += 32)
+          S.xv[k] = make_double2(S.xv[k].x + S.rv[k].x, S.xv[k].y + S.rv[k].y);
+      }
+      __syncthreads();
+    } else if (tid < N) {
+      const double re = (S.psum[0][2 * tid] + S.psum[1][2 * tid]) +
+                        (S.psum[2][2 * tid] + S.psum[3][2 * tid]);
+      const double im = (S.psum[0][2 * tid + 1] + S.psum[1][2 * tid + 1]) +
+                        (S.psum[2][2 * tid + 1] + S.psum[3][2 * tid + 1]);
+      p.out.rho[pair * N + tid] = make_double2(re, im);
+      const double g2 = S.gam2[tid];
+      p.out.eta[pair * N + tid] =
+          (g2 > 0.0) ? (re * re + im * im) * sin_t0 * sqrt(S.gam2[0]) / sqrt(g2) : 0.0;
+    }
+  }
+}
+
 // Integrates one (set, angle) pair. The mbarrier phases carry over from pair to pair.
-template <int KS>
+//
+// SPLIT: the two CTAs of a cluster share the pair, CTA r owning columns 32 r .. 32 r + 31 of Q
+// and P. A column of the kick and the drift needs only the same column (W_c = U Q_c), so the
+// kicks run without communication; each step exchanges the CTAs' row sums for the Varah bound
+// (both then take the same RHST decision from the same numbers), an RHST exchanges the column
+// halves of Q and P (every CTA inverts the full Q and applies T to its own columns), and at the
+// end CTA 0 receives the other half and assembles rho. Every exchange is a remote mbarrier
+// arrival and a bounded wait; a wait that runs out ends the pair with TRH_ETIMEOUT.
+template <int KS, bool SPLIT>
 __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int angle, int set,
-                                           uint32_t tmem, uint32_t& ph_tma, uint32_t& ph_mma) {
+                                           uint32_t tmem, uint32_t& ph_tma, uint32_t& ph_mma,
+                                           uint32_t& xk) {
+  constexpr int CP = SPLIT ? 8 : 16;
+  constexpr int NCOL = ColCfg<CP>::NCOL;
+  constexpr int BT = ColCfg<CP>::BT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int qd = warp & 3, cq = warp >> 2;
   const int m = 32 * qd + lane;  // real-ified row = TMEM lane
   const int j = m >> 1, part = m & 1;
-  const int c0 = CPT * cq;
+  const uint32_t rank = SPLIT ? cluster_ctarank() : 0u, peer = rank ^ 1u;
+  const int c0 = NCOL * (int)rank + CP * cq;  // this thread's first column (of all N)
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   const unsigned char* img_set = p.img + (size_t)set * p.n_nodes * IMG_BYTES;
@@ -416,12 +554,12 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   const float g2h = (float)g2d, g2l = (float)(g2d - (double)g2h);
 
   // initial value [I; i Gamma], or [I; X] with a bulk boundary condition X
-  float Qh[CPT], Ql[CPT], Ph[CPT], Pl[CPT];
+  float Qh[CP], Ql[CP], Ph[CP], Pl[CP];
   {
     const double pv = (j < N) ? (part ? S.Gr[j] : -S.Gi[j]) : 0.0;
     const double2* x0 = p.p0 ? p.p0 + (size_t)angle * N * N : nullptr;
 #pragma unroll
-    for (int i = 0; i < CPT; ++i) {
+    for (int i = 0; i < CP; ++i) {
       const bool dg = (j < N) && (c0 + i == j);
       double v = dg ? pv : 0.0;
       if (x0 && j < N && c0 + i < N) {
@@ -435,7 +573,8 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
     }
   }
   if (tid == 0) S.ovf = 0;
-  write_b_exact(S, Qh, m, c0, qd, lane, 0);
+  if (tid < NC) S.ovfc[tid] = 0;
+  write_b_exact<CP>(S, Qh, m, c0, qd, lane, 0);
   fence_proxy_async_smem();
   bool tma_pending = false;
   if (tid == 0 && S.status == kOk) {
@@ -453,13 +592,84 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   int abort = (S.status != kOk);
   int kick_no = 0;
 
+  // ---- column split: exchanges with the other CTA ----
+  // Every thread has written its part of the payload into the other CTA's shared memory; one
+  // release arrival on that CTA's mbarrier, then a bounded acquire wait on this CTA's. The two
+  // mbarriers alternate so that the other CTA, one exchange ahead, never completes a phase
+  // twice before it is waited for; a buffer is written again only after an exchange that the
+  // receiver entered after reading it. Returns false (for every thread) after a timed-out wait.
+  auto exchange = [&]() -> bool {
+    fence_acq_rel_cluster();
+    __syncthreads();
+    const int slot = (int)(xk & 1u);
+    if (tid == 0) mbar_arrive_remote(mapa_u32(smem_u32(&S.bar_x[slot]), peer));
+    const bool ok = mbar_wait_cluster(&S.bar_x[slot], (xk >> 1) & 1u, kWaitCycles);
+    ++xk;
+    return __syncthreads_and(ok) != 0;
+  };
+  const uint32_t xb_peer = SPLIT ? mapa_u32(smem_u32(S.B + XB_OFF), peer) : 0u;
+  const float* xb = reinterpret_cast<const float*>(S.B + XB_OFF);
+  // this thread's columns of a double-float matrix into the other CTA's exchange buffer
+  auto send_half = [&](const float (&h)[CP], const float (&l)[CP]) {
+#pragma unroll
+    for (int i = 0; i < CP; ++i) {
+      const uint32_t at = xb_peer + 4u * (uint32_t)((CP * cq + i) * MT + m);
+      st_cluster_f32(at, h[i]);
+      st_cluster_f32(at + 4u * XB_LO, l[i]);
+    }
+  };
+  // Full rows of Q and P in TMEM (TM_QH .. TM_PL): this CTA's columns and, with SPLIT, the other
+  // CTA's (exchanges: Q, buffer read, P, buffer read); with T, Q's high part also into T.
+  auto gather = [&](float2* T) -> bool {
+    tmem_stx<CP>(t_lane + TM_QH + c0, Qh);
+    tmem_stx<CP>(t_lane + TM_QL + c0, Ql);
+    tmem_stx<CP>(t_lane + TM_PH + c0, Ph);
+    tmem_stx<CP>(t_lane + TM_PL + c0, Pl);
+    if (T) {
+#pragma unroll
+      for (int c = 0; c < CP; ++c)
+        if (j < N && c0 + c < N) reinterpret_cast<float*>(&T[j * TS + c0 + c])[part] = Qh[c];
+    }
+    if constexpr (SPLIT) {
+      const int cp0 = NCOL * (int)peer + CP * cq;  // the other CTA's columns of this thread
+      // one matrix: send this CTA's half, receive the other's into TMEM (and T), then confirm
+      // that the buffer has been read
+      auto swap_half = [&](const float (&h)[CP], const float (&l)[CP], uint32_t col_h,
+                           uint32_t col_l, float2* Tq) -> bool {
+        send_half(h, l);
+        if (!exchange()) return false;
+        float rh[CP], rl[CP];
+#pragma unroll
+        for (int i = 0; i < CP; ++i) {
+          rh[i] = xb[(CP * cq + i) * MT + m];
+          rl[i] = xb[XB_LO + (CP * cq + i) * MT + m];
+        }
+        tmem_stx<CP>(t_lane + col_h + cp0, rh);
+        tmem_stx<CP>(t_lane + col_l + cp0, rl);
+        if (Tq) {
+#pragma unroll
+          for (int c = 0; c < CP; ++c)
+            if (j < N && cp0 + c < N) reinterpret_cast<float*>(&Tq[j * TS + cp0 + c])[part] = rh[c];
+        }
+        return exchange();
+      };
+      const bool ok = swap_half(Qh, Ql, TM_QH, TM_QL, T) && swap_half(Ph, Pl, TM_PH, TM_PL, nullptr);
+      if (!ok) {
+        tmem_wait_st();
+        return false;
+      }
+    }
+    tmem_wait_st();
+    return true;
+  };
+
   // [Q; P] as binary64 (hi + lo) into checkpoint slot `slot` (for the reverse sweep)
   auto checkpoint = [&](int slot) {
     if (j >= N) return;
     const size_t NN = (size_t)N * N;
     double2* dst = p.ckpt + ((size_t)pair * p.n_ckpt + slot) * 2 * NN;
 #pragma unroll
-    for (int c = 0; c < CPT; ++c)
+    for (int c = 0; c < CP; ++c)
       if (c0 + c < N) {
         reinterpret_cast<double*>(&dst[(size_t)j * N + c0 + c])[part] = (double)Qh[c] + (double)Ql[c];
         reinterpret_cast<double*>(&dst[NN + (size_t)j * N + c0 + c])[part] =
@@ -486,18 +696,19 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
         if (!to) {
           tc_fence_after();
           // digit a of A against the digit planes b = 3-a, ..., 0 of B, which lie contiguous from
-          // plane position a (plane b is stored at position 3-b): one MMA of N = 64 (3-a) + n
-          // columns puts the product of order a+b into the accumulator at TMEM column 64 (3-a-b),
-          // so every group writes from column 0 and the first MMA clears all four. Descriptors are
-          // built once; the 14-bit start-address field (bits 0-13, in 16-byte units) is advanced
-          // directly (shared addresses stay below 256 KB, so it never carries).
+          // plane position a (plane b is stored at position 3-b): one MMA of N = NCOL (3-a) + n
+          // columns puts the product of order a+b into the accumulator at TMEM column
+          // NCOL (3-a-b), so every group writes from column 0 and the first MMA clears all four.
+          // Descriptors are built once; the 14-bit start-address field (bits 0-13, in 16-byte
+          // units) is advanced directly (shared addresses stay below 256 KB, so it never carries).
           const uint64_t a0 = smem_desc(a_base, A_LBO, A_SBO);
           const uint64_t b0 = smem_desc(b_base, B_LBO, B_SBO);
+          const int n_last = SPLIT ? NCOL : p.n_mma;
 #pragma unroll
           for (int a = 0; a < NDIG; ++a) {
             const uint64_t at = a0 + (uint64_t)((a * A_TERM) >> 4);
-            const uint64_t bt = b0 + (uint64_t)((a * B_TERM) >> 4);
-            const uint32_t id = idesc_bf16_f32(MT, NC * (NDIG - 1 - a) + p.n_mma);
+            const uint64_t bt = b0 + (uint64_t)((a * BT) >> 4);
+            const uint32_t id = idesc_bf16_f32(MT, NCOL * (NDIG - 1 - a) + n_last);
 #pragma unroll
             for (int ks = 0; ks < KS; ++ks)
               mma_bf16(tmem, at + (uint64_t)(ks * ((2 * A_LBO) >> 4)),
@@ -516,19 +727,20 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
         bulk_g2s(S.alpha[(kick_no + 1) & 1], img + A_DIGITS, A_SCALES, &S.bar_tma);
         tma_pending = true;
       }
-      // epilogue: W from the three exact accumulators, kick P -= hb W + (hb Gamma_j^2) Q with
+      // epilogue: W from the four exact accumulators, kick P -= hb W + (hb Gamma_j^2) Q with
       // the Gamma^2 term in double-float, drift Q += ha P (double-float)
       // acc = D_0 + 2^-8 (D_1 + 2^-8 (D_2 + 2^-8 D_3)), folded as the accumulators arrive
       constexpr float kQ = 0.00390625f;  // 2^-8
-      float acc[CPT], dt[CPT];
-      tmem_ld16x2(t_lane + TM_D3 + c0, acc, t_lane + TM_D2 + c0, dt);
+      const uint32_t t_acc = t_lane + CP * cq;  // accumulator columns are this CTA's
+      float acc[CP], dt[CP];
+      tmem_ldx2<CP>(t_acc + 0 * NCOL, acc, t_acc + 1 * NCOL, dt);  // D_3, D_2
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
+      for (int c = 0; c < CP; ++c) acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
       {
-        float d1[CPT];
-        tmem_ld16x2(t_lane + TM_D1 + c0, d1, t_lane + TM_D0 + c0, dt);
+        float d1[CP];
+        tmem_ldx2<CP>(t_acc + 2 * NCOL, d1, t_acc + 3 * NCOL, dt);  // D_1, D_0
 #pragma unroll
-        for (int c = 0; c < CPT; ++c)
+        for (int c = 0; c < CP; ++c)
           acc[c] = __fadd_rn(dt[c], __fmul_rn(__fadd_rn(d1[c], __fmul_rn(acc[c], kQ)), kQ));
       }
       const float hbh = p.kick_hi[kidx], hbl = p.kick_lo[kidx];
@@ -543,7 +755,7 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       const float hah = last ? 0.0f : p.drift_hi[r], hal = last ? 0.0f : p.drift_lo[r];
       const float wscale = alpha_m * (1.0f / 16384.0f);
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
+      for (int c = 0; c < CP; ++c) {
         if (c0 + c >= N) continue;  // padding columns stay zero (TMEM there is never written)
         const float w = __fmul_rn(__fmul_rn(acc[c], S.gamma[kick_no & 1][c0 + c]), wscale);
         const float t1 = __fmul_rn(hbh, w);
@@ -569,19 +781,32 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       // maxima are complete since the previous barrier); the new maxima go to the other parity
       const int pc = kick_no & 1, pn = pc ^ 1;
       if (!last) {
-        column_maxima(S, Qh, c0, qd, lane, pn);
-        if (digits_b(S, Qh, m, c0, qd, lane, pc, pn)) S.ovf = 1;
+        column_maxima<CP>(S, Qh, c0, qd, lane, pn);
+        const uint32_t grew = digits_b<CP>(S, Qh, m, c0, qd, lane, pc, pn);
+        if (grew) {
+          S.ovf = 1;
+#pragma unroll
+          for (int c = 0; c < CP; ++c)
+            if ((grew >> c) & 1u) S.ovfc[c0 + c] = 1;
+        }
       }
       fence_proxy_async_smem();
       tc_fence_before();
       abort = __syncthreads_or(to);
       tc_fence_after();
       if (abort) break;
-      if (S.ovf) {  // a column grew more than twofold: redo with the exact maxima of the new Q
-        digits_b(S, Qh, m, c0, qd, lane, pn, pn);
+      if (S.ovf) {
+        // a column grew more than twofold: redo that column with the exact maxima of the new Q
+        // (column by column, so the result does not depend on how columns share a CTA)
+        uint32_t redo = 0;
+#pragma unroll
+        for (int c = 0; c < CP; ++c)
+          if (S.ovfc[c0 + c]) redo |= 1u << c;
+        digits_b<CP>(S, Qh, m, c0, qd, lane, pn, pn, redo);
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) S.ovf = 0;
+        if (tid < NC) S.ovfc[tid] = 0;
         __syncthreads();
       }
     }
@@ -590,26 +815,52 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       break;
     }
 
-    // badness xi of Q (FP32 Varah bound) after the step
+    // badness xi of Q (FP32 Varah bound) after the step. Row sums over 8-column groups, combined
+    // in a fixed tree (groups 0-3, groups 4-7, then the two halves), so that the one-CTA and the
+    // column-split forms take the same decisions from the same numbers.
     {
-      float sum = 0.0f, dg = 0.0f;
+      const int par = i & 1;
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        const float o = __shfl_xor_sync(0xffffffffu, Qh[c], 1);
-        const float a = sqrtf(Qh[c] * Qh[c] + o * o);
-        if (c0 + c < N) sum += a;
-        if (c0 + c == j) dg = a;
-      }
-      if (part == 0 && j < N) {
-        S.rowsum[cq][j] = sum;
-        if (j >= c0 && j < c0 + CPT) S.diag[j] = dg;
+      for (int h = 0; h < CP / 8; ++h) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int c = 8 * h; c < 8 * h + 8; ++c) {
+          const float o = __shfl_xor_sync(0xffffffffu, Qh[c], 1);
+          const float a = sqrtf(__fmaf_rn(Qh[c], Qh[c], __fmul_rn(o, o)));
+          if (c0 + c < N) sum = __fadd_rn(sum, a);
+          if (c0 + c == j && part == 0) {
+            S.xdiag[par][j] = a;
+            if (SPLIT) st_cluster_f32(mapa_u32(smem_u32(&S.xdiag[par][j]), peer), a);
+          }
+        }
+        if (part == 0 && j < N) S.rs8[(c0 >> 3) + h][j] = sum;
       }
       __syncthreads();
+      if (tid < N) {
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          if (SPLIT && hf != (int)rank) continue;
+          const int g = 4 * hf;
+          const float l = __fadd_rn(__fadd_rn(S.rs8[g][tid], S.rs8[g + 1][tid]),
+                                    __fadd_rn(S.rs8[g + 2][tid], S.rs8[g + 3][tid]));
+          S.xrow[par][hf][tid] = l;
+          if (SPLIT) st_cluster_f32(mapa_u32(smem_u32(&S.xrow[par][hf][tid]), peer), l);
+        }
+      }
+      if constexpr (SPLIT) {
+        if (!exchange()) {
+          if (tid == 0) S.status = kTimeout;
+          abort = 1;
+          break;
+        }
+      } else {
+        __syncthreads();
+      }
       if (warp < 2) {
         float rs = 0.0f, mg = INFINITY;
         if (tid < N) {
-          rs = (S.rowsum[0][tid] + S.rowsum[1][tid]) + (S.rowsum[2][tid] + S.rowsum[3][tid]);
-          mg = S.diag[tid] - (rs - S.diag[tid]);
+          rs = __fadd_rn(S.xrow[par][0][tid], S.xrow[par][1][tid]);
+          mg = S.xdiag[par][tid] - (rs - S.xdiag[par][tid]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -631,31 +882,28 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       __syncthreads();
     }
     if (S.flag) {
-      // RHST: T = Q^{-1} (FP32 Gauss-Jordan), Z <- Z T (double-float)
+      // RHST: T = Q^{-1} (FP32 Gauss-Jordan, every CTA of a split pair inverts the full Q),
+      // Z <- Z T (double-float) for this CTA's columns
       float2* T = reinterpret_cast<float2*>(S.B);
-#pragma unroll
-      for (int c = 0; c < CPT; ++c)
-        if (j < N && c0 + c < N) reinterpret_cast<float*>(&T[j * TS + c0 + c])[part] = Qh[c];
+      if (!gather(T)) {
+        if (tid == 0) S.status = kTimeout;
+        abort = 1;
+        break;
+      }
+      tc_fence_before();
       __syncthreads();
+      tc_fence_after();
       gj_invert(S, T, N);
       if (S.status != kOk) {
         abort = 1;
         break;
       }
-      tmem_st16(t_lane + TM_QH + c0, Qh);
-      tmem_st16(t_lane + TM_QL + c0, Ql);
-      tmem_st16(t_lane + TM_PH + c0, Ph);
-      tmem_st16(t_lane + TM_PL + c0, Pl);
-      tmem_wait_st();
+      apply_t<CP>(T, t_lane, TM_QH, TM_QL, part, c0, N, Qh, Ql);
+      apply_t<CP>(T, t_lane, TM_PH, TM_PL, part, c0, N, Ph, Pl);
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      apply_t(T, t_lane, TM_QH, TM_QL, part, c0, N, Qh, Ql);
-      apply_t(T, t_lane, TM_PH, TM_PL, part, c0, N, Ph, Pl);
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      write_b_exact(S, Qh, m, c0, qd, lane, kick_no & 1);
+      write_b_exact<CP>(S, Qh, m, c0, qd, lane, kick_no & 1);
       fence_proxy_async_smem();
       if (tid == 0) S.n_rhst++;
       tc_fence_before();
@@ -674,86 +922,45 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   __syncthreads();
   if (S.drained) ph_tma ^= 1;
 
-  if (S.status == kOk) {
-    // ---- assembly in FP64: A0 = Gamma Q - i P, x = A0^{-1} e_1 (+1 refinement), rho = B0 x
-    const double gr = (j < N) ? S.Gr[j] : 0.0, gi = (j < N) ? S.Gi[j] : 0.0;
-    double2* LU = reinterpret_cast<double2*>(S.A);
-    // sign = -1: A0 = Gamma Q - i P ; sign = +1: B0 = Gamma Q + i P (complex entry of (j, c0+c))
-    auto entry = [&](int c, double sign) {
-      const double qv = (double)Qh[c] + (double)Ql[c];
-      const double pv = (double)Ph[c] + (double)Pl[c];
-      const double qo = __shfl_xor_sync(0xffffffffu, qv, 1);
-      const double po = __shfl_xor_sync(0xffffffffu, pv, 1);
-      const double qr = part ? qo : qv, qi = part ? qv : qo;
-      const double pr = part ? po : pv, pi = part ? pv : po;
-      return make_double2(gr * qr - gi * qi - sign * pi, gr * qi + gi * qr + sign * pr);
-    };
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const double2 a = entry(c, -1.0);
-      if (j < N && c0 + c < N)
-        reinterpret_cast<double*>(&LU[j * NC + c0 + c])[part] = part ? a.y : a.x;
+  bool assemble_here = true;
+  if constexpr (SPLIT) {
+    // the other CTA's status and columns; CTA 0 assembles. After a timed-out wait the two CTAs
+    // are out of step: no further exchange (the other CTA's waits run out on their own).
+    assemble_here = (rank == 0);
+    if (S.status != kTimeout) {
+      if (tid == 0) st_cluster_s32(mapa_u32(smem_u32(&S.xstatus), peer), S.status);
+      const bool ok = gather(nullptr);
+      if (tid == 0) {
+        if (!ok) S.status = kTimeout;
+        else if (S.status == kOk) S.status = S.xstatus;
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (assemble_here) {
+    if (S.status == kOk) {
+      if constexpr (SPLIT) {
+        float aQh[16], aQl[16], aPh[16], aPl[16];
+        tmem_ld16x2(t_lane + TM_QH + 16 * cq, aQh, t_lane + TM_QL + 16 * cq, aQl);
+        tmem_ld16x2(t_lane + TM_PH + 16 * cq, aPh, t_lane + TM_PL + 16 * cq, aPl);
+        mixed_assemble(S, p, pair, sin_t0, aQh, aQl, aPh, aPl);
+      } else {
+        mixed_assemble(S, p, pair, sin_t0, Qh, Ql, Ph, Pl);
+      }
     }
     __syncthreads();
-    dense::lu_factor(LU, NC, N, S.piv, &S.status, nullptr, nullptr);
-    if (S.status == kOk) {
-      if (warp == 0) {
-        for (int k = lane; k < N; k += 32) S.xv[k] = make_double2(k == 0 ? 1.0 : 0.0, 0.0);
-        __syncwarp();
-        dense::lu_solve_warp(LU, NC, N, S.piv, S.xv);
-      }
-      __syncthreads();
-      // pass 0: residual r = e_1 - A0 x and one correction; pass 1: rho = B0 x
-      for (int pass = 0; pass < 2; ++pass) {
-        double acc = 0.0;
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          const double2 a = entry(c, pass == 0 ? -1.0 : 1.0);
-          if (c0 + c < N) {
-            const double2 x = S.xv[c0 + c];
-            acc += part ? (a.x * x.y + a.y * x.x) : (a.x * x.x - a.y * x.y);
-          }
-        }
-        S.psum[cq][m] = acc;
-        __syncthreads();
-        if (pass == 0) {
-          if (tid < N) {
-            const double re = (S.psum[0][2 * tid] + S.psum[1][2 * tid]) +
-                              (S.psum[2][2 * tid] + S.psum[3][2 * tid]);
-            const double im = (S.psum[0][2 * tid + 1] + S.psum[1][2 * tid + 1]) +
-                              (S.psum[2][2 * tid + 1] + S.psum[3][2 * tid + 1]);
-            S.rv[tid] = make_double2((tid == 0 ? 1.0 : 0.0) - re, -im);
-          }
-          __syncthreads();
-          if (warp == 0) {
-            dense::lu_solve_warp(LU, NC, N, S.piv, S.rv);
-            for (int k = lane; k < N; k += 32)
-              S.xv[k] = make_double2(S.xv[k].x + S.rv[k].x, S.xv[k].y + S.rv[k].y);
-          }
-          __syncthreads();
-        } else if (tid < N) {
-          const double re = (S.psum[0][2 * tid] + S.psum[1][2 * tid]) +
-                            (S.psum[2][2 * tid] + S.psum[3][2 * tid]);
-          const double im = (S.psum[0][2 * tid + 1] + S.psum[1][2 * tid + 1]) +
-                            (S.psum[2][2 * tid + 1] + S.psum[3][2 * tid + 1]);
-          p.out.rho[pair * N + tid] = make_double2(re, im);
-          const double g2 = S.gam2[tid];
-          p.out.eta[pair * N + tid] =
-              (g2 > 0.0) ? (re * re + im * im) * sin_t0 * sqrt(S.gam2[0]) / sqrt(g2) : 0.0;
-        }
+    if (S.status != kOk) {
+      for (int k = tid; k < N; k += NT) {
+        p.out.rho[pair * N + k] = make_double2(NAN, NAN);
+        p.out.eta[pair * N + k] = NAN;
       }
     }
-  }
-  __syncthreads();
-  if (S.status != kOk) {
-    for (int k = tid; k < N; k += NT) {
-      p.out.rho[pair * N + k] = make_double2(NAN, NAN);
-      p.out.eta[pair * N + k] = NAN;
+    if (tid == 0) {
+      p.out.status[pair] = S.status;
+      p.out.n_rhst[pair] = S.n_rhst;
     }
-  }
-  if (tid == 0) {
-    p.out.status[pair] = S.status;
-    p.out.n_rhst[pair] = S.n_rhst;
   }
   tc_fence_before();
   __syncthreads();
@@ -765,8 +972,22 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
   const uint32_t tmem = mixed_prologue(S);
-  uint32_t ph_tma = 0, ph_mma = 0;
-  mixed_pair<KS>(S, p, blockIdx.x, blockIdx.y, tmem, ph_tma, ph_mma);
+  uint32_t ph_tma = 0, ph_mma = 0, xk = 0;
+  mixed_pair<KS, false>(S, p, blockIdx.x, blockIdx.y, tmem, ph_tma, ph_mma, xk);
+  mixed_epilogue(S, tmem);
+}
+
+// Column split: a cluster of two CTAs (blockIdx.x = 2 angle + rank) per (set, angle) pair.
+template <int KS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 1)
+    k_integrate_mixed_split(MixedParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const uint32_t tmem = mixed_prologue(S);
+  cluster_sync();  // both CTAs' mbarriers are initialised before any remote arrival
+  uint32_t ph_tma = 0, ph_mma = 0, xk = 0;
+  mixed_pair<KS, true>(S, p, blockIdx.x >> 1, blockIdx.y, tmem, ph_tma, ph_mma, xk);
+  cluster_sync();  // no CTA exits while the other may still write to its shared memory
   mixed_epilogue(S, tmem);
 }
 
@@ -782,7 +1003,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_items(const MixedPara
   MixedParams& job = *reinterpret_cast<MixedParams*>(smem_raw + sizeof(Smem));
   int& next = *reinterpret_cast<int*>(smem_raw + sizeof(Smem) + sizeof(MixedParams));
   const uint32_t tmem = mixed_prologue(S);
-  uint32_t ph_tma = 0, ph_mma = 0;
+  uint32_t ph_tma = 0, ph_mma = 0, xk = 0;
   for (;;) {
     if (threadIdx.x == 0) next = atomicAdd(counter, 1);
     __syncthreads();
@@ -792,14 +1013,14 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_items(const MixedPara
     if (threadIdx.x == 0) job = jobs[w.x];
     __syncthreads();
     switch (job.k_slices) {
-      case 1: mixed_pair<1>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
-      case 2: mixed_pair<2>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
-      case 3: mixed_pair<3>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
-      case 4: mixed_pair<4>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
-      case 5: mixed_pair<5>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
-      case 6: mixed_pair<6>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
-      case 7: mixed_pair<7>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
-      default: mixed_pair<8>(S, job, w.z, w.y, tmem, ph_tma, ph_mma); break;
+      case 1: mixed_pair<1, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
+      case 2: mixed_pair<2, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
+      case 3: mixed_pair<3, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
+      case 4: mixed_pair<4, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
+      case 5: mixed_pair<5, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
+      case 6: mixed_pair<6, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
+      case 7: mixed_pair<7, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
+      default: mixed_pair<8, false>(S, job, w.z, w.y, tmem, ph_tma, ph_mma, xk); break;
     }
     if (S.status == kTimeout) break;
   }
@@ -882,8 +1103,16 @@ cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* 
 }
 
 template <int KS>
-static cudaError_t launch_ks(const MixedParams& p, cudaStream_t st) {
+static cudaError_t launch_ks(const MixedParams& p, bool split, cudaStream_t st) {
   const size_t smem = sizeof(Smem) + 1024;
+  if (split) {
+    cudaError_t e = cudaFuncSetAttribute(k_integrate_mixed_split<KS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(2 * p.ang.n_angles, p.n_sets);
+    k_integrate_mixed_split<KS><<<grid, NT, smem, st>>>(p);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(k_integrate_mixed<KS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -904,17 +1133,19 @@ cudaError_t launch_integrate_mixed_items(const MixedParams* jobs, const int4* it
   return cudaGetLastError();
 }
 
-cudaError_t launch_integrate_mixed(const MixedParams& p, cudaStream_t st, int* n_launched) {
+cudaError_t launch_integrate_mixed(const MixedParams& p, bool split, cudaStream_t st,
+                                   int* n_launched) {
+  if (split && p.N <= 32) return cudaErrorInvalidValue;  // the second CTA would own no column
   cudaError_t e;
   switch (p.k_slices) {
-    case 1: e = launch_ks<1>(p, st); break;
-    case 2: e = launch_ks<2>(p, st); break;
-    case 3: e = launch_ks<3>(p, st); break;
-    case 4: e = launch_ks<4>(p, st); break;
-    case 5: e = launch_ks<5>(p, st); break;
-    case 6: e = launch_ks<6>(p, st); break;
-    case 7: e = launch_ks<7>(p, st); break;
-    case 8: e = launch_ks<8>(p, st); break;
+    case 1: e = launch_ks<1>(p, split, st); break;
+    case 2: e = launch_ks<2>(p, split, st); break;
+    case 3: e = launch_ks<3>(p, split, st); break;
+    case 4: e = launch_ks<4>(p, split, st); break;
+    case 5: e = launch_ks<5>(p, split, st); break;
+    case 6: e = launch_ks<6>(p, split, st); break;
+    case 7: e = launch_ks<7>(p, split, st); break;
+    case 8: e = launch_ks<8>(p, split, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (n_launched) *n_launched += 1;

@@ -155,7 +155,9 @@ cudaError_t launch_rfactor(const RFactorParams& r, cudaStream_t st, int* n_launc
 
 cudaError_t launch_potential(const PotentialParams& p, cudaStream_t st, int* n_launched);
 cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* n_launched);
-cudaError_t launch_integrate_mixed(const MixedParams& p, cudaStream_t st, int* n_launched);
+// split: two CTAs (a cluster) per pair, each owning 32 columns; needs N > 32.
+cudaError_t launch_integrate_mixed(const MixedParams& p, bool split, cudaStream_t st,
+                                   int* n_launched);
 // Persistent mixed-precision batch kernel (items as for launch_integrate_fp64_items; any k_slices).
 cudaError_t launch_integrate_mixed_items(const MixedParams* jobs, const int4* items, int n_items,
                                          int* counter, int n_ctas, cudaStream_t st,

@@ -80,11 +80,46 @@ def test_mixed_matches_fp64_path(api):
     assert curve_error(e_m.cpu().numpy()[0], e_d.cpu().numpy()[0]) <= TOL
 
 
-def test_full_rocking_curve_61_beams(api):
-    """Full size (61 beams, 2000 slices, 60 angles), the launch the benchmark times."""
+@pytest.mark.parametrize("n_beams", [33, 61])
+def test_column_split_matches_one_cta(api, n_beams):
+    """Two CTAs per pair (a cluster sharing the columns) against one CTA per pair: the same
+    arithmetic per column and the same order of the Varah row sums, so the same RHST steps and
+    the same curve to rounding; both against the oracle."""
+    wl = W.tiny(n_beams=n_beams, seed=40 + n_beams, n_steps=160,
+                theta0=(0.6, 1.4, 2.9, 4.4), depth=10.0)
+    out = {}
+    for mode in ("on", "off"):
+        eng = api.Engine(wl, "mixed", "sp4")
+        eng.set_column_split(mode)
+        rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+        st = eng.stats()
+        assert st["column_split"] == (1 if mode == "on" else 0) and st["n_bad"] == 0
+        out[mode] = (rho.cpu().numpy()[0], eta.cpu().numpy()[0], st["rhst_total"])
+    assert out["on"][2] == out["off"][2] > 0
+    assert np.max(np.abs(out["on"][0] - out["off"][0])) <= 1e-12 * np.max(np.abs(out["off"][0]))
+    rho_o, eta_o, _, _ = rocking_curve(wl, "sp4")
+    _check(out["on"][0], out["on"][1], rho_o, eta_o)
+
+
+def test_column_split_modes(api):
+    wl = W.tiny(n_beams=19, seed=3, n_steps=20, theta0=(1.0,), depth=4.0)
+    eng = api.Engine(wl, "mixed", "sp4")
+    eng.set_column_split("on")   # 19 beams: one CTA owns every column, no split
+    eng.rocking_curve(wl.theta0, wl.theta1)
+    assert eng.stats()["column_split"] == 0
+    assert eng.lib.trh_set_column_split(eng.ctx, 7) == api.TRH_EINVAL
+
+
+@pytest.mark.parametrize("mode", ["auto", "off"])
+def test_full_rocking_curve_61_beams(api, mode):
+    """Full size (61 beams, 2000 slices, 60 angles), the launch the benchmark times (auto: two
+    CTAs per angle on a device with at least 120 SMs), and the one-CTA form."""
     wl = W.trhepd_n61()
     eng = api.Engine(wl, "mixed", "sp4")
+    eng.set_column_split(mode)
     rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    if mode == "off":
+        assert eng.stats()["column_split"] == 0
     rho, eta = rho.cpu().numpy()[0], eta.cpu().numpy()[0]
     if os.path.exists(GOLDEN):
         g = np.load(GOLDEN)
