@@ -104,7 +104,8 @@ struct __align__(128) Smem {
   float xdiag[2][NC];           // [step parity] |Q_jj|
   float redf[4];
   double gam2[NC], Gr[NC], Gi[NC];
-  float2 frow[NC], fcol[NC], oldk[NC];
+  float2 gstage[2][NC];         // Gauss-Jordan: column k at the start of step k, by parity
+  int gpr[2];                   // ... and its pivot row
   double2 xv[NC], rv[NC];
   double psum[4][MT];
 };
@@ -250,81 +251,108 @@ __device__ __forceinline__ void tmem_stx(uint32_t ta, const float (&v)[CP]) {
   else tmem_st8(ta, v);
 }
 
+// tv[i] for a run-time i in [0, 8) by a tree of selects (no indexed access: keeps tv in registers)
+__device__ __forceinline__ float2 pick8(const float2 (&tv)[8], int i) {
+  const bool b0 = i & 1, b1 = i & 2, b2 = i & 4;
+  const float2 a0 = b0 ? tv[1] : tv[0], a1 = b0 ? tv[3] : tv[2];
+  const float2 a2 = b0 ? tv[5] : tv[4], a3 = b0 ? tv[7] : tv[6];
+  const float2 c0 = b1 ? a1 : a0, c1 = b1 ? a3 : a2;
+  return b2 ? c1 : c0;
+}
+
+// Gauss-Jordan step c: the eight owners of column c (lanes `grp`, rows rg, rg + 8, ... in tv)
+// publish the column and choose its pivot among rows >= c.
+__device__ __forceinline__ void gj_publish(Smem& S, const float2 (&tv)[8], int c, int n, int rg,
+                                           unsigned grp) {
+  const int par = c & 1;
+  float best = -1.0f;
+  int bi = n;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = rg + 8 * i;
+    if (r < n) {
+      S.gstage[par][r] = tv[i];
+      const float m2 = tv[i].x * tv[i].x + tv[i].y * tv[i].y;
+      if (r >= c && (m2 > best || (m2 == best && r < bi))) {
+        best = m2;
+        bi = r;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const float v2 = __shfl_xor_sync(grp, best, o);
+    const int i2 = __shfl_xor_sync(grp, bi, o);
+    if (v2 > best || (v2 == best && i2 < bi)) {
+      best = v2;
+      bi = i2;
+    }
+  }
+  if (rg == 0) {
+    S.gpr[par] = bi;
+    S.piv[c] = bi;
+    if (!(best > 0.0f) || !isfinite(best)) S.status = kSingular;
+  }
+}
+
 // In-place inverse of the n x n complex FP32 matrix T (row stride TS) by Gauss-Jordan elimination
-// with row pivoting; the row interchanges are undone on the columns in reverse order at the end.
-// Thread t owns column t % 64 and rows t / 64, t / 64 + 8, ... (no index division in the update).
-// Inlined so that T and S stay shared-space pointers (shared loads and stores rather than generic).
+// with row pivoting (largest modulus in the column, lowest row on ties). Thread t owns column
+// t / 8 and rows t % 8, t % 8 + 8, ..., kept in registers for the whole elimination; the eight
+// owners of a column sit in one warp and pass the pivot row and row k to each other by shuffles.
+// At the end of step k-1 the owners of column k publish that column (the multipliers of step k)
+// and its pivot, in buffers that alternate by step parity, so a step needs one block barrier.
+// The row interchanges are undone on the columns in reverse order at the end. Inlined so that
+// T and S stay shared-space pointers.
 __device__ __forceinline__ void gj_invert(Smem& S, float2* T, int n) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int col = tid & 63, rg = tid >> 6;  // 8 row groups
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int col = tid >> 3, rg = tid & 7;
+  const int base = lane & ~7;               // lane of (col, rg = 0)
+  const unsigned grp = 0xFFu << base;       // the eight lanes owning this column
+  float2 tv[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = rg + 8 * i;
+    tv[i] = (r < n && col < n) ? T[r * TS + col] : make_float2(0.f, 0.f);
+  }
+  if (col == 0) gj_publish(S, tv, 0, n, rg, grp);
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
-    // warp 0: pivot row, then the scaled pivot row, the multipliers and the old row k
-    if (warp == 0) {
-      float best = -1.0f;
-      int bi = k;
-      for (int r = k + lane; r < n; r += 32) {
-        const float2 a = T[r * TS + k];
-        const float m2 = a.x * a.x + a.y * a.y;
-        if (m2 > best) {
-          best = m2;
-          bi = r;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (v2 > best || (v2 == best && i2 < bi)) {
-          best = v2;
-          bi = i2;
-        }
-      }
-      const int pr = bi;
-      if (lane == 0) {
-        S.piv[k] = pr;
-        if (!(best > 0.0f) || !isfinite(best)) S.status = kSingular;
-      }
-      // any invertible T is a valid RHST (Section 3.2): the reciprocal needs no correction step
-      const float2 a = T[pr * TS + k];
-      const float id = __frcp_rn(a.x * a.x + a.y * a.y);
-      const float2 inv = make_float2(a.x * id, -a.y * id);
-      for (int c = lane; c < n; c += 32) {
-        const float2 t = T[pr * TS + c];
-        S.frow[c] = (c == k) ? inv : make_float2(t.x * inv.x - t.y * inv.y,
-                                                 t.x * inv.y + t.y * inv.x);
-        // row r's multiplier: rows k and pr trade places
-        const int src = (c == k) ? pr : (c == pr ? k : c);
-        S.fcol[c] = (c == k) ? make_float2(0.f, 0.f) : T[src * TS + k];
-        S.oldk[c] = T[k * TS + c];  // old row k, overwritten by the pivot row below
-      }
-    }
-    __syncthreads();
     if (S.status != kOk) return;
-    const int pr = S.piv[k];
-    if (col < n) {
-      // the interchange: old row k moves to pr, old row pr becomes the new pivot row k; all of
-      // this thread's loads first (its rows and column are its own), then the updates
-      const float2 fr = S.frow[col], ok = S.oldk[col];
-      float2 tv[8], fc[8];
+    const int par = k & 1;
+    const int pr = S.gpr[par];
+    const float2* stg = S.gstage[par];
+    // any invertible T is a valid RHST (Section 3.2): the reciprocal needs no correction step
+    const float2 a = stg[pr];
+    const float id = __frcp_rn(a.x * a.x + a.y * a.y);
+    const float2 inv = make_float2(a.x * id, -a.y * id);
+    // this column's entries in the pivot row and in row k, from their owners
+    const float2 vp = pick8(tv, pr >> 3), vk = pick8(tv, k >> 3);
+    const float2 tp = make_float2(__shfl_sync(0xffffffffu, vp.x, base + (pr & 7)),
+                                  __shfl_sync(0xffffffffu, vp.y, base + (pr & 7)));
+    const float2 tk = make_float2(__shfl_sync(0xffffffffu, vk.x, base + (k & 7)),
+                                  __shfl_sync(0xffffffffu, vk.y, base + (k & 7)));
+    // the scaled pivot row becomes row k; old row k moves to row pr
+    const float2 fr = (col == k) ? inv
+                                 : make_float2(tp.x * inv.x - tp.y * inv.y,
+                                               tp.x * inv.y + tp.y * inv.x);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = rg + 8 * i;
-        tv[i] = (r < n) ? T[r * TS + col] : make_float2(0.f, 0.f);
-        fc[i] = (r < n) ? S.fcol[r] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = rg + 8 * i;
-        if (r < n) {
-          float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? ok : tv[i]);
-          t.x -= fc[i].x * fr.x - fc[i].y * fr.y;
-          t.y -= fc[i].x * fr.y + fc[i].y * fr.x;
-          T[r * TS + col] = (r == k) ? fr : t;
-        }
-      }
+    for (int i = 0; i < 8; ++i) {
+      const int r = rg + 8 * i;
+      const float2 fc = (r == k) ? make_float2(0.f, 0.f) : stg[r == pr ? k : r];
+      float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? tk : tv[i]);
+      t.x -= fc.x * fr.x - fc.y * fr.y;
+      t.y -= fc.x * fr.y + fc.y * fr.x;
+      if (r < n && col < n) tv[i] = (r == k) ? fr : t;
     }
+    if (k + 1 < n && col == k + 1) gj_publish(S, tv, k + 1, n, rg, grp);
     __syncthreads();
   }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = rg + 8 * i;
+    if (r < n && col < n) T[r * TS + col] = tv[i];
+  }
+  __syncthreads();
   for (int k = n - 1; k >= 0; --k) {
     const int pr = S.piv[k];
     if (pr != k) {
