@@ -239,6 +239,33 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Four 32x32b.x8 loads, one wait (the four accumulators of the column-split epilogue).
+__device__ __forceinline__ void tmem_ld8x4(uint32_t ta, float (&va)[8], uint32_t tb,
+                                           float (&vb)[8], uint32_t tc, float (&vc)[8],
+                                           uint32_t td, float (&vd)[8]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb), "r"(tc), "r"(td)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(r[8 + i]);
+    vc[i] = __uint_as_float(r[16 + i]);
+    vd[i] = __uint_as_float(r[24 + i]);
+  }
+}
+
 template <int CP>
 __device__ __forceinline__ void tmem_ldx2(uint32_t ta, float (&va)[CP], uint32_t tb,
                                           float (&vb)[CP]) {
@@ -761,10 +788,19 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       constexpr float kQ = 0.00390625f;  // 2^-8
       const uint32_t t_acc = t_lane + CP * cq;  // accumulator columns are this CTA's
       float acc[CP], dt[CP];
-      tmem_ldx2<CP>(t_acc + 0 * NCOL, acc, t_acc + 1 * NCOL, dt);  // D_3, D_2
+      if constexpr (CP == 8) {  // all four accumulators in flight at once
+        float d1[CP], d0[CP];
+        tmem_ld8x4(t_acc + 0 * NCOL, acc, t_acc + 1 * NCOL, dt, t_acc + 2 * NCOL, d1,
+                   t_acc + 3 * NCOL, d0);
 #pragma unroll
-      for (int c = 0; c < CP; ++c) acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
-      {
+        for (int c = 0; c < CP; ++c) {
+          acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
+          acc[c] = __fadd_rn(d0[c], __fmul_rn(__fadd_rn(d1[c], __fmul_rn(acc[c], kQ)), kQ));
+        }
+      } else {
+        tmem_ldx2<CP>(t_acc + 0 * NCOL, acc, t_acc + 1 * NCOL, dt);  // D_3, D_2
+#pragma unroll
+        for (int c = 0; c < CP; ++c) acc[c] = __fadd_rn(dt[c], __fmul_rn(acc[c], kQ));
         float d1[CP];
         tmem_ldx2<CP>(t_acc + 2 * NCOL, d1, t_acc + 3 * NCOL, dt);  // D_1, D_0
 #pragma unroll
