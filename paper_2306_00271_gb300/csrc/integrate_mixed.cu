@@ -98,7 +98,7 @@ struct __align__(128) Smem {
   uint32_t tmem_base;
   int status, flag, n_rhst;
   int xstatus;                  // column split: the other CTA's status at the end of a pair
-  int piv[NC];
+  int piv[NC], ipiv[NC];
   float rs8[8][NC];             // row sums of |Q_jk| over the 8-column groups k (Varah bound)
   float xrow[2][2][NC];         // [step parity][CTA or column half] row sums of its 32 columns
   float xdiag[2][NC];           // [step parity] |Q_jj|
@@ -287,91 +287,100 @@ __device__ __forceinline__ float2 pick8(const float2 (&tv)[8], int i) {
   return b2 ? c1 : c0;
 }
 
-// Gauss-Jordan step c: the eight owners of column c (lanes `grp`, rows rg, rg + 8, ... in tv)
-// publish the column and choose its pivot among rows >= c.
-__device__ __forceinline__ void gj_publish(Smem& S, const float2 (&tv)[8], int c, int n, int rg,
-                                           unsigned grp) {
+// Gauss-Jordan step c, executed by the whole warp that holds column c (lanes col == c publish):
+// the column is staged for step c and its pivot chosen among the rows not yet used (`used`,
+// bit i for row rg + 8 i; largest modulus, lowest row on ties) by a tree over this thread's
+// eight rows and then over the column's eight lanes.
+__device__ __forceinline__ void gj_publish(Smem& S, const float2 (&tv)[8], uint32_t used, int c,
+                                           int n, int col, int rg) {
   const int par = c & 1;
-  float best = -1.0f;
-  int bi = n;
+  float m2[8];
+  int ri[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = rg + 8 * i;
-    if (r < n) {
-      S.gstage[par][r] = tv[i];
-      const float m2 = tv[i].x * tv[i].x + tv[i].y * tv[i].y;
-      if (r >= c && (m2 > best || (m2 == best && r < bi))) {
-        best = m2;
-        bi = r;
-      }
-    }
+    const bool ok = r < n && !((used >> i) & 1u);
+    m2[i] = ok ? tv[i].x * tv[i].x + tv[i].y * tv[i].y : -1.0f;
+    ri[i] = r;
+    if (col == c && r < n) S.gstage[par][r] = tv[i];
   }
 #pragma unroll
+  for (int w = 1; w < 8; w <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; i += 2 * w)
+      if (m2[i + w] > m2[i]) {  // ties keep the left (lower) row
+        m2[i] = m2[i + w];
+        ri[i] = ri[i + w];
+      }
+  float best = m2[0];
+  int bi = ri[0];
+#pragma unroll
   for (int o = 4; o > 0; o >>= 1) {
-    const float v2 = __shfl_xor_sync(grp, best, o);
-    const int i2 = __shfl_xor_sync(grp, bi, o);
+    const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
     if (v2 > best || (v2 == best && i2 < bi)) {
       best = v2;
       bi = i2;
     }
   }
-  if (rg == 0) {
+  if (col == c && rg == 0) {
     S.gpr[par] = bi;
     S.piv[c] = bi;
     if (!(best > 0.0f) || !isfinite(best)) S.status = kSingular;
   }
 }
 
-// In-place inverse of the n x n complex FP32 matrix T (row stride TS) by Gauss-Jordan elimination
-// with row pivoting (largest modulus in the column, lowest row on ties). Thread t owns column
-// t / 8 and rows t % 8, t % 8 + 8, ..., kept in registers for the whole elimination; the eight
-// owners of a column sit in one warp and pass the pivot row and row k to each other by shuffles.
-// At the end of step k-1 the owners of column k publish that column (the multipliers of step k)
-// and its pivot, in buffers that alternate by step parity, so a step needs one block barrier.
-// The row interchanges are undone on the columns in reverse order at the end. Inlined so that
-// T and S stay shared-space pointers.
+// Inverse of the n x n complex FP32 matrix T (row stride TS) by Gauss-Jordan elimination with
+// implicit row pivoting (the exchange form: step k trades column k for the pivot row p_k, no
+// row is moved). On return T holds B with Q^{-1}[k][j] = B[piv[k]][ipiv[j]] (S.piv, S.ipiv).
+// Thread t owns column t / 8 and rows t % 8, t % 8 + 8, ..., kept in registers for the whole
+// elimination; the eight owners of a column sit in one warp and pass the pivot row's entry by a
+// shuffle. At the end of step k-1 the owners of column k publish that column (the multipliers
+// of step k) and its pivot, in buffers that alternate by step parity: one block barrier a step.
+// Inlined so that T and S stay shared-space pointers.
 __device__ __forceinline__ void gj_invert(Smem& S, float2* T, int n) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int col = tid >> 3, rg = tid & 7;
   const int base = lane & ~7;               // lane of (col, rg = 0)
-  const unsigned grp = 0xFFu << base;       // the eight lanes owning this column
+  const int warp = tid >> 5;                // holds columns 4 warp .. 4 warp + 3
   float2 tv[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = rg + 8 * i;
     tv[i] = (r < n && col < n) ? T[r * TS + col] : make_float2(0.f, 0.f);
   }
-  if (col == 0) gj_publish(S, tv, 0, n, rg, grp);
+  uint32_t used = 0;  // bit i: row rg + 8 i has been a pivot
+  if (warp == 0) gj_publish(S, tv, used, 0, n, col, rg);
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (S.status != kOk) return;
     const int par = k & 1;
-    const int pr = S.gpr[par];
+    const int p = S.gpr[par];
     const float2* stg = S.gstage[par];
-    // any invertible T is a valid RHST (Section 3.2): the reciprocal needs no correction step
-    const float2 a = stg[pr];
-    const float id = __frcp_rn(a.x * a.x + a.y * a.y);
+    const float2 a = stg[p];
+    const float a2 = a.x * a.x + a.y * a.y;
+    if (!(a2 > 0.0f) || !isfinite(a2)) return;  // every thread sees the same pivot (S.status set)
+    // any invertible T is a valid RHST (Section 3.2): an approximate reciprocal serves
+    const float id = __fdividef(1.0f, a2);
     const float2 inv = make_float2(a.x * id, -a.y * id);
-    // this column's entries in the pivot row and in row k, from their owners
-    const float2 vp = pick8(tv, pr >> 3), vk = pick8(tv, k >> 3);
-    const float2 tp = make_float2(__shfl_sync(0xffffffffu, vp.x, base + (pr & 7)),
-                                  __shfl_sync(0xffffffffu, vp.y, base + (pr & 7)));
-    const float2 tk = make_float2(__shfl_sync(0xffffffffu, vk.x, base + (k & 7)),
-                                  __shfl_sync(0xffffffffu, vk.y, base + (k & 7)));
-    // the scaled pivot row becomes row k; old row k moves to row pr
-    const float2 fr = (col == k) ? inv
-                                 : make_float2(tp.x * inv.x - tp.y * inv.y,
-                                               tp.x * inv.y + tp.y * inv.x);
+    // this column's entry in the pivot row, from its owner, scaled: the new pivot row
+    const float2 vp = pick8(tv, p >> 3);
+    const float2 tp = make_float2(__shfl_sync(0xffffffffu, vp.x, base + (p & 7)),
+                                  __shfl_sync(0xffffffffu, vp.y, base + (p & 7)));
+    const bool ck = (col == k);
+    const float2 fr = ck ? inv
+                         : make_float2(tp.x * inv.x - tp.y * inv.y, tp.x * inv.y + tp.y * inv.x);
+    const int ip = ((p & 7) == rg) ? (p >> 3) : -1;  // which of this thread's rows is p
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = rg + 8 * i;
-      const float2 fc = (r == k) ? make_float2(0.f, 0.f) : stg[r == pr ? k : r];
-      float2 t = (col == k) ? make_float2(0.f, 0.f) : (r == pr ? tk : tv[i]);
-      t.x -= fc.x * fr.x - fc.y * fr.y;
-      t.y -= fc.x * fr.y + fc.y * fr.x;
-      if (r < n && col < n) tv[i] = (r == k) ? fr : t;
+      const float2 f = stg[r];
+      float2 t = ck ? make_float2(0.f, 0.f) : tv[i];
+      t.x -= f.x * fr.x - f.y * fr.y;
+      t.y -= f.x * fr.y + f.y * fr.x;
+      if (r < n && col < n) tv[i] = (i == ip) ? fr : t;
     }
-    if (k + 1 < n && col == k + 1) gj_publish(S, tv, k + 1, n, rg, grp);
+    if (ip >= 0) used |= 1u << ip;
+    if (k + 1 < n && warp == ((k + 1) >> 2)) gj_publish(S, tv, used, k + 1, n, col, rg);
     __syncthreads();
   }
 #pragma unroll
@@ -379,29 +388,24 @@ __device__ __forceinline__ void gj_invert(Smem& S, float2* T, int n) {
     const int r = rg + 8 * i;
     if (r < n && col < n) T[r * TS + col] = tv[i];
   }
+  if (tid < n) S.ipiv[S.piv[tid]] = tid;
   __syncthreads();
-  for (int k = n - 1; k >= 0; --k) {
-    const int pr = S.piv[k];
-    if (pr != k) {
-      for (int r = tid; r < n; r += NT) {
-        const float2 t = T[r * TS + k];
-        T[r * TS + k] = T[r * TS + pr];
-        T[r * TS + pr] = t;
-      }
-      __syncthreads();
-    }
-  }
 }
 
 // out = Z T for this thread's part of row j and its CP columns c0.., Z read from TMEM (full rows,
-// hi at col_h, lo at col_l) in double-float, T (FP32) from shared memory; products are exact
-// (FMA residual) and summed with error-free additions.
+// hi at col_h, lo at col_l) in double-float, T (FP32) from shared memory as B of gj_invert,
+// T[k][c] = B[piv[k]][ipiv[c]]; products are exact (FMA residual) and summed with error-free
+// additions.
 template <int CP>
-__device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32_t col_h,
-                                        uint32_t col_l, int part, int c0, int n,
-                                        float (&oh)[CP], float (&ol)[CP]) {
+__device__ __forceinline__ void apply_t(const float2* B, const int* piv, const int* ipiv,
+                                        uint32_t t_lane, uint32_t col_h, uint32_t col_l, int part,
+                                        int c0, int n, float (&oh)[CP], float (&ol)[CP]) {
+  int bc[CP];  // columns of B (padding columns read a stale in-range entry; zeroed below)
 #pragma unroll
-  for (int i = 0; i < CP; ++i) oh[i] = ol[i] = 0.0f;
+  for (int i = 0; i < CP; ++i) {
+    oh[i] = ol[i] = 0.0f;
+    bc[i] = (c0 + i < n) ? ipiv[c0 + i] : c0 + i;
+  }
   for (int kc = 0; kc < n; kc += 8) {
     float zh[8], zl[8], ph[8], pl[8];
     tmem_ld8x2(t_lane + col_h + kc, zh, t_lane + col_l + kc, zl);
@@ -417,10 +421,10 @@ __device__ __forceinline__ void apply_t(const float2* T, uint32_t t_lane, uint32
       const float zrh = part ? ph[kk] : zh[kk], zrl = part ? pl[kk] : zl[kk];
       const float zih = part ? zh[kk] : ph[kk], zil = part ? zl[kk] : pl[kk];
       const float x2h = part ? zih : -zih, x2l = part ? zil : -zil;
-      const float2* Trow = T + (kc + kk) * TS + c0;
+      const float2* Brow = B + piv[kc + kk] * TS;
 #pragma unroll
       for (int i = 0; i < CP; ++i) {
-        const float2 t = Trow[i];
+        const float2 t = Brow[bc[i]];
         const float y1 = part ? t.y : t.x;
         const float y2 = part ? t.x : t.y;
         const float p1 = __fmul_rn(zrh, y1);
@@ -962,8 +966,8 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
         abort = 1;
         break;
       }
-      apply_t<CP>(T, t_lane, TM_QH, TM_QL, part, c0, N, Qh, Ql);
-      apply_t<CP>(T, t_lane, TM_PH, TM_PL, part, c0, N, Ph, Pl);
+      apply_t<CP>(T, S.piv, S.ipiv, t_lane, TM_QH, TM_QL, part, c0, N, Qh, Ql);
+      apply_t<CP>(T, S.piv, S.ipiv, t_lane, TM_PH, TM_PL, part, c0, N, Ph, Pl);
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
