@@ -164,10 +164,12 @@ def run_large_sample(slices: int = 30):
 
 
 # DRAM bytes per kick node of the integration kernels, from one ncu capture each (dram__bytes_read
-# + dram__bytes_write of a small case, divided by its node count; the traffic of both kernels is
-# proportional to the node count). Summaries: profiles/k_integrate_mixed_trhepd_n61_L400.md and
-# profiles/k_integrate_fp64_trhepd_n61_L60.md. Set to None when the kernel changes.
-TRAFFIC_PER_NODE = {"mixed": 325.42e6 / 2401, "fp64": 1.624832e6 / 361}
+# + dram__bytes_write of a small case, divided by its node count; the traffic of these kernels is
+# proportional to the node count). Summaries: profiles/k_integrate_mixed_split_trhepd_n61_L400.md,
+# profiles/k_integrate_mixed_trhepd_n61_L400.md and profiles/k_integrate_fp64_trhepd_n61_L60.md.
+# Set to None when the kernel changes.
+TRAFFIC_PER_NODE = {"mixed_split": 323.71968e6 / 2401, "mixed": 325.20192e6 / 2401,
+                    "fp64": 1.624832e6 / 361}
 
 
 def algorithmic_flops(N: int, s_eff: int, L: int, n_angles: int, n_rhst_total: int) -> float:
@@ -191,6 +193,8 @@ def run_ours(args):
     engines = {}
     for path in args.paths:
         engines[path] = api.Engine(wl, path, "sp4")
+        if path == "mixed":
+            engines[path].set_column_split(args.column_split)
     atoms_d = torch.tensor(wl.atoms, dtype=torch.float64, device=dev)
     dw_d = torch.tensor(wl.dw, dtype=torch.float64, device=dev)
     t0_d = torch.tensor(wl.theta0, dtype=torch.float64, device=dev)
@@ -211,7 +215,7 @@ def run_ours(args):
             torch.distributed.barrier()
         clocks = Clocks(local)
         clocks.start()
-        ms_steps, ms_int, ms_pot, launches, rhst = [], [], [], 0, 0
+        ms_steps, ms_int, ms_pot, launches, rhst, split = [], [], [], 0, 0, 0
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         for _ in range(args.steps):
@@ -226,6 +230,7 @@ def run_ours(args):
             ms_pot.append(st["ms_potential"])
             launches += st["kernels_launched"]
             rhst += st["rhst_total"]
+            split = st["column_split"]
         clk = clocks.stop()
         total_ms = float(np.sum(ms_steps))
         total_ms = D.max_over_ranks(total_ms)
@@ -244,7 +249,7 @@ def run_ours(args):
         e2e_s = (time.perf_counter() - t) / e2e_steps
         results[path] = dict(ms_per_step=total_ms / args.steps, ms_integrate=float(np.mean(ms_int)),
                              ms_potential=float(np.mean(ms_pot)), launches=launches,
-                             rhst_per_step=rhst / args.steps, clocks=clk,
+                             rhst_per_step=rhst / args.steps, clocks=clk, column_split=split,
                              value=ws * A * args.steps / (total_ms / 1e3),
                              e2e=dict(value=ws * A / e2e_s, unit=UNIT,
                                       h2d_bytes_per_step=int(atoms_h.nbytes + dw_h.nbytes
@@ -354,6 +359,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload lines")
+    ap.add_argument("--column-split", default="auto", choices=["auto", "on", "off"],
+                    help="mixed path: two CTAs per angle (auto: when the angles fit on half "
+                         "the SMs)")
     args = ap.parse_args()
     ws, rank, _ = _dist()
     wl = W.trhepd_n61()
@@ -398,7 +406,8 @@ def main():
     achieved = flops / (head["ms_integrate"] / 1e3) / 1e12
     if paths[0] == "mixed":
         peak = peaks.get("bf16_tflops", 1900.0)
-        tpn = TRAFFIC_PER_NODE["mixed"]
+        kern = "mixed_split" if head["column_split"] else "mixed"
+        tpn = TRAFFIC_PER_NODE[kern]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": None if tpn is None else tpn * (6 * L + 1),
@@ -416,9 +425,11 @@ def main():
     out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "bf16x3+f32pair" if paths[0] == "mixed" else "f64",
+           "dtype": "bf16x4+f32pair" if paths[0] == "mixed" else "f64",
            "data": "synthetic (seeded structure, see paper_2306_00271_gb300/workloads.py)",
-           "config": dict(cfg, path=paths[0]), "e2e": head["e2e"],
+           "config": dict(cfg, path=paths[0],
+                          ctas_per_angle=2 if head.get("column_split") else 1),
+           "e2e": head["e2e"],
            "gpu_launches": int(head["launches"]), "clocks": head["clocks"],
            "roofline": roof,
            "kernels_ms": {"integrate": head["ms_integrate"], "potential": head["ms_potential"]},
