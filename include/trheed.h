@@ -123,7 +123,7 @@ typedef struct trh_stats {
   int bulk_periods;       /* bulk periods the last bulk computation needed (largest over angles;
                              0 without a bulk or when the cached one was reused)                 */
   double ms_bulk;         /* device time of that bulk computation (0 if none ran)               */
-  int column_split;       /* mixed path: 1 if the last call ran two CTAs per (set, angle) pair
+  int column_split;       /* 1 if the last call ran two CTAs per (set, angle) pair
                              (trh_set_column_split), else 0                                    */
 } trh_stats;
 
@@ -185,12 +185,12 @@ int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* d
                  const int* species, double period, int steps_per_period, int max_periods,
                  double tol);
 
-/* ---- mixed path: CTAs per (set, angle) pair ------------------------------------------------
+/* ---- CTAs per (set, angle) pair --------------------------------------------------------------
  * The kick and the drift act column by column (W_c = U Q_c, Section 3.4), so on the mixed path
- * the columns of one pair can be shared by the two CTAs of a thread-block cluster, 32 each. They
- * exchange the Varah row sums once per step, the column halves of Q and P at every RHST
- * (Section 3.2: each CTA inverts the whole Q and transforms its own columns) and at the end
- * (CTA 0 assembles rho). This shortens a pair's critical path but takes two SMs per pair:
+ * and on the FP64 path (N <= 64, SP4/SP6) the columns of one pair can be shared by the two CTAs
+ * of a thread-block cluster, 32 each. They exchange the Varah row sums once per step, the column
+ * halves of Q and P at every RHST (Section 3.2: both CTAs hold the whole [Q; P] for it) and at
+ * the end (CTA 0 assembles rho). This shortens a pair's critical path but takes two SMs per pair:
  * TRH_SPLIT_AUTO (the default) uses it when N > 32 and the call has at most (SM count / 2)
  * pairs, TRH_SPLIT_OFF never, TRH_SPLIT_ON whenever N > 32. Results are identical either way:
  * every column sees the same arithmetic, and the row sums are added in the same fixed order, so

@@ -271,8 +271,9 @@ class Engine:
                                      float(tol)))
 
     def set_column_split(self, mode: str = "auto"):
-        """Mixed path: two CTAs per (set, angle) pair ("on"), one ("off"), or two when the
-        call's pairs fit on half the SMs ("auto", the default). Results are identical."""
+        """Mixed and FP64 (N <= 64) paths: two CTAs per (set, angle) pair ("on"), one ("off"),
+        or two when the call's pairs fit on half the SMs ("auto", the default). Results are
+        identical."""
         _check(self.lib.trh_set_column_split(self.ctx, SPLIT_MODES[mode]))
 
     def set_fit(self, free_atoms, dw_class=None, ckpt_every: int = 64):

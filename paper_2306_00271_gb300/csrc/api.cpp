@@ -490,11 +490,16 @@ static trh::IntegrateParams integrate_params(trh_ctx* c, int n_angles, size_t pa
   return ip;
 }
 
-// Mixed path: whether a call of `pairs` (set, angle) pairs runs with two CTAs per pair. The
-// split halves every CTA's kick work but needs twice the SMs, so AUTO takes it when one wave of
-// two-CTA clusters still fits on the device; 32 beams or fewer leave the second CTA no column.
+// Whether a call of `pairs` (set, angle) pairs runs with two CTAs per pair (the mixed path and
+// the shared-memory FP64 path, N <= 64 with a splitting integrator). The split halves every
+// CTA's kick work but needs twice the SMs, so AUTO takes it when one wave of two-CTA clusters
+// still fits on the device; 32 beams or fewer leave the second CTA no column.
 static bool use_split(const trh_ctx* c, size_t pairs) {
-  if (c->precision != TRH_MIXED || c->N <= 32 || c->split_mode == TRH_SPLIT_OFF) return false;
+  const bool fp64_smem = c->precision == TRH_FP64 && c->N <= trh::kMaxBeamsFp64 &&
+                         (c->integrator == TRH_SP4 || c->integrator == TRH_SP6);
+  if ((c->precision != TRH_MIXED && !fp64_smem) || c->N <= 32 ||
+      c->split_mode == TRH_SPLIT_OFF)
+    return false;
   if (c->split_mode == TRH_SPLIT_ON) return true;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -819,7 +824,7 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
     trh::MixedParams mp = mixed_params(c, ip);
     TRH_CUDA(trh::launch_integrate_mixed(mp, split, st, &launched));
   } else if (!wide) {
-    TRH_CUDA(trh::launch_integrate_fp64(ip, st, &launched));
+    TRH_CUDA(trh::launch_integrate_fp64(ip, split, st, &launched));
   } else {
     TRH_CUDA(trh::launch_integrate_fp64_wide(ip, c->d_wide.p, tile, st, &launched));
   }
@@ -963,7 +968,9 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
     TRH_CUDA(trh::launch_integrate_mixed(mixed_params(c, ip), split, st, launched));
     c->stats.column_split = split ? 1 : 0;
   } else {
-    TRH_CUDA(trh::launch_integrate_fp64(ip, st, launched));
+    split = use_split(c, pairs);
+    TRH_CUDA(trh::launch_integrate_fp64(ip, split, st, launched));
+    c->stats.column_split = split ? 1 : 0;
   }
   TRH_CUDA(cudaEventRecord(c->ev[3], st));
 

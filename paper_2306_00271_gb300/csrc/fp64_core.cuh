@@ -6,6 +6,7 @@
 // 4 x 2 grid of 16 x 32 output tiles cover the padded 64 x 64 result.
 #pragma once
 #include "internal.h"
+#include "umma.cuh"
 
 namespace trh {
 namespace fp64 {
@@ -15,6 +16,7 @@ constexpr int NP = kMaxBeamsFp64;  // padded beam count
 constexpr int LD = NP + 4;         // row stride (doubles): conflict-free m16n8k4 fragment loads
 constexpr int NT = 256;            // 8 warps
 constexpr double kPi = 3.14159265358979323846;
+constexpr long long kWaitCyclesX = 4000000000LL;  // bound of a wait for the other CTA (~2 s)
 
 struct Smem {
   double Ur[NP * LD], Ui[NP * LD];
@@ -28,7 +30,14 @@ struct Smem {
   double red0[NT / 32], red1[NT / 32];
   double sin_t0;
   int piv, flag, status, n_rhst;
+  // column split (two CTAs of a cluster per pair): exchanges with the other CTA
+  uint64_t bar_x[2];               // its arrivals, alternating
+  double xs[2][2][NP];             // [step parity][column half] row sums of |q_rc| (Varah)
+  double xd[2][NP];                // [step parity] |q_rr|
+  int xstatus;                     // its status at the end of a pair
 };
+static_assert(sizeof(Smem) + sizeof(IntegrateParams) + 16 <= 232448,
+              "shared memory above the 227 KB a CTA may use");
 
 __device__ __forceinline__ void dmma(double (&c)[4], double a0, double a1, double b) {
   asm volatile(
@@ -38,28 +47,33 @@ __device__ __forceinline__ void dmma(double (&c)[4], double a0, double a1, doubl
       : "d"(a0), "d"(a1), "d"(b));
 }
 
-// Element (row, col) of this thread's accumulator fragment q of tile s.
+// Element (row, col) of this thread's accumulator fragment q of tile s. The 8 warps form a 4 x 2
+// grid of 16-row x (8 NS)-column tiles starting at column col0: NS = 4, col0 = 0 covers all 64
+// columns; NS = 2, col0 = 32 r covers the 32 columns of CTA r of a column split.
 __device__ __forceinline__ int frag_row(int q) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   return 16 * (warp & 3) + (lane >> 2) + 8 * (q >> 1);
 }
-__device__ __forceinline__ int frag_col(int s, int q) {
+template <int NS = 4>
+__device__ __forceinline__ int frag_col(int s, int q, int col0 = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  return 32 * (warp >> 2) + 8 * s + 2 * (lane & 3) + (q & 1);
+  return col0 + 8 * NS * (warp >> 2) + 8 * s + 2 * (lane & 3) + (q & 1);
 }
-__device__ __forceinline__ bool tile_active(int N) {
+template <int NS = 4>
+__device__ __forceinline__ bool tile_active(int N, int col0 = 0) {
   const int warp = threadIdx.x >> 5;
-  return (16 * (warp & 3) < N) && (32 * (warp >> 2) < N);
+  return (16 * (warp & 3) < N) && (col0 + 8 * NS * (warp >> 2) < N);
 }
 
 // W = op(A) op(B) for N x N complex planes, into this warp's fragments (wr, wi) [tile s][q].
 // TA / TB: use the transpose; CA / CB: use the complex conjugate. The accumulation order is fixed
 // (real part: Re A Re B then -Im A Im B; imaginary part: Re A Im B then Im A Re B), so equal
-// inputs give bitwise equal results in every kernel that calls it.
-template <bool TA, bool CA, bool TB, bool CB>
+// inputs give bitwise equal results in every kernel that calls it, whatever the tile grid
+// (NS, col0; see frag_col): an element sees the same instructions in the same order.
+template <bool TA, bool CA, bool TB, bool CB, int NS = 4>
 __device__ __forceinline__ void cgemm(const double* Ar, const double* Ai, const double* Br,
                                       const double* Bi, int N, double (&wr)[4][4],
-                                      double (&wi)[4][4]) {
+                                      double (&wi)[4][4], int col0 = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mt = warp & 3, nt = warp >> 2;
   const int g = lane >> 2, t = lane & 3;
@@ -67,7 +81,7 @@ __device__ __forceinline__ void cgemm(const double* Ar, const double* Ai, const 
   for (int s = 0; s < 4; ++s)
 #pragma unroll
     for (int q = 0; q < 4; ++q) wr[s][q] = wi[s][q] = 0.0;
-  if (!tile_active(N)) return;
+  if (!tile_active<NS>(N, col0)) return;
   const int kmax = (N + 3) & ~3;
   const double sa = CA ? -1.0 : 1.0, sb = CB ? -1.0 : 1.0;
   for (int k0 = 0; k0 < kmax; k0 += 4) {
@@ -77,8 +91,8 @@ __device__ __forceinline__ void cgemm(const double* Ar, const double* Ai, const 
     const double ar0 = Ar[a0], ar1 = Ar[a1];
     const double ai0 = sa * Ai[a0], ai1 = sa * Ai[a1];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int col = 32 * nt + 8 * s + g;
+    for (int s = 0; s < NS; ++s) {
+      const int col = col0 + 8 * NS * nt + 8 * s + g;
       const int cb = TB ? col * LD + kk : kk * LD + col;
       const double br = Br[cb], bi = sb * Bi[cb];
       dmma(wr[s], ar0, ar1, br);
@@ -125,19 +139,21 @@ __device__ __forceinline__ void load_mat(double* Sr, double* Si, const double2* 
 
 // One kick P <- P - h b (U Q + Gamma^2 Q) at the U currently in shared memory, the drift
 // Q <- Q + h a P fused into its epilogue (if do_drift), and the gather of U(next_node) (if >= 0).
+// Columns col0 .. col0 + 16 NS - 1 only (the kick and the drift act column by column).
+template <int NS = 4>
 __device__ __forceinline__ void kick_drift(Smem& S, const IntegrateParams& p, int set, double coef, double adrift,
-                           bool do_drift, int next_node) {
+                           bool do_drift, int next_node, int col0 = 0) {
   const int N = p.N;
   double wr[4][4], wi[4][4];
-  cgemm<false, false, false, false>(S.Ur, S.Ui, S.Qr, S.Qi, N, wr, wi);
+  cgemm<false, false, false, false, NS>(S.Ur, S.Ui, S.Qr, S.Qi, N, wr, wi, col0);
   __syncthreads();  // every warp is done reading Q and U
   const double hb = p.h * coef, ha = p.h * adrift;
-  if (tile_active(N)) {
+  if (tile_active<NS>(N, col0)) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int row = frag_row(q), col = frag_col(s, q);
+        const int row = frag_row(q), col = frag_col<NS>(s, q, col0);
         if (row < N && col < N) {
           const int o = row * LD + col;
           const double g2 = S.gam2[row];
@@ -176,21 +192,62 @@ __device__ __forceinline__ void warp_argmax(double& val, int& idx) {
   }
 }
 
+// Column split: one exchange with the other CTA of the cluster, whose part of the payload every
+// thread has already written into that CTA's shared memory: a release arrival on its mbarrier,
+// then a bounded acquire wait on this CTA's (the two mbarriers alternate, so the other CTA, at
+// most one exchange ahead, never completes a phase twice before it is waited for). Returns false
+// for every thread after a timed-out wait.
+__device__ __forceinline__ bool cta_exchange(Smem& S, uint32_t peer, uint32_t& xk) {
+  umma::fence_acq_rel_cluster();
+  __syncthreads();
+  const int slot = (int)(xk & 1u);
+  if (threadIdx.x == 0)
+    umma::mbar_arrive_remote(umma::mapa_u32(umma::smem_u32(&S.bar_x[slot]), peer));
+  const bool ok = umma::mbar_wait_cluster(&S.bar_x[slot], (xk >> 1) & 1u, kWaitCyclesX);
+  ++xk;
+  return __syncthreads_and(ok) != 0;
+}
+
 // xi = max_i sum_j |q_ij| / min_i (|q_ii| - sum_{j != i} |q_ij|); sets S.flag = (xi > threshold)
-// (a non-positive denominator means xi = infinity).
-__device__ __forceinline__ void badness(Smem& S, const IntegrateParams& p) {
+// (a non-positive denominator means xi = infinity). The row sums are taken over the column
+// halves 0..31 and 32..63 (a warp sum each) and then added, so that with SPLIT each CTA of a
+// column split sums its own half, the halves are exchanged (slot `par`), and both CTAs reach the
+// same xi as one CTA would. Returns false after a timed-out exchange.
+template <bool SPLIT = false>
+__device__ __forceinline__ bool badness(Smem& S, const IntegrateParams& p, int par = 0,
+                                        uint32_t rank = 0, uint32_t peer = 0,
+                                        uint32_t* xk = nullptr) {
   const int N = p.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < N; r += NT / 32) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (SPLIT && h != (int)rank) continue;
+      const int c = 32 * h + lane;
+      double a = 0.0;
+      if (c < N) a = sqrt(S.Qr[r * LD + c] * S.Qr[r * LD + c] + S.Qi[r * LD + c] * S.Qi[r * LD + c]);
+      const double sum = warp_sum(a);
+      const double dg = warp_sum(c == r ? a : 0.0);
+      if (lane == 0) {
+        S.xs[par][h][r] = sum;
+        const bool diag_here = (r >> 5) == h;
+        if (diag_here) S.xd[par][r] = dg;
+        if (SPLIT) {
+          umma::st_cluster_f64(umma::mapa_u32(umma::smem_u32(&S.xs[par][h][r]), peer), sum);
+          if (diag_here) umma::st_cluster_f64(umma::mapa_u32(umma::smem_u32(&S.xd[par][r]), peer), dg);
+        }
+      }
+    }
+  }
+  if constexpr (SPLIT) {
+    if (!cta_exchange(S, peer, *xk)) return false;
+  } else {
+    __syncthreads();
+  }
   double rowmax = 0.0, minmargin = INFINITY;
   for (int r = warp; r < N; r += NT / 32) {
-    double sum = 0.0, dg = 0.0;
-    for (int c = lane; c < N; c += 32) {
-      const double a = sqrt(S.Qr[r * LD + c] * S.Qr[r * LD + c] + S.Qi[r * LD + c] * S.Qi[r * LD + c]);
-      sum += a;
-      if (c == r) dg = a;
-    }
-    sum = warp_sum(sum);
-    dg = warp_sum(dg);
+    const double sum = S.xs[par][0][r] + S.xs[par][1][r];
+    const double dg = S.xd[par][r];
     rowmax = fmax(rowmax, sum);
     minmargin = fmin(minmargin, dg - (sum - dg));
   }
@@ -209,6 +266,26 @@ __device__ __forceinline__ void badness(Smem& S, const IntegrateParams& p) {
     S.flag = !(xi <= p.threshold);
   }
   __syncthreads();
+  return true;
+}
+
+// Column split: this CTA's columns (32 rank ..) of Q and P into the same places of the other
+// CTA's planes (the payload of one exchange).
+__device__ __forceinline__ void send_columns(Smem& S, int N, uint32_t rank, uint32_t peer) {
+  const int c0 = 32 * (int)rank, nc = min(32, N - c0);
+  if (nc <= 0) return;
+  const uint32_t qr = umma::mapa_u32(umma::smem_u32(S.Qr), peer);
+  const uint32_t qi = umma::mapa_u32(umma::smem_u32(S.Qi), peer);
+  const uint32_t pr = umma::mapa_u32(umma::smem_u32(S.Pr), peer);
+  const uint32_t pi = umma::mapa_u32(umma::smem_u32(S.Pi), peer);
+  for (int e = threadIdx.x; e < N * nc; e += NT) {
+    const int j = e / nc, c = c0 + (e - j * nc);
+    const int o = j * LD + c;
+    umma::st_cluster_f64(qr + 8u * o, S.Qr[o]);
+    umma::st_cluster_f64(qi + 8u * o, S.Qi[o]);
+    umma::st_cluster_f64(pr + 8u * o, S.Pr[o]);
+    umma::st_cluster_f64(pi + 8u * o, S.Pi[o]);
+  }
 }
 
 // Stack of NB row blocks of N x N complex planes; block 0 is the pivot block.

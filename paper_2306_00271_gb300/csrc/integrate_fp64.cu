@@ -1,4 +1,5 @@
-// FP64 path: one CTA integrates one (parameter set, angle) pair from z_e to 0 (Algorithm 1).
+// FP64 path: one CTA, or the two CTAs of a cluster (column split), integrate one (parameter
+// set, angle) pair from z_e to 0 (Algorithm 1).
 //
 // State Z = [Q; P] (Eq. mateq2; Q = c-block, P = c'-block) lives in shared memory as separate
 // real/imaginary planes, zero-padded to 64 x 64. Per step of a BAB splitting scheme
@@ -56,20 +57,44 @@ __device__ __forceinline__ void assemble(Smem& S, const IntegrateParams& p, size
   }
 }
 
-// State [Q; P] into checkpoint slot `slot` of this (set, angle) pair.
+// State [Q; P] into checkpoint slot `slot` of this (set, angle) pair: columns c0 .. c0 + nc - 1.
 __device__ __forceinline__ void write_checkpoint(const Smem& S, const IntegrateParams& p,
-                                                 size_t pair, int slot) {
-  const size_t nn = (size_t)p.N * p.N;
+                                                 size_t pair, int slot, int c0 = 0,
+                                                 int nc = NP) {
+  const int N = p.N;
+  const size_t nn = (size_t)N * N;
   double2* dst = p.ckpt + (pair * p.n_ckpt + slot) * 2 * nn;
-  store_mat(dst, S.Qr, S.Qi, p.N);
-  store_mat(dst + nn, S.Pr, S.Pi, p.N);
+  nc = min(nc, N - c0);
+  for (int e = threadIdx.x; e < N * nc; e += NT) {
+    const int j = e / nc, c = c0 + (e - j * nc);
+    dst[j * N + c] = make_double2(S.Qr[j * LD + c], S.Qi[j * LD + c]);
+    dst[nn + j * N + c] = make_double2(S.Pr[j * LD + c], S.Pi[j * LD + c]);
+  }
 }
 
 // Integrates one (set, angle) pair of `p` and writes rho, eta, status and the RHST count.
-__device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p, int angle, int set) {
+//
+// SPLIT: the two CTAs of a cluster share the pair, CTA r owning columns 32 r .. 32 r + 31 of Q and
+// P (each still loads the whole U). Kicks and drifts act column by column, so they run without
+// communication, on a 4 x 2 warp grid of 16 x 16 tiles per CTA; per step the CTAs exchange the
+// Varah row sums of their halves (both then decide the same); an RHST exchanges the column halves
+// so that both hold the whole [Q; P], and both run the same elimination (and confirm with one
+// more exchange that each has finished reading its planes before they are written again); at the
+// end CTA 0 receives the other half and assembles. Every result is bitwise the one-CTA result.
+template <bool SPLIT>
+__device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p, int angle,
+                                               int set) {
+  constexpr int NS = SPLIT ? 2 : 4;
   const int tid = threadIdx.x;
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
+  const uint32_t rank = SPLIT ? umma::cluster_ctarank() : 0u, peer = rank ^ 1u;
+  const int col0 = SPLIT ? 32 * (int)rank : 0, ncol = SPLIT ? 32 : NP;
+  uint32_t xk = 0;
+  auto timed_out = [&]() {
+    if (tid == 0) S.status = kTimeout;
+    __syncthreads();
+  };
 
   setup_angle(S, p.ang, angle, N, true, p.p0 ? p.p0 + (size_t)angle * N * N : nullptr);
   const double sin_t0 = S.sin_t0;
@@ -80,37 +105,73 @@ __device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p
     for (int i = 0; i < p.L; ++i) {
       // checkpoint c holds the state at the start of step c * ckpt_every (after the RHST of
       // the step before), for the reverse sweep's recomputation
-      if (p.ckpt && i % p.ckpt_every == 0) write_checkpoint(S, p, pair, i / p.ckpt_every);
+      if (p.ckpt && i % p.ckpt_every == 0)
+        write_checkpoint(S, p, pair, i / p.ckpt_every, col0, ncol);
       for (int r = 0; r < s; ++r) {
         const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
-        kick_drift(S, p, set, coef, p.sch.a[r], true, s * i + r + 1);
+        kick_drift<NS>(S, p, set, coef, p.sch.a[r], true, s * i + r + 1, col0);
       }
-      badness(S, p);
+      if (!badness<SPLIT>(S, p, i & 1, rank, peer, &xk)) {
+        timed_out();
+        break;
+      }
       if (S.flag) {
+        if constexpr (SPLIT) {
+          send_columns(S, N, rank, peer);
+          if (!cta_exchange(S, peer, xk)) {
+            timed_out();
+            break;
+          }
+        }
         rhst(S, p);
         if (tid == 0) S.n_rhst++;
         if (S.status != kOk) break;
+        if constexpr (SPLIT) {
+          if (!cta_exchange(S, peer, xk)) {  // both have read their planes
+            timed_out();
+            break;
+          }
+        }
       }
     }
     if (S.status == kOk) {
-      kick_drift(S, p, set, p.sch.b[s], 0.0, false, -1);
+      kick_drift<NS>(S, p, set, p.sch.b[s], 0.0, false, -1, col0);
       if (p.ckpt) {
-        write_checkpoint(S, p, pair, p.n_ckpt - 1);  // final state, seeds the reverse sweep
+        write_checkpoint(S, p, pair, p.n_ckpt - 1, col0, ncol);  // final state, seeds the sweep
         __syncthreads();
       }
-      assemble(S, p, pair, sin_t0);
     }
   }
-  __syncthreads();
-  if (S.status != kOk) {
-    for (int j = tid; j < N; j += NT) {
-      p.out.rho[pair * N + j] = make_double2(NAN, NAN);
-      p.out.eta[pair * N + j] = NAN;
+  bool assemble_here = true;
+  if constexpr (SPLIT) {
+    // the other half and the other CTA's status; CTA 0 assembles. After a timed-out wait the
+    // CTAs are out of step: no further exchange (the other CTA's waits run out on their own).
+    assemble_here = (rank == 0);
+    if (S.status != kTimeout) {
+      if (tid == 0)
+        umma::st_cluster_s32(umma::mapa_u32(umma::smem_u32(&S.xstatus), peer), S.status);
+      send_columns(S, N, rank, peer);
+      const bool ok = cta_exchange(S, peer, xk);
+      if (tid == 0) {
+        if (!ok) S.status = kTimeout;
+        else if (S.status == kOk) S.status = S.xstatus;
+      }
+      __syncthreads();
     }
   }
-  if (tid == 0) {
-    p.out.status[pair] = S.status;
-    p.out.n_rhst[pair] = S.n_rhst;
+  if (assemble_here) {
+    if (S.status == kOk) assemble(S, p, pair, sin_t0);
+    __syncthreads();
+    if (S.status != kOk) {
+      for (int j = tid; j < N; j += NT) {
+        p.out.rho[pair * N + j] = make_double2(NAN, NAN);
+        p.out.eta[pair * N + j] = NAN;
+      }
+    }
+    if (tid == 0) {
+      p.out.status[pair] = S.status;
+      p.out.n_rhst[pair] = S.n_rhst;
+    }
   }
   __syncthreads();
 }
@@ -118,7 +179,22 @@ __device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p
 __global__ void __launch_bounds__(NT, 1) k_integrate_fp64(IntegrateParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-  integrate_pair(S, p, blockIdx.x, blockIdx.y);
+  integrate_pair<false>(S, p, blockIdx.x, blockIdx.y);
+}
+
+// Column split: a cluster of two CTAs (blockIdx.x = 2 angle + rank) per (set, angle) pair.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 1)
+    k_integrate_fp64_split(IntegrateParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  if (threadIdx.x == 0) {
+    umma::mbar_init(&S.bar_x[0], 1);
+    umma::mbar_init(&S.bar_x[1], 1);
+    umma::mbar_fence_init();
+  }
+  umma::cluster_sync();  // both CTAs' mbarriers are initialised before any remote arrival
+  integrate_pair<true>(S, p, blockIdx.x >> 1, blockIdx.y);
+  umma::cluster_sync();  // no CTA exits while the other may still write to its shared memory
 }
 
 // Persistent form for batches: each CTA takes work items (job, set, angle) in list order from an
@@ -139,7 +215,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_fp64_items(const IntegrateP
     const int4 w = items[it];
     if (threadIdx.x == 0) job = jobs[w.x];
     __syncthreads();
-    integrate_pair(S, job, w.z, w.y);   // ends with a barrier: `next` and `job` are free again
+    integrate_pair<false>(S, job, w.z, w.y);  // ends with a barrier: `next` and `job` are free
   }
 }
 
@@ -223,13 +299,20 @@ cudaError_t launch_bulk_fp64(const IntegrateParams& p, double2* X, int* periods,
 
 size_t integrate_fp64_smem_bytes() { return sizeof(Smem); }
 
-cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int* n_launched) {
+cudaError_t launch_integrate_fp64(const IntegrateParams& p, bool split, cudaStream_t st,
+                                  int* n_launched) {
   const size_t smem = sizeof(Smem);
-  cudaError_t e = cudaFuncSetAttribute(k_integrate_fp64,
+  if (split && p.N <= 32) return cudaErrorInvalidValue;  // the second CTA would own no column
+  cudaError_t e = cudaFuncSetAttribute(split ? k_integrate_fp64_split : k_integrate_fp64,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(p.ang.n_angles, p.n_sets);
-  k_integrate_fp64<<<grid, NT, smem, st>>>(p);
+  if (split) {
+    dim3 grid(2 * p.ang.n_angles, p.n_sets);
+    k_integrate_fp64_split<<<grid, NT, smem, st>>>(p);
+  } else {
+    dim3 grid(p.ang.n_angles, p.n_sets);
+    k_integrate_fp64<<<grid, NT, smem, st>>>(p);
+  }
   if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }

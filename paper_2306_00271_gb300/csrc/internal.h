@@ -165,7 +165,9 @@ cudaError_t launch_integrate_mixed_items(const MixedParams* jobs, const int4* it
 size_t mixed_image_bytes_per_node();
 // Records the message trh_last_error() returns on this thread.
 void set_last_error(const char* msg);
-cudaError_t launch_integrate_fp64(const IntegrateParams& p, cudaStream_t st, int* n_launched);
+// split: two CTAs (a cluster) per pair, each owning 32 columns; needs N > 32.
+cudaError_t launch_integrate_fp64(const IntegrateParams& p, bool split, cudaStream_t st,
+                                  int* n_launched);
 size_t integrate_fp64_smem_bytes();
 // Bulk boundary condition (integrate_fp64.cu): per angle the fixed point X of one bulk period's
 // map, iterated from i Gamma until the largest change is below tol times the largest entry.

@@ -268,7 +268,7 @@ extern "C" int trh_rocking_curve_noalloc(const trh_problem* p, int n_angles, con
   ip.L = L;
   ip.h = h;
   ip.threshold = p->rhst_threshold > 0 ? p->rhst_threshold : 1000.0;
-  NA_CUDA(trh::launch_integrate_fp64(ip, st, &launched));
+  NA_CUDA(trh::launch_integrate_fp64(ip, false, st, &launched));
 #undef NA_CUDA
   return TRH_OK;
 }

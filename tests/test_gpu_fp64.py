@@ -114,6 +114,28 @@ def test_grazing_beam_is_reported(api):
     assert eng.stats()["first_bad_status"] == api.TRH_EGRAZING
 
 
+@pytest.mark.parametrize("n_beams", [33, 61])
+def test_column_split_is_bitwise_one_cta(api, n_beams):
+    """Two CTAs per pair (a cluster sharing the columns of Q and P) against one CTA per pair:
+    every element sees the same DMMA sequence and the Varah halves are added in the same order,
+    so the curves and RHST counts are bitwise equal; both against the oracle."""
+    wl = W.tiny(n_beams=n_beams, seed=60 + n_beams, n_steps=120, theta0=(0.6, 1.7, 3.9),
+                depth=8.0)
+    out = {}
+    for mode in ("on", "off"):
+        eng = api.Engine(wl, "fp64", "sp4")
+        eng.set_column_split(mode)
+        rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+        st = eng.stats()
+        assert st["column_split"] == (1 if mode == "on" else 0) and st["n_bad"] == 0
+        out[mode] = (rho.cpu().numpy()[0], eta.cpu().numpy()[0], st["rhst_total"])
+    assert out["on"][2] == out["off"][2] > 0
+    assert np.array_equal(out["on"][0], out["off"][0])
+    assert np.array_equal(out["on"][1], out["off"][1])
+    rho_o, eta_o, _, _ = rocking_curve(wl, "sp4")
+    _check(out["on"][0], out["on"][1], rho_o, eta_o)
+
+
 def test_full_rocking_curve_61_beams_sampled(api):
     """Full size (61 beams, 2000 slices, 60 angles) in the launch configuration the benchmark
     times; all 60 angles are checked against stored oracle values when present, else 4."""
