@@ -166,10 +166,11 @@ def run_large_sample(slices: int = 30):
 # DRAM bytes per kick node of the integration kernels, from one ncu capture each (dram__bytes_read
 # + dram__bytes_write of a small case, divided by its node count; the traffic of these kernels is
 # proportional to the node count). Summaries: profiles/k_integrate_mixed_split_trhepd_n61_L400.md,
-# profiles/k_integrate_mixed_trhepd_n61_L400.md and profiles/k_integrate_fp64_trhepd_n61_L60.md.
+# profiles/k_integrate_mixed_trhepd_n61_L400.md, profiles/k_integrate_fp64_split_trhepd_n61_L60.md
+# and profiles/k_integrate_fp64_trhepd_n61_L60.md.
 # Set to None when the kernel changes.
 TRAFFIC_PER_NODE = {"mixed_split": 323.71968e6 / 2401, "mixed": 325.20192e6 / 2401,
-                    "fp64": 1.624832e6 / 361}
+                    "fp64_split": 1.504512e6 / 361, "fp64": 1.624832e6 / 361}
 
 
 def algorithmic_flops(N: int, s_eff: int, L: int, n_angles: int, n_rhst_total: int) -> float:
@@ -416,7 +417,7 @@ def main():
     else:
         bf = peaks.get("bf16_tflops", 1900.0)
         peak = bf * 1.25 / 2250.0
-        tpn = TRAFFIC_PER_NODE["fp64"]
+        tpn = TRAFFIC_PER_NODE["fp64_split" if head["column_split"] else "fp64"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": None if tpn is None else tpn * (6 * L + 1),
