@@ -359,8 +359,9 @@ __device__ __forceinline__ void gj_invert(Smem& S, float2* T, int n) {
     const float2 a = stg[p];
     const float a2 = a.x * a.x + a.y * a.y;
     if (!(a2 > 0.0f) || !isfinite(a2)) return;  // every thread sees the same pivot (S.status set)
-    // any invertible T is a valid RHST (Section 3.2): an approximate reciprocal serves
-    const float id = __fdividef(1.0f, a2);
+    // any invertible T is a valid RHST (Section 3.2): an approximate reciprocal serves (the
+    // fast one returns 0 above 2^126, where the rounded one still holds)
+    const float id = (a2 < 1e37f) ? __fdividef(1.0f, a2) : __frcp_rn(a2);
     const float2 inv = make_float2(a.x * id, -a.y * id);
     // this column's entry in the pivot row, from its owner, scaled: the new pivot row
     const float2 vp = pick8(tv, p >> 3);
