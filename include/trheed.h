@@ -154,9 +154,10 @@ int trh_set_structure(trh_ctx* ctx, int n_sets, const double* atoms, const doubl
  *   stream         : cudaStream_t (NULL = legacy default stream).
  * Steps per set: potential table at every kick position (one kernel), then one kernel that
  * integrates every (set, angle) pair from z_e to 0 with the RHST and assembles rho and eta.
- * TRH_FP64 computes everything in binary64. TRH_MIXED computes U*Q on the tensor cores
- * (BF16 3-term split, FP32 accumulation), keeps Q, P and the RHST elimination in double-float
- * (pairs of FP32, about 48 significant bits) and assembles rho in binary64 with one step of
+ * TRH_FP64 computes everything in binary64. TRH_MIXED computes U*Q on the tensor cores (four
+ * 8-bit fixed-point digits per operand in BF16, FP32 accumulators that never round), keeps Q and
+ * P in double-float (pairs of FP32, about 48 significant bits), inverts Q for the RHST in FP32
+ * and applies the inverse in double-float, and assembles rho in binary64 with one step of
  * iterative refinement.
  * Errors: TRH_EINVAL (n_angles < 1, theta0 outside (0, 90)), TRH_EGRAZING, TRH_ESINGULAR (the
  * outputs of the failing pairs are NaN; trh_query names the first one), TRH_ETIMEOUT,

@@ -1,5 +1,6 @@
-"""Mixed-precision CUDA path (BF16x3 tensor-core kicks, double-float state, FP32 RHST inverse
-applied in double-float, FP64 assembly with one refinement step) vs the oracle's Algorithm 1.
+"""Mixed-precision CUDA path (tensor-core kicks on four-digit fixed-point BF16 operands,
+double-float state, FP32 RHST inverse applied in double-float, FP64 assembly with one refinement
+step) vs the oracle's Algorithm 1, with one and with two CTAs per angle.
 
 Bar: <= 1e-6 per rocking curve (eacc-style, as in the FP64 tests); rho elementwise within 1e-6
 of the curve's largest |rho|."""
