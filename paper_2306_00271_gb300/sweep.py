@@ -9,6 +9,10 @@ beams, divided by the maximum over angles of the reference norm. Time is the int
 device time per curve (CUDA events, no table build).
 
     python -m paper_2306_00271_gb300.sweep [--workload trhepd_n61] [--angles 60] [--out FILE]
+        [--column-split auto|on|off]
+
+The splitting integrators can run two CTAs per angle (column split, `Engine.set_column_split`);
+the conventional method runs one. The table records which.
 """
 from __future__ import annotations
 
@@ -27,12 +31,13 @@ def curve_error(eta, ref) -> float:
     return float(np.max(np.linalg.norm(eta - ref, axis=1)) / np.max(np.linalg.norm(ref, axis=1)))
 
 
-def _curve(api, wl, precision, integrator):
+def _curve(api, wl, precision, integrator, split="auto"):
     """(eta, device ms of the integration kernel, RHST count, failed pairs). A step too coarse
     for the fastest evanescent beams can overflow Q within one step; the library reports that
     as a singular pivot and returns NaN for those angles."""
     import torch
     eng = api.Engine(wl, precision, integrator)
+    eng.set_column_split(split)
     eta = torch.empty((1, len(wl.theta0), eng.N), dtype=torch.float64, device="cuda")
     try:
         eng.rocking_curve(wl.theta0, wl.theta1, eta=eta)
@@ -40,10 +45,11 @@ def _curve(api, wl, precision, integrator):
         pass   # the failed angles are NaN; the count is in the stats
     st = eng.stats()
     eng.close()
-    return eta.cpu().numpy()[0], st["ms_integrate"], st["rhst_total"], st["n_bad"]
+    return eta.cpu().numpy()[0], st["ms_integrate"], st["rhst_total"], st["n_bad"], \
+        1 + st["column_split"]
 
 
-def run(workload: str = "trhepd_n61", n_angles: int = 60, runs=None):
+def run(workload: str = "trhepd_n61", n_angles: int = 60, runs=None, split: str = "auto"):
     import torch
     from . import api
     api.load()
@@ -52,7 +58,7 @@ def run(workload: str = "trhepd_n61", n_angles: int = 60, runs=None):
     base = base.with_angles(base.theta0[idx], base.theta1[idx])
     depth = -base.z_e
     ref_L = int(round(depth / (E6[0] / 2)))
-    ref, ref_ms, _, _ = _curve(api, base.with_steps(ref_L), "fp64", "sp6")
+    ref, ref_ms, _, _, _ = _curve(api, base.with_steps(ref_L), "fp64", "sp6", split)
     runs = runs or [("fp64", "conventional"), ("fp64", "sp4"), ("fp64", "sp6"), ("fp64", "rk4"),
                     ("mixed", "sp4"), ("mixed", "sp6")]
     rows = []
@@ -60,11 +66,11 @@ def run(workload: str = "trhepd_n61", n_angles: int = 60, runs=None):
         for dz in E6:
             L = max(1, int(round(depth / dz)))
             t = time.perf_counter()
-            eta, ms, nr, bad = _curve(api, base.with_steps(L), precision, integrator)
+            eta, ms, nr, bad, ctas = _curve(api, base.with_steps(L), precision, integrator, split)
             ok = np.all(np.isfinite(eta))
             rows.append(dict(precision=precision, integrator=integrator, dz=depth / L, L=L,
                              err=curve_error(eta, ref) if ok else float("nan"), ms=ms, rhst=nr,
-                             failed=bad, wall=time.perf_counter() - t))
+                             failed=bad, ctas=ctas, wall=time.perf_counter() - t))
             torch.cuda.synchronize()
     return dict(workload=workload, angles=len(idx), ref_L=ref_L, ref_ms=ref_ms, rows=rows)
 
@@ -75,12 +81,13 @@ def to_markdown(res) -> str:
              f"Reference: sp6, FP64, {res['ref_L']} slices ({res['ref_ms']:.0f} ms). Error: "
              "max over angles of the beam-norm of the intensity difference / max reference norm.",
              "",
-             "| path | integrator | dz (A) | slices | curve error | ms per curve | RHST | failed angles |",
-             "|---|---|---|---|---|---|---|---|"]
+             "| path | integrator | dz (A) | slices | curve error | ms per curve | RHST | failed angles "
+             "| CTAs per angle |",
+             "|---|---|---|---|---|---|---|---|---|"]
     for r in res["rows"]:
         err = "overflow" if r["failed"] else f"{r['err']:.2e}"
         lines.append(f"| {r['precision']} | {r['integrator']} | {r['dz']:.4f} | {r['L']} | "
-                     f"{err} | {r['ms']:.1f} | {r['rhst']} | {r['failed']} |")
+                     f"{err} | {r['ms']:.1f} | {r['rhst']} | {r['failed']} | {r['ctas']} |")
     return "\n".join(lines) + "\n"
 
 
@@ -89,8 +96,9 @@ def main():
     ap.add_argument("--workload", default="trhepd_n61", choices=sorted(W.RECIPES))
     ap.add_argument("--angles", type=int, default=60)
     ap.add_argument("--out", default="")
+    ap.add_argument("--column-split", default="auto", choices=["auto", "on", "off"])
     args = ap.parse_args()
-    md = to_markdown(run(args.workload, args.angles))
+    md = to_markdown(run(args.workload, args.angles, split=args.column_split))
     if args.out:
         with open(args.out, "w") as f:
             f.write(md)
