@@ -192,20 +192,9 @@ __device__ __forceinline__ void warp_argmax(double& val, int& idx) {
   }
 }
 
-// Column split: one exchange with the other CTA of the cluster, whose part of the payload every
-// thread has already written into that CTA's shared memory: a release arrival on its mbarrier,
-// then a bounded acquire wait on this CTA's (the two mbarriers alternate, so the other CTA, at
-// most one exchange ahead, never completes a phase twice before it is waited for). Returns false
-// for every thread after a timed-out wait.
+// Column split: one exchange with the other CTA of the cluster (umma::cluster_exchange).
 __device__ __forceinline__ bool cta_exchange(Smem& S, uint32_t peer, uint32_t& xk) {
-  umma::fence_acq_rel_cluster();
-  __syncthreads();
-  const int slot = (int)(xk & 1u);
-  if (threadIdx.x == 0)
-    umma::mbar_arrive_remote(umma::mapa_u32(umma::smem_u32(&S.bar_x[slot]), peer));
-  const bool ok = umma::mbar_wait_cluster(&S.bar_x[slot], (xk >> 1) & 1u, kWaitCyclesX);
-  ++xk;
-  return __syncthreads_and(ok) != 0;
+  return umma::cluster_exchange(S.bar_x, peer, xk, kWaitCyclesX);
 }
 
 // xi = max_i sum_j |q_ij| / min_i (|q_ii| - sum_{j != i} |q_ij|); sets S.flag = (xi > threshold)

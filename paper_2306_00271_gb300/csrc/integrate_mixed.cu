@@ -652,21 +652,8 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   int abort = (S.status != kOk);
   int kick_no = 0;
 
-  // ---- column split: exchanges with the other CTA ----
-  // Every thread has written its part of the payload into the other CTA's shared memory; one
-  // release arrival on that CTA's mbarrier, then a bounded acquire wait on this CTA's. The two
-  // mbarriers alternate so that the other CTA, one exchange ahead, never completes a phase
-  // twice before it is waited for; a buffer is written again only after an exchange that the
-  // receiver entered after reading it. Returns false (for every thread) after a timed-out wait.
-  auto exchange = [&]() -> bool {
-    fence_acq_rel_cluster();
-    __syncthreads();
-    const int slot = (int)(xk & 1u);
-    if (tid == 0) mbar_arrive_remote(mapa_u32(smem_u32(&S.bar_x[slot]), peer));
-    const bool ok = mbar_wait_cluster(&S.bar_x[slot], (xk >> 1) & 1u, kWaitCycles);
-    ++xk;
-    return __syncthreads_and(ok) != 0;
-  };
+  // ---- column split: exchanges with the other CTA (umma::cluster_exchange) ----
+  auto exchange = [&]() -> bool { return cluster_exchange(S.bar_x, peer, xk, kWaitCycles); };
   const uint32_t xb_peer = SPLIT ? mapa_u32(smem_u32(S.B + XB_OFF), peer) : 0u;
   const float* xb = reinterpret_cast<const float*>(S.B + XB_OFF);
   // this thread's columns of a double-float matrix into the other CTA's exchange buffer

@@ -267,6 +267,24 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
   }
   return true;
 }
+// One exchange with the other CTA of a two-CTA cluster, whose part of the payload every thread of
+// this CTA has already written into that CTA's shared memory: a release arrival on its mbarrier
+// bars[xk % 2], then a bounded acquire wait on this CTA's. The two mbarriers (count 1 each)
+// alternate, so the other CTA, at most one exchange ahead, never completes a phase twice before
+// it is waited for; a buffer must only be written again after an exchange that its reader
+// entered after reading it. Called by every thread of the CTA; returns false for every thread
+// after a timed-out wait (the CTAs are then out of step).
+__device__ __forceinline__ bool cluster_exchange(uint64_t* bars, uint32_t peer, uint32_t& xk,
+                                                 long long max_cycles) {
+  fence_acq_rel_cluster();
+  __syncthreads();
+  const int slot = (int)(xk & 1u);
+  if (threadIdx.x == 0) mbar_arrive_remote(mapa_u32(smem_u32(&bars[slot]), peer));
+  const bool ok = mbar_wait_cluster(&bars[slot], (xk >> 1) & 1u, max_cycles);
+  ++xk;
+  return __syncthreads_and(ok) != 0;
+}
+
 // Every thread of every CTA of the cluster (at kernel start, after the mbarrier initialisation,
 // and before exit, so no CTA leaves while another may still write to its shared memory).
 __device__ __forceinline__ void cluster_sync() {

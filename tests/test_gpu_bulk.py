@@ -51,11 +51,13 @@ def test_bulk_fp64_against_oracle(api, n_beams):
     assert eng.stats()["bulk_periods"] == 0
 
 
-def test_bulk_mixed_against_oracle(api):
-    wl, atoms, dw, sp = _case(19)
+@pytest.mark.parametrize("n_beams", [19, 37])
+def test_bulk_mixed_against_oracle(api, n_beams):
+    wl, atoms, dw, sp = _case(n_beams)
     eng = api.Engine(wl, "mixed", "sp4")
     eng.set_bulk(atoms, dw, sp, PERIOD, STEPS)
     _, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    assert eng.stats()["column_split"] == (1 if n_beams > 32 else 0)
     _, eta_o, _ = _oracle(wl, atoms, dw, sp)
     assert curve_error(eta.cpu().numpy()[0], eta_o) <= 1e-6
 

@@ -114,7 +114,7 @@ def test_grazing_beam_is_reported(api):
     assert eng.stats()["first_bad_status"] == api.TRH_EGRAZING
 
 
-@pytest.mark.parametrize("n_beams", [33, 61])
+@pytest.mark.parametrize("n_beams", [33, 48, 61, 64])
 def test_column_split_is_bitwise_one_cta(api, n_beams):
     """Two CTAs per pair (a cluster sharing the columns of Q and P) against one CTA per pair:
     every element sees the same DMMA sequence and the Varah halves are added in the same order,

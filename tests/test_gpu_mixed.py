@@ -81,7 +81,7 @@ def test_mixed_matches_fp64_path(api):
     assert curve_error(e_m.cpu().numpy()[0], e_d.cpu().numpy()[0]) <= TOL
 
 
-@pytest.mark.parametrize("n_beams", [33, 61])
+@pytest.mark.parametrize("n_beams", [33, 48, 61, 64])
 def test_column_split_matches_one_cta(api, n_beams):
     """Two CTAs per pair (a cluster sharing the columns) against one CTA per pair: the same
     arithmetic per column and the same order of the Varah row sums, so the same RHST steps and
