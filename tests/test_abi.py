@@ -100,7 +100,28 @@ def test_large_beam_sets_are_unsupported_not_wrong(lib):
     assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
 
 
+def _header_struct_fields(name):
+    import re
+    text = open(api.HEADER).read()
+    body = text[text.index(f"typedef struct {name} {{"):]
+    body = body[body.index("{") + 1:body.index(f"}} {name};")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:  # one or more declarators after the type: "double a1[2], a2[2]"
+            names += re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[[^]]*\])?\s*(?=,|$)", decl)
+    return names
+
+
+@pytest.mark.parametrize("name, cls", [("trh_stats", api.TrhStats),
+                                       ("trh_problem", api.TrhProblem)])
+def test_binding_structs_match_the_header(name, cls):
+    assert [f[0] for f in cls._fields_] == _header_struct_fields(name)
+
+
 def test_null_arguments(lib):
+    assert lib.trh_set_column_split(None, 0) == api.TRH_EINVAL
     assert lib.trh_create(None, None) == api.TRH_EINVAL
     assert lib.trh_query(None, None) == api.TRH_EINVAL
     assert lib.trh_rocking_curve(None, 1, None, None, None, None, None) == api.TRH_EINVAL
