@@ -49,19 +49,26 @@ __device__ __forceinline__ void dmma(double (&c)[4], double a0, double a1, doubl
 
 // Element (row, col) of this thread's accumulator fragment q of tile s. The 8 warps form a 4 x 2
 // grid of 16-row x (8 NS)-column tiles starting at column col0: NS = 4, col0 = 0 covers all 64
-// columns; NS = 2, col0 = 32 r covers the 32 columns of CTA r of a column split.
+// columns; NS = 2, col0 = 32 r covers the 32 columns of CTA r of a column split. NS = 1 is the
+// narrow grid for N <= 32: 2 x 4 tiles of 16 x 8 (warp w: rows 16 (w >> 2), columns 8 (w & 3)),
+// so that the few tiles of a small matrix spread over the four SM sub-partitions, each with its
+// own FP64 pipe (with the 4 x 2 grid, N <= 16 left all the work to warp 0).
+template <int NS = 4>
 __device__ __forceinline__ int frag_row(int q) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  return 16 * (warp & 3) + (lane >> 2) + 8 * (q >> 1);
+  const int mt = (NS == 1) ? (warp >> 2) : (warp & 3);
+  return 16 * mt + (lane >> 2) + 8 * (q >> 1);
 }
 template <int NS = 4>
 __device__ __forceinline__ int frag_col(int s, int q, int col0 = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  return col0 + 8 * NS * (warp >> 2) + 8 * s + 2 * (lane & 3) + (q & 1);
+  const int c = (NS == 1) ? 8 * (warp & 3) : 8 * NS * (warp >> 2) + 8 * s;
+  return col0 + c + 2 * (lane & 3) + (q & 1);
 }
 template <int NS = 4>
 __device__ __forceinline__ bool tile_active(int N, int col0 = 0) {
   const int warp = threadIdx.x >> 5;
+  if (NS == 1) return (16 * (warp >> 2) < N) && (col0 + 8 * (warp & 3) < N);
   return (16 * (warp & 3) < N) && (col0 + 8 * NS * (warp >> 2) < N);
 }
 
@@ -75,7 +82,7 @@ __device__ __forceinline__ void cgemm(const double* Ar, const double* Ai, const 
                                       const double* Bi, int N, double (&wr)[4][4],
                                       double (&wi)[4][4], int col0 = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int mt = warp & 3, nt = warp >> 2;
+  const int mt = (NS == 1) ? (warp >> 2) : (warp & 3), nt = warp >> 2;
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int s = 0; s < 4; ++s)
@@ -92,7 +99,7 @@ __device__ __forceinline__ void cgemm(const double* Ar, const double* Ai, const 
     const double ai0 = sa * Ai[a0], ai1 = sa * Ai[a1];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const int col = col0 + 8 * NS * nt + 8 * s + g;
+      const int col = col0 + ((NS == 1) ? 8 * (warp & 3) : 8 * NS * nt + 8 * s) + g;
       const int cb = TB ? col * LD + kk : kk * LD + col;
       const double br = Br[cb], bi = sb * Bi[cb];
       dmma(wr[s], ar0, ar1, br);
@@ -153,7 +160,7 @@ __device__ __forceinline__ void kick_drift(Smem& S, const IntegrateParams& p, in
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int row = frag_row(q), col = frag_col<NS>(s, q, col0);
+        const int row = frag_row<NS>(q), col = frag_col<NS>(s, q, col0);
         if (row < N && col < N) {
           const int o = row * LD + col;
           const double g2 = S.gam2[row];

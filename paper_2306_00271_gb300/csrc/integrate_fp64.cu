@@ -109,7 +109,10 @@ __device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p
         write_checkpoint(S, p, pair, i / p.ckpt_every, col0, ncol);
       for (int r = 0; r < s; ++r) {
         const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
-        kick_drift<NS>(S, p, set, coef, p.sch.a[r], true, s * i + r + 1, col0);
+        if (!SPLIT && N <= 32)  // narrow tile grid: the small product on all four FP64 pipes
+          kick_drift<1>(S, p, set, coef, p.sch.a[r], true, s * i + r + 1);
+        else
+          kick_drift<NS>(S, p, set, coef, p.sch.a[r], true, s * i + r + 1, col0);
       }
       if (!badness<SPLIT>(S, p, i & 1, rank, peer, &xk)) {
         timed_out();
@@ -135,7 +138,10 @@ __device__ __forceinline__ void integrate_pair(Smem& S, const IntegrateParams& p
       }
     }
     if (S.status == kOk) {
-      kick_drift<NS>(S, p, set, p.sch.b[s], 0.0, false, -1, col0);
+      if (!SPLIT && N <= 32)
+        kick_drift<1>(S, p, set, p.sch.b[s], 0.0, false, -1);
+      else
+        kick_drift<NS>(S, p, set, p.sch.b[s], 0.0, false, -1, col0);
       if (p.ckpt) {
         write_checkpoint(S, p, pair, p.n_ckpt - 1, col0, ncol);  // final state, seeds the sweep
         __syncthreads();
