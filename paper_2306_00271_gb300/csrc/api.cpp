@@ -446,13 +446,15 @@ static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuil
   pp.u32 = nullptr;
   TRH_CUDA(trh::launch_potential(pp, st, launched));
   if (c->precision == TRH_MIXED) {
-    TRH_CUDA(c->d_img.ensure((size_t)c->n_sets * c->n_nodes * trh::mixed_image_bytes_per_node()));
+    const int ks = (2 * c->N + 15) / 16;
+    TRH_CUDA(c->d_img.ensure((size_t)c->n_sets * c->n_nodes * trh::mixed_image_bytes_per_node(ks)));
     trh::MixedImageParams mp{};
     mp.u = c->d_u.p;
     mp.lmap = c->d_lmap.p;
     mp.img = c->d_img.p;
     mp.N = c->N;
     mp.M = c->M;
+    mp.k_slices = ks;
     mp.n_nodes = c->n_nodes;
     mp.n_sets = c->n_sets;
     TRH_CUDA(trh::launch_umma_images(mp, st, launched));

@@ -53,12 +53,20 @@ constexpr int NT = 512;
 constexpr int MT = 128;
 constexpr int KT = 128;
 constexpr int NC = 64;
-constexpr int A_LBO = 128, A_SBO = 16 * 128;
+constexpr int A_LBO = 128;                   // K-blocks of 8 elements, 128 B apart
 constexpr int NDIG = 4;                      // fixed-point digits per operand
-constexpr int A_TERM = MT * KT * 2;          // one digit plane of A
-constexpr int A_DIGITS = NDIG * A_TERM;      // 128 KB
+constexpr int A_DIGITS = NDIG * MT * KT * 2;  // 128 KB: the largest image (K = 128)
 constexpr int A_SCALES = MT * 4;             // row scales
-constexpr int IMG_BYTES = A_DIGITS + A_SCALES;
+// The digit image of a node holds only the K = 16 KS columns the products read: in each 8-row
+// group the 2 KS K-blocks are contiguous (SBO = 2 KS x 128 B), a plane is 16 groups, and the 128
+// row scales follow the four planes. At KS = 8 (61 beams) that is the full 128 x 128.
+template <int KS>
+struct ImgCfg {
+  static constexpr int SBO = 2 * KS * A_LBO;
+  static constexpr int TERM = (MT / 8) * SBO;      // one digit plane
+  static constexpr int DIGITS = NDIG * TERM;
+  static constexpr int BYTES = DIGITS + A_SCALES;  // a multiple of 16 (bulk copies)
+};
 constexpr int B_LBO = 144, B_SBO = 16 * 144;  // padded K-block stride: conflict-free stores
 constexpr int B_TERM = (NC / 8) * B_SBO;
 constexpr int TS = NC + 1;                   // row stride (float2) of T = Q^{-1} in the B region:
@@ -581,7 +589,8 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   const int c0 = NCOL * (int)rank + CP * cq;  // this thread's first column (of all N)
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
-  const unsigned char* img_set = p.img + (size_t)set * p.n_nodes * IMG_BYTES;
+  using Img = ImgCfg<KS>;
+  const unsigned char* img_set = p.img + (size_t)set * p.n_nodes * Img::BYTES;
 
   if (tid == 0) {
     S.status = kOk;
@@ -638,9 +647,9 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   fence_proxy_async_smem();
   bool tma_pending = false;
   if (tid == 0 && S.status == kOk) {
-    mbar_arrive_expect_tx(&S.bar_tma, IMG_BYTES);
-    bulk_g2s(S.A, img_set, A_DIGITS, &S.bar_tma);
-    bulk_g2s(S.alpha[0], img_set + A_DIGITS, A_SCALES, &S.bar_tma);
+    mbar_arrive_expect_tx(&S.bar_tma, Img::BYTES);
+    bulk_g2s(S.A, img_set, Img::DIGITS, &S.bar_tma);
+    bulk_g2s(S.alpha[0], img_set + Img::DIGITS, A_SCALES, &S.bar_tma);
     tma_pending = true;
   }
   tc_fence_before();
@@ -748,12 +757,12 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
           // NCOL (3-a-b), so every group writes from column 0 and the first MMA clears all four.
           // Descriptors are built once; the 14-bit start-address field (bits 0-13, in 16-byte
           // units) is advanced directly (shared addresses stay below 256 KB, so it never carries).
-          const uint64_t a0 = smem_desc(a_base, A_LBO, A_SBO);
+          const uint64_t a0 = smem_desc(a_base, A_LBO, Img::SBO);
           const uint64_t b0 = smem_desc(b_base, B_LBO, B_SBO);
           const int n_last = SPLIT ? NCOL : p.n_mma;
 #pragma unroll
           for (int a = 0; a < NDIG; ++a) {
-            const uint64_t at = a0 + (uint64_t)((a * A_TERM) >> 4);
+            const uint64_t at = a0 + (uint64_t)((a * Img::TERM) >> 4);
             const uint64_t bt = b0 + (uint64_t)((a * BT) >> 4);
             const uint32_t id = idesc_bf16_f32(MT, NCOL * (NDIG - 1 - a) + n_last);
 #pragma unroll
@@ -768,10 +777,10 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       ph_mma ^= 1;
       tc_fence_after();
       if (tid == 0 && next >= 0 && !to) {
-        const unsigned char* img = img_set + (size_t)next * IMG_BYTES;
-        mbar_arrive_expect_tx(&S.bar_tma, IMG_BYTES);
-        bulk_g2s(S.A, img, A_DIGITS, &S.bar_tma);
-        bulk_g2s(S.alpha[(kick_no + 1) & 1], img + A_DIGITS, A_SCALES, &S.bar_tma);
+        const unsigned char* img = img_set + (size_t)next * Img::BYTES;
+        mbar_arrive_expect_tx(&S.bar_tma, Img::BYTES);
+        bulk_g2s(S.A, img, Img::DIGITS, &S.bar_tma);
+        bulk_g2s(S.alpha[(kick_no + 1) & 1], img + Img::DIGITS, A_SCALES, &S.bar_tma);
         tma_pending = true;
       }
       // epilogue: W from the four exact accumulators, kick P -= hb W + (hb Gamma_j^2) Q with
@@ -836,7 +845,8 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
       // B for the next kick: digits of the new Q with the scales of this kick's Q (its column
       // maxima are complete since the previous barrier); the new maxima go to the other parity
       const int pc = kick_no & 1, pn = pc ^ 1;
-      if (!last) {
+      // a group of padding columns only (c0 >= N) keeps Q = 0 and its zero digits throughout
+      if (!last && c0 < N) {
         column_maxima<CP>(S, Qh, c0, qd, lane, pn);
         const uint32_t grew = digits_b<CP>(S, Qh, m, c0, qd, lane, pc, pn);
         if (grew) {
@@ -1084,9 +1094,9 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_items(const MixedPara
 }
 
 // Fixed-point digit images of the real-ified U(tau), one CTA per node: row scales
-// alpha_i = 2^ceil(log2 max_k |A_ik|) and four BF16 digit planes of 128 x 128 in the canonical
+// alpha_i = 2^ceil(log2 max_k |A_ik|) and four BF16 digit planes of 128 x 16 KS in the canonical
 // K-major no-swizzle layout (8-row x 16-byte core matrices, K-blocks 128 B apart, 8-row groups
-// 2048 B apart), then the 128 row scales.
+// 2 KS x 128 B apart; ImgCfg), then the 128 row scales.
 __global__ void __launch_bounds__(256) k_umma_images(MixedImageParams p) {
   __shared__ float s_alpha[MT];
   __shared__ float s_inv[MT];
@@ -1112,9 +1122,11 @@ __global__ void __launch_bounds__(256) k_umma_images(MixedImageParams p) {
     }
   }
   __syncthreads();
-  unsigned char* img = p.img + node_all * IMG_BYTES;
-  for (int t = tid; t < MT * KT / 8; t += blockDim.x) {
-    const int mg = t >> 7, kb = (t >> 3) & 15, mr = t & 7;
+  const int nkb = 2 * p.k_slices;                       // K-blocks per 8-row group
+  const int sbo = nkb * A_LBO, term_bytes = (MT / 8) * sbo, digit_bytes = NDIG * term_bytes;
+  unsigned char* img = p.img + node_all * (size_t)(digit_bytes + A_SCALES);
+  for (int t = tid; t < (MT / 8) * nkb * 8; t += blockDim.x) {
+    const int mg = t / (8 * nkb), kb = (t >> 3) % nkb, mr = t & 7;
     const int m = 8 * mg + mr;
     const int j = m >> 1, pp = m & 1;
     uint16_t v[NDIG][8];
@@ -1132,7 +1144,7 @@ __global__ void __launch_bounds__(256) k_umma_images(MixedImageParams p) {
 #pragma unroll
       for (int t = 0; t < NDIG; ++t) v[t][e] = b[t];
     }
-    unsigned char* dst = img + (size_t)mg * A_SBO + kb * A_LBO + mr * 16;
+    unsigned char* dst = img + (size_t)mg * sbo + kb * A_LBO + mr * 16;
 #pragma unroll
     for (int term = 0; term < NDIG; ++term) {
       uint4 w;
@@ -1140,16 +1152,18 @@ __global__ void __launch_bounds__(256) k_umma_images(MixedImageParams p) {
       w.y = v[term][2] | ((uint32_t)v[term][3] << 16);
       w.z = v[term][4] | ((uint32_t)v[term][5] << 16);
       w.w = v[term][6] | ((uint32_t)v[term][7] << 16);
-      *reinterpret_cast<uint4*>(dst + term * A_TERM) = w;
+      *reinterpret_cast<uint4*>(dst + term * term_bytes) = w;
     }
   }
-  if (tid < MT) reinterpret_cast<float*>(img + A_DIGITS)[tid] = s_alpha[tid];
+  if (tid < MT) reinterpret_cast<float*>(img + digit_bytes)[tid] = s_alpha[tid];
 }
 
 }  // namespace
 
 bool mixed_available() { return true; }
-size_t mixed_image_bytes_per_node() { return IMG_BYTES; }
+size_t mixed_image_bytes_per_node(int k_slices) {
+  return (size_t)NDIG * MT * 16 * k_slices * 2 + A_SCALES;
+}
 
 cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* n_launched) {
   const unsigned blocks = (unsigned)((size_t)p.n_sets * p.n_nodes);

@@ -84,8 +84,9 @@ struct PotentialParams {
 struct MixedImageParams {
   const double2* u;            // FP64 table [n_sets][n_nodes][M]
   const int* lmap;             // [N][N]
-  unsigned char* img;          // [n_sets][n_nodes][mixed_image_bytes_per_node()]
+  unsigned char* img;          // [n_sets][n_nodes][mixed_image_bytes_per_node(k_slices)]
   int N, M, n_nodes, n_sets;
+  int k_slices;                // ceil(2N / 16): the image holds K = 16 k_slices columns
 };
 
 struct MixedParams {
@@ -162,7 +163,8 @@ cudaError_t launch_integrate_mixed(const MixedParams& p, bool split, cudaStream_
 cudaError_t launch_integrate_mixed_items(const MixedParams* jobs, const int4* items, int n_items,
                                          int* counter, int n_ctas, cudaStream_t st,
                                          int* n_launched);
-size_t mixed_image_bytes_per_node();
+// Bytes of one node's digit image: four planes of 128 rows x 16 k_slices BF16 plus 128 row scales.
+size_t mixed_image_bytes_per_node(int k_slices);
 // Records the message trh_last_error() returns on this thread.
 void set_last_error(const char* msg);
 // split: two CTAs (a cluster) per pair, each owning 32 columns; needs N > 32.
