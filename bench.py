@@ -169,7 +169,7 @@ def run_large_sample(slices: int = 30):
 # profiles/k_integrate_mixed_trhepd_n61_L400.md, profiles/k_integrate_fp64_split_trhepd_n61_L60.md
 # and profiles/k_integrate_fp64_trhepd_n61_L60.md.
 # Set to None when the kernel changes.
-TRAFFIC_PER_NODE = {"mixed_split": 323.71968e6 / 2401, "mixed": 325.20192e6 / 2401,
+TRAFFIC_PER_NODE = {"mixed_split": 324.232704e6 / 2401, "mixed": 325.20192e6 / 2401,
                     "fp64_split": 1.504512e6 / 361, "fp64": 1.624832e6 / 361}
 
 
