@@ -114,6 +114,29 @@ def test_grazing_beam_is_reported(api):
     assert eng.stats()["first_bad_status"] == api.TRH_EGRAZING
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grazing_beam_with_two_ctas_per_angle(api, precision):
+    """The error path of the column-split kernels: both CTAs of the grazing pair see the same
+    status and end together; the pair's outputs are NaN, the other angle of the call is not."""
+    wl = W.tiny(n_beams=37, seed=2, n_steps=20, depth=4.0, theta0=(1.0,))
+    gamma = model.vacuum_wavenumber(wl.energy_ev)
+    k = model.rods(wl.beams, wl.a1, wl.a2)
+    j = int(np.argmax(k[:, 0]))
+    theta = float(np.rad2deg(np.arccos((-k[j, 0] + np.sqrt(gamma ** 2 - k[j, 1] ** 2)) / gamma)))
+    assert abs(model.Angle(wl, theta, 0.0).gam2[j]) < 1e-9
+    eng = api.Engine(wl, precision, "sp4")
+    eng.set_column_split("on")
+    import torch
+    eta = torch.empty((1, 2, 37), dtype=torch.float64, device="cuda")
+    with pytest.raises(api.TrhError) as ei:
+        eng.rocking_curve([theta, 2.0], [0.0, 0.0], eta=eta)
+    assert ei.value.code == api.TRH_EGRAZING
+    st = eng.stats()
+    assert st["column_split"] == 1 and st["n_bad"] == 1 and st["first_bad_angle"] == 0
+    e = eta.cpu().numpy()[0]
+    assert np.all(np.isnan(e[0])) and np.all(np.isfinite(e[1]))
+
+
 @pytest.mark.parametrize("n_beams", [33, 48, 61, 64])
 def test_column_split_is_bitwise_one_cta(api, n_beams):
     """Two CTAs per pair (a cluster sharing the columns of Q and P) against one CTA per pair:
