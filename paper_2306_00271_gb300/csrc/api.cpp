@@ -944,7 +944,13 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   TRH_CUDA(c->d_jacA.ensure(pairs * 2 * n_act));
   TRH_CUDA(cudaMemsetAsync(c->d_jacA.p, 0, pairs * 2 * n_act * sizeof(double), st));
   if (!c->gs[0]) {
-    for (int k = 0; k < 3; ++k) TRH_CUDA(cudaStreamCreateWithFlags(&c->gs[k], cudaStreamNonBlocking));
+    // recompute and adjoint form the critical path of the pipeline; the contraction, whose many
+    // short CTAs fill the remaining SMs, gets the lowest priority so that it does not delay them
+    int least = 0, greatest = 0;
+    TRH_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    for (int k = 0; k < 3; ++k)
+      TRH_CUDA(cudaStreamCreateWithPriority(&c->gs[k], cudaStreamNonBlocking,
+                                            k < 2 ? greatest : least));
     for (int k = 0; k < 4; ++k)
       for (int b = 0; b < 2; ++b)
         TRH_CUDA(cudaEventCreateWithFlags(&c->gev[k][b], cudaEventDisableTiming));
