@@ -1,10 +1,11 @@
-// Mixed-precision path: one CTA integrates one (parameter set, angle) pair (Algorithm 1) with the
-// kick products U(tau) Q on the 5th-generation tensor cores, accumulated exactly.
+// Mixed-precision path: one CTA, or the two CTAs of a cluster (column split), integrate one
+// (parameter set, angle) pair (Algorithm 1) with the kick products U(tau) Q on the
+// 5th-generation tensor cores, accumulated exactly.
 //
 // Real-ified complex product. Rows and columns interleave real and imaginary parts: real row
 // 2j+p is part p of beam j, so
-//   A[2j+p][2k+q] = [[Re U_jk, -Im U_jk], [Im U_jk, Re U_jk]][p][q]     (M = K = 128, N <= 64)
-//   B[2k+q][c]    = part q of Q_kc                                       (K = 128, n columns)
+//   A[2j+p][2k+q] = [[Re U_jk, -Im U_jk], [Im U_jk, Re U_jk]][p][q]     (M = 128, K = 16 KS)
+//   B[2k+q][c]    = part q of Q_kc                                       (K = 16 KS, n columns)
 //   D = A B       = real-ified W = U Q, with D[2j+p][c] = part p of W_jc
 // so TMEM lane 2j+p holds part p of row j and a lane pair (2j, 2j+1) holds whole complex numbers.
 //
@@ -26,13 +27,14 @@
 // State: Q and P as double-float pairs (hi, lo FP32; about 48 significant bits) in registers; the
 // kick P <- P - hb W - (hb Gamma^2) Q and the drift Q <- Q + ha P are exact to that precision.
 //
-// Per kick: every thread waits for the bulk copy of U(tau)'s digit image (128 KB + row scales, TMA
-// engine); thread 0 issues 4 x 8 tcgen05.mma (128 x (64 (3 - a) + n) x 16 for digit a of A, which
-// meets all the digits of B it pairs with in one instruction) into the four accumulators and
-// commits to an mbarrier; the next image is fetched as soon as the MMAs are done, overlapping the
-// epilogue. The epilogue (16 warps; warp w reads TMEM lanes 32(w%4).. and columns 16(w/4)..)
-// applies the kick and the drift, takes the exact column maxima of the new Q (warp reductions,
-// then shared memory) and writes its digits as the next B operand.
+// Per kick: every thread waits for the bulk copy of U(tau)'s digit image (16 KS KB + row scales,
+// TMA engine; KS = ceil(2N / 16)); thread 0 issues 4 x KS tcgen05.mma (128 x (w (3 - a) + n) x 16
+// for digit a of A, w the width of a B digit plane, so that one instruction meets all the digits
+// of B that digit a pairs with) into the four accumulators and commits to an mbarrier; the next
+// image is fetched as soon as the MMAs are done, overlapping the epilogue. The epilogue (16 warps;
+// warp w reads TMEM lanes 32(w%4).. and CP columns from CP (w/4), CP = 16, or 8 per CTA of a
+// column split) applies the kick and the drift, takes the exact column maxima of the new Q (warp
+// reductions, then shared memory) and writes its digits as the next B operand.
 //
 // Per step: the Varah bound xi of Q (FP32); if xi > threshold the RHST Z <- Z T with T = Q^{-1}
 // computed by FP32 Gauss-Jordan elimination (any invertible T leaves rho unchanged, Section 3.2,
