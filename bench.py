@@ -42,7 +42,8 @@ def _peaks():
 
 
 class Clocks:
-    """Samples nvidia-smi every 200 ms during the timed region."""
+    """Samples nvidia-smi every 50 ms; started before the warm-up steps (nvidia-smi takes a
+    moment to start) and stopped after the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -54,7 +55,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -224,13 +225,13 @@ def run_ours(args):
             eng.set_structures(atoms_d, dw_d)
             eng.rocking_curve(t0_d, t1_d, rho, eta)
             return eng.stats()
+        clocks = Clocks(local)
+        clocks.start()
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        clocks = Clocks(local)
-        clocks.start()
         ms_steps, ms_int, ms_pot, launches, rhst, split = [], [], [], 0, 0, 0
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
