@@ -107,8 +107,8 @@ def cpu_baseline(wl, n_angles: int):
 
 def oracle_timings(cores: int):
     """The oracle's other timings on the host cores: O1 (conventional, eigendecomposition route)
-    on the same 61-beam sample at 2000 slices, and O1 / O2 on the 11-beam RHEED workload
-    (1 angle, 400 slices)."""
+    on the same 61-beam sample at 2000 slices and at 4000 (its Richardson level), and O1 / O2 on
+    the 11-beam RHEED workload (1 angle, 400 slices)."""
     from oracle.curve import rocking_curve, rocking_curve_parallel
     out = {}
     wl = W.trhepd_n61()
@@ -118,6 +118,14 @@ def oracle_timings(cores: int):
     dt = time.perf_counter() - t
     out["o1_trhepd_n61"] = {"value": len(idx) / dt, "unit": UNIT,
                             "sample": f"{len(idx)} angles, 2000 slices, {cores} processes"}
+    # the second Richardson level of O1 (order 2): the same angles at half the slice width
+    t = time.perf_counter()
+    rocking_curve_parallel(wl.with_steps(2 * wl.n_steps), "conventional", angles=idx,
+                           processes=cores)
+    dt = time.perf_counter() - t
+    out["o1_richardson_level_trhepd_n61"] = {
+        "value": len(idx) / dt, "unit": UNIT,
+        "sample": f"{len(idx)} angles, 4000 slices, {cores} processes"}
     row = W.rheed_row()
     for name, method in (("o2_rheed_row", "sp4"), ("o1_rheed_row", "conventional")):
         t = time.perf_counter()
