@@ -39,6 +39,8 @@
 #ifndef TRHEED_H
 #define TRHEED_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -125,6 +127,12 @@ typedef struct trh_stats {
   double ms_bulk;         /* device time of that bulk computation (0 if none ran)               */
   int column_split;       /* 1 if the last call ran two CTAs per (set, angle) pair
                              (trh_set_column_split), else 0                                    */
+  int ctas_per_pair;      /* CTAs (one thread-block cluster) that integrated each pair in the
+                             last call: 1 or 2 (N <= 64), ceil(N / 32) on the mixed path for
+                             N > 64                                                            */
+  int set_chunks;         /* mixed path: chunks of parameter sets the last call ran in (the
+                             sets' digit images are built for one chunk at a time, at most
+                             40 GiB of them; 1 when every set fits)                            */
 } trh_stats;
 
 /* Create a context for one beam set and method. Validates and copies `p` (the caller may free
@@ -200,6 +208,18 @@ int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* d
  * Errors: TRH_EINVAL (mode not one of the three). */
 enum trh_split_mode { TRH_SPLIT_AUTO = 0, TRH_SPLIT_OFF = 1, TRH_SPLIT_ON = 2 };
 int trh_set_column_split(trh_ctx* ctx, int mode);
+
+/* ---- device memory of the mixed path ---------------------------------------------------------
+ * The mixed path multiplies by U(tau) on the tensor cores from fixed-point digit images of U at
+ * every kick position, built once per parameter set from the binary64 potential table (Section
+ * 3.4: one U(z) serves every angle) and read by every angle's integration: 131.6 KB per node at
+ * N = 61 (1.58 GB per set at 2000 slices), 512 KB per node at N = 121 (6.1 GB per set). The
+ * images of at most `bytes` (0 selects the default, 40 GiB) are kept at once: a call whose sets
+ * need more builds them for a chunk of sets, integrates those sets, then moves to the next chunk
+ * (trh_stats.set_chunks). Results do not depend on the chunking. At least one set is always
+ * taken, whatever the budget.
+ * Errors: TRH_EINVAL (ctx is NULL). */
+int trh_set_image_budget(trh_ctx* ctx, size_t bytes);
 
 /* ---- reverse analysis ---------------------------------------------------------------------
  * The paper's motivation (Section 1) is the reverse analysis of measured curves: a structure
@@ -301,9 +321,10 @@ void trh_destroy(trh_ctx* ctx);
 /* Rocking curve of one structure on the binary64 path without any device allocation.
  *
  * The paper has no counterpart: this entry exists for callers that cannot call cudaMalloc when
- * they need a curve, e.g. code running inside a CUDA stream capture (allocations there are not
- * capturable), code with a fixed device-memory budget, or host applications that own all device
- * memory. The caller passes device buffers for the angles and the outputs; the potential table,
+ * they need a curve: code that runs under a fixed device-memory budget which must not grow,
+ * plug-ins whose host application owns and hands out all device memory itself, and loops where
+ * cudaMalloc's implicit device synchronisation is not acceptable. The caller passes device
+ * buffers for the angles and the outputs; the potential table,
  * scattering factors, geometry tables and status words live in one fixed-size device array of
  * 16 MiB inside this library, which every GPU that loads the library keeps until process exit.
  *   p              : problem as for trh_create (host memory); precision must be TRH_FP64,

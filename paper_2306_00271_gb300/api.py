@@ -45,6 +45,7 @@ class TrhStats(C.Structure):
         ("ms_potential", C.c_double), ("ms_integrate", C.c_double),
         ("ms_gradient", C.c_double), ("wide_tile", C.c_int), ("graph_replay", C.c_int),
         ("bulk_periods", C.c_int), ("ms_bulk", C.c_double), ("column_split", C.c_int),
+        ("ctas_per_pair", C.c_int), ("set_chunks", C.c_int),
     ]
 
     def as_dict(self):
@@ -92,6 +93,7 @@ def load():
     lib.trh_set_bulk.argtypes = [vp, C.c_int, vp, vp, vp, C.c_double, C.c_int, C.c_int,
                                  C.c_double]
     lib.trh_set_column_split.argtypes = [vp, C.c_int]
+    lib.trh_set_image_budget.argtypes = [vp, C.c_size_t]
     lib.trh_curve_jacobian.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     lib.trh_rfactor_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.trh_batch_create.argtypes = [C.POINTER(vp)]
@@ -101,7 +103,8 @@ def load():
     lib.trh_batch_destroy.argtypes = [vp]
     lib.trh_batch_destroy.restype = None
     for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query", "trh_set_fit",
-              "trh_curve_jacobian", "trh_rfactor_grad", "trh_set_bulk", "trh_set_column_split", "trh_batch_create",
+              "trh_curve_jacobian", "trh_rfactor_grad", "trh_set_bulk", "trh_set_column_split", "trh_set_image_budget",
+              "trh_batch_create",
               "trh_batch_add",
               "trh_batch_run", "trh_batch_query"):
         getattr(lib, f).restype = C.c_int
@@ -275,6 +278,11 @@ class Engine:
         or two when the call's pairs fit on half the SMs ("auto", the default). Results are
         identical."""
         _check(self.lib.trh_set_column_split(self.ctx, SPLIT_MODES[mode]))
+
+    def set_image_budget(self, nbytes: int = 0):
+        """Mixed path: device bytes of digit images kept at once (0: the default, 40 GiB); sets
+        beyond it run in chunks (stats()["set_chunks"]). Results do not depend on it."""
+        _check(self.lib.trh_set_image_budget(self.ctx, int(nbytes)))
 
     def set_fit(self, free_atoms, dw_class=None, ckpt_every: int = 64):
         """Fit parameters for curve_jacobian / rfactor_grad: z of the atoms ``free_atoms`` and

@@ -42,47 +42,6 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-constexpr double kPi = 3.14159265358979323846;
-constexpr double kHbarC = 1973.269804;   // eV * Angstrom
-constexpr double kMc2 = 510998.95;       // electron rest energy, eV
-
-// SRKN_6^b and SRKN_11^b (Blanes & Moan 2002), the coefficients of the paper's sp4 / sp6.
-void bab_scheme(int integrator, trh::Scheme* s) {
-  std::vector<double> a, b;
-  if (integrator == TRH_RK4 || integrator == TRH_CONVENTIONAL) {
-    // classical Runge-Kutta and the conventional slice method: no splitting coefficients; two
-    // potential nodes per step (z_i and the midpoint z_i + h/2), as node fractions 0 and 1/2
-    s->s = 2;
-    s->a[0] = s->a[1] = 0.5;
-    for (int i = 0; i <= 2; ++i) s->b[i] = 0.0;
-    return;
-  }
-  if (integrator == TRH_SP4) {
-    const double a1 = 0.209515106613362, a2 = -0.143851773179818, a3 = 0.5 - a1 - a2;
-    const double b1 = 0.0792036964311957, b2 = 0.353172906049774, b3 = -0.0420650803577195;
-    const double b4 = 1.0 - 2.0 * (b1 + b2 + b3);
-    a = {a1, a2, a3, a3, a2, a1};
-    b = {b1, b2, b3, b4, b3, b2, b1};
-  } else {
-    const double aa[5] = {0.123229775946271, 0.290553797799558, -0.127049212625417,
-                          -0.246331761062075, 0.357208872795928};
-    const double bb[5] = {0.0414649985182624, 0.198128671918067, -0.0400061921041533,
-                          0.0752539843015807, -0.0115113874206879};
-    double sa = 0, sb = 0;
-    for (int i = 0; i < 5; ++i) { sa += aa[i]; sb += bb[i]; }
-    for (int i = 0; i < 5; ++i) a.push_back(aa[i]);
-    a.push_back(1.0 - 2.0 * sa);
-    for (int i = 4; i >= 0; --i) a.push_back(aa[i]);
-    for (int i = 0; i < 5; ++i) b.push_back(bb[i]);
-    b.push_back(0.5 - sb);
-    b.push_back(0.5 - sb);
-    for (int i = 4; i >= 0; --i) b.push_back(bb[i]);
-  }
-  s->s = (int)a.size();
-  for (int i = 0; i < s->s; ++i) s->a[i] = a[i];
-  for (int i = 0; i <= s->s; ++i) s->b[i] = b[i];
-}
-
 template <class T>
 struct DevBuf {
   T* p = nullptr;
@@ -153,8 +112,15 @@ struct trh_ctx {
   DevBuf<double2> d_kvec, d_g, d_u, d_F, d_rho;
   DevBuf<double> d_atoms, d_dw, d_sf, d_nodes, d_theta, d_eta;
   DevBuf<int> d_species, d_lmap, d_status;
-  DevBuf<unsigned char> d_img;
-  DevBuf<double2> d_wide;         // state of the wide FP64 kernel (N > 64)
+  DevBuf<unsigned char> d_img;    // mixed path: digit images of sets img_s0 .. img_s0 + img_ns - 1
+  DevBuf<float> d_scale;          // mixed path, N > 64: one scale per node of those images
+  bool img_valid = false;
+  int img_s0 = 0, img_ns = 0;
+  size_t img_budget = size_t(40) << 30;  // trh_set_image_budget
+  DevBuf<double2> d_wide;         // state of the wide FP64 kernel (N > 64); final state of the
+                                  // mixed cluster kernel (N > 64)
+  DevBuf<float> d_zg;             // mixed path, N > 64: RHST gather buffer
+  DevBuf<int> d_cst;              // mixed path, N > 64: status of each CTA of each pair
   int split_mode = TRH_SPLIT_AUTO;  // mixed path: two CTAs per pair (trh_set_column_split)
   std::vector<int> h_status;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -231,8 +197,8 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
     return fail(TRH_EUNSUPPORTED, "mixed path is not built in this library");
   if (p->precision == TRH_FP64 && p->n_beams > trh::kMaxBeamsWide)
     return fail(TRH_EUNSUPPORTED, "FP64 path supports N <= %d", trh::kMaxBeamsWide);
-  if (p->precision == TRH_MIXED && p->n_beams > trh::kMaxBeamsMixed)
-    return fail(TRH_EUNSUPPORTED, "mixed path supports N <= %d", trh::kMaxBeamsMixed);
+  if (p->precision == TRH_MIXED && p->n_beams > trh::kMaxBeamsMixedWide)
+    return fail(TRH_EUNSUPPORTED, "mixed path supports N <= %d", trh::kMaxBeamsMixedWide);
   const double det = p->a1[0] * p->a2[1] - p->a1[1] * p->a2[0];
   if (!(std::fabs(det) > 0)) return fail(TRH_EINVAL, "lattice vectors are parallel");
   for (int a = 0; a < p->n_atoms; ++a) {
@@ -262,56 +228,31 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
   c->species.assign(p->species, p->species + p->n_atoms);
   c->sf.assign(p->sf, p->sf + 8 * p->n_species);
 
-  // reciprocal basis b_i . a_j = 2 pi delta_ij and rods k_j
-  const double b1x = 2 * kPi * p->a2[1] / det, b1y = -2 * kPi * p->a2[0] / det;
-  const double b2x = -2 * kPi * p->a1[1] / det, b2y = 2 * kPi * p->a1[0] / det;
-  c->kvec.resize(2 * c->N);
-  std::map<std::pair<int, int>, int> seen;
-  for (int j = 0; j < c->N; ++j) {
-    const int m1 = p->beams[2 * j], m2 = p->beams[2 * j + 1];
-    if (!seen.emplace(std::make_pair(m1, m2), j).second) {
+  // rods k_j, distinct differences g_j - g_k and the index map l(j, k) of Eq. sch2
+  {
+    const int slots = trh::geometry_slots(c->N);
+    std::vector<long long> keys(slots);
+    std::vector<int> ids(slots);
+    std::vector<double> gd(2 * (size_t)c->N * c->N);
+    c->kvec.resize(2 * c->N);
+    c->lmap.resize((size_t)c->N * c->N);
+    const int dup = trh::build_geometry(p->beams, c->N, p->a1, p->a2, c->kvec.data(), gd.data(),
+                                        c->lmap.data(), &c->M, keys.data(), ids.data(), slots);
+    if (dup >= 0) {
       delete c;
-      return fail(TRH_EINVAL, "beam %d duplicates another", j);
+      return fail(TRH_EINVAL, "beam %d duplicates another", dup);
     }
-    c->kvec[2 * j] = m1 * b1x + m2 * b2x;
-    c->kvec[2 * j + 1] = m1 * b1y + m2 * b2y;
+    c->gdiff.assign(gd.begin(), gd.begin() + 2 * (size_t)c->M);
   }
-  // distinct differences g_j - g_k and the index map l(j, k) of Eq. sch2
-  std::map<std::pair<int, int>, int> diffs;
-  c->lmap.resize((size_t)c->N * c->N);
-  for (int j = 0; j < c->N; ++j)
-    for (int k = 0; k < c->N; ++k) {
-      const auto key = std::make_pair(p->beams[2 * j] - p->beams[2 * k],
-                                      p->beams[2 * j + 1] - p->beams[2 * k + 1]);
-      auto it = diffs.find(key);
-      int id;
-      if (it == diffs.end()) {
-        id = (int)diffs.size();
-        diffs.emplace(key, id);
-      } else {
-        id = it->second;
-      }
-      c->lmap[(size_t)j * c->N + k] = id;
-    }
-  c->M = (int)diffs.size();
-  c->gdiff.resize(2 * c->M);
-  for (const auto& kv : diffs) {
-    c->gdiff[2 * kv.second] = kv.first.first * b1x + kv.first.second * b2x;
-    c->gdiff[2 * kv.second + 1] = kv.first.first * b1y + kv.first.second * b2y;
-  }
-  // kick positions: node s*i + r at z_i + c_r h (c_r = a_0 + ... + a_{r-1}), last node at 0
-  bab_scheme(c->integrator, &c->scheme);
+  // kick positions (trh::node_position)
+  trh::bab_scheme(c->integrator, &c->scheme);
   const int s = c->scheme.s;
   c->n_nodes = s * c->L + 1;
   c->node_z.resize(c->n_nodes);
-  std::vector<double> cr(s, 0.0);
-  for (int r = 1; r < s; ++r) cr[r] = cr[r - 1] + c->scheme.a[r - 1];
-  for (int i = 0; i < c->L; ++i)
-    for (int r = 0; r < s; ++r) c->node_z[(size_t)s * i + r] = c->z_e + i * c->h + cr[r] * c->h;
-  c->node_z[(size_t)s * c->L] = c->z_e + c->L * c->h;
+  for (int n = 0; n < c->n_nodes; ++n)
+    c->node_z[n] = trh::node_position(c->scheme, n, c->L, c->z_e, c->h);
 
-  const double E = c->energy;
-  c->gamma = std::sqrt(E * E + 2.0 * E * kMc2) / kHbarC;
+  c->gamma = trh::vacuum_wavenumber(c->energy);
   c->phi_a1 = std::atan2(p->a1[1], p->a1[0]);
   c->area = std::fabs(det);
 
@@ -418,13 +359,74 @@ static int upload_angles(trh_ctx* c, int n_angles, const double* theta0, const d
 }
 
 static double2 potential_prefactor(const trh_ctx* c) {
-  const double gl = 1.0 + c->energy / kMc2;
-  const double scale = 4.0 * kPi * gl / c->area;
-  return make_double2(c->particle * scale, -c->absorption * scale);
+  return trh::potential_prefactor(c->particle, c->energy, c->absorption, c->area);
 }
 
-// Potential tables (and, on the mixed path, the tensor-core images) if the structure changed;
-// events ev[0], ev[1] bracket them. Sets *rebuilt.
+// Device bytes the mixed path's digit images may occupy at once (trh_set_image_budget; default
+// 40 GiB). A call whose sets need more runs them in chunks of sets (images built, then those
+// sets integrated); the images of one 61-beam structure at 2000 slices take 1.58 GB, of a
+// 121-beam one 6.1 GB.
+constexpr size_t kDefaultImageBudget = size_t(40) << 30;
+
+static size_t mixed_image_bytes_per_set(const trh_ctx* c) {
+  const int ks = (2 * c->N + 15) / 16;
+  const size_t per_node = c->N > trh::kMaxBeamsMixed ? trh::mixed_wide_image_bytes_per_node(ks)
+                                                     : trh::mixed_image_bytes_per_node(ks);
+  return per_node * (size_t)c->n_nodes;
+}
+
+// Sets per chunk of the mixed path (at least one).
+static int mixed_chunk_sets(const trh_ctx* c) {
+  const size_t per_set = mixed_image_bytes_per_set(c);
+  const size_t k = std::max<size_t>(1, c->img_budget / std::max<size_t>(per_set, 1));
+  return (int)std::min<size_t>(k, (size_t)c->n_sets);
+}
+
+// Digit images of sets s0 .. s0 + ns - 1 on the mixed path from the binary64 potential table:
+// one image per node with row scales (N <= 64, integrate_mixed.cu) or in streaming stages with
+// one scale per node (N > 64, integrate_mixed_wide.cu); nothing to do if d_img holds them.
+static int ensure_images(trh_ctx* c, int s0, int ns, cudaStream_t st, int* launched) {
+  if (c->img_valid && c->img_s0 == s0 && c->img_ns == ns) return TRH_OK;
+  const int ks = (2 * c->N + 15) / 16;
+  const unsigned char* old = c->d_img.p;
+  TRH_CUDA(c->d_img.ensure((size_t)ns * mixed_image_bytes_per_set(c)));
+  const double2* u = c->d_u.p + (size_t)s0 * c->n_nodes * c->M;
+  if (c->N > trh::kMaxBeamsMixed) {
+    const float* olds = c->d_scale.p;
+    TRH_CUDA(c->d_scale.ensure((size_t)ns * c->n_nodes));
+    if (c->d_scale.p != olds) c->generation++;
+    trh::MixedWideImageParams mp{};
+    mp.u = u;
+    mp.lmap = c->d_lmap.p;
+    mp.img = c->d_img.p;
+    mp.scale = c->d_scale.p;
+    mp.N = c->N;
+    mp.M = c->M;
+    mp.n_nodes = c->n_nodes;
+    mp.n_sets = ns;
+    mp.k_slices = ks;
+    TRH_CUDA(trh::launch_umma_images_wide(mp, st, launched));
+  } else {
+    trh::MixedImageParams mp{};
+    mp.u = u;
+    mp.lmap = c->d_lmap.p;
+    mp.img = c->d_img.p;
+    mp.N = c->N;
+    mp.M = c->M;
+    mp.k_slices = ks;
+    mp.n_nodes = c->n_nodes;
+    mp.n_sets = ns;
+    TRH_CUDA(trh::launch_umma_images(mp, st, launched));
+  }
+  if (c->d_img.p != old) c->generation++;  // batch plans hold the image pointer
+  c->img_valid = true;
+  c->img_s0 = s0;
+  c->img_ns = ns;
+  return TRH_OK;
+}
+
+// Potential tables (and, on the mixed path when all sets' images fit the budget, the
+// tensor-core images) if the structure changed; events ev[0], ev[1] bracket them. Sets *rebuilt.
 static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuilt) {
   *rebuilt = c->tables_dirty;
   if (!c->tables_dirty) return TRH_OK;
@@ -445,22 +447,13 @@ static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuil
   pp.u = c->d_u.p;
   pp.u32 = nullptr;
   TRH_CUDA(trh::launch_potential(pp, st, launched));
-  if (c->precision == TRH_MIXED) {
-    const int ks = (2 * c->N + 15) / 16;
-    TRH_CUDA(c->d_img.ensure((size_t)c->n_sets * c->n_nodes * trh::mixed_image_bytes_per_node(ks)));
-    trh::MixedImageParams mp{};
-    mp.u = c->d_u.p;
-    mp.lmap = c->d_lmap.p;
-    mp.img = c->d_img.p;
-    mp.N = c->N;
-    mp.M = c->M;
-    mp.k_slices = ks;
-    mp.n_nodes = c->n_nodes;
-    mp.n_sets = c->n_sets;
-    TRH_CUDA(trh::launch_umma_images(mp, st, launched));
+  c->img_valid = false;
+  c->tables_dirty = false;
+  if (c->precision == TRH_MIXED && mixed_chunk_sets(c) >= c->n_sets) {
+    const int rc = ensure_images(c, 0, c->n_sets, st, launched);
+    if (rc != TRH_OK) return rc;
   }
   TRH_CUDA(cudaEventRecord(c->ev[1], st));
-  c->tables_dirty = false;
   return TRH_OK;
 }
 
@@ -539,6 +532,50 @@ static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParam
   split(c->h * c->scheme.b[sc], &mp.kick_hi[sc + 1], &mp.kick_lo[sc + 1]);
   for (int r = 0; r < sc; ++r) split(c->h * c->scheme.a[r], &mp.drift_hi[r], &mp.drift_lo[r]);
   return mp;
+}
+
+// The mixed path over every set of the call, in chunks of sets whose digit images fit the
+// budget: N <= 64 on integrate_mixed.cu (one or two CTAs per pair), 64 < N <= 128 on the cluster
+// kernel of integrate_mixed_wide.cu followed by the binary64 assembly.
+static int run_mixed(trh_ctx* c, const trh::IntegrateParams& ip, int n_angles, bool split,
+                     cudaStream_t st, int* launched, int* chunks, int* ctas) {
+  const int cs = mixed_chunk_sets(c);
+  const bool wide = c->N > trh::kMaxBeamsMixed;
+  const int n_cta = wide ? (c->N + 31) / 32 : (split ? 2 : 1);
+  *ctas = n_cta;
+  *chunks = 0;
+  if (wide) {
+    const size_t lp = (size_t)cs * n_angles, N = (size_t)c->N;
+    TRH_CUDA(c->d_wide.ensure(lp * 2 * N * N));
+    TRH_CUDA(c->d_zg.ensure(lp * 4 * N * 2 * N));
+    TRH_CUDA(c->d_cst.ensure(lp * n_cta));
+  }
+  for (int s0 = 0; s0 < c->n_sets; s0 += cs) {
+    const int ns = std::min(cs, c->n_sets - s0);
+    const int rc = ensure_images(c, s0, ns, st, launched);
+    if (rc != TRH_OK) return rc;
+    trh::MixedParams mp = mixed_params(c, ip);
+    mp.set0 = s0;
+    mp.img_set0 = s0;
+    mp.n_sets = ns;
+    if (!wide) {
+      TRH_CUDA(trh::launch_integrate_mixed(mp, split, st, launched));
+    } else {
+      trh::MixedWideParams wp{};
+      wp.m = mp;
+      wp.scale = c->d_scale.p;
+      wp.fstate = c->d_wide.p;
+      wp.zg = c->d_zg.p;
+      wp.cta_status = c->d_cst.p;
+      wp.n_cta = n_cta;
+      TRH_CUDA(trh::launch_integrate_mixed_wide(wp, st, launched));
+      trh::IntegrateParams ipc = ip;
+      ipc.n_sets = ns;
+      TRH_CUDA(trh::launch_assemble_wide(ipc, s0, c->d_wide.p, c->d_cst.p, n_cta, st, launched));
+    }
+    ++*chunks;
+  }
+  return TRH_OK;
 }
 
 // Reads back the per-pair status words (the stream is synchronised) and fills the counters.
@@ -620,6 +657,12 @@ static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* s
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_wide_tile[2 * c->N + ip.method] = best_tile;
   *tile = best_tile;
+  return TRH_OK;
+}
+
+int trh_set_image_budget(trh_ctx* c, size_t bytes) {
+  if (!c) return fail(TRH_EINVAL, "ctx is NULL");
+  c->img_budget = bytes > 0 ? bytes : kDefaultImageBudget;
   return TRH_OK;
 }
 
@@ -821,10 +864,11 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
     if (rc != TRH_OK) return rc;
   }
   const bool split = use_split(c, pairs);
+  int chunks = 1, ctas = split ? 2 : 1;
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
-    trh::MixedParams mp = mixed_params(c, ip);
-    TRH_CUDA(trh::launch_integrate_mixed(mp, split, st, &launched));
+    rc = run_mixed(c, ip, n_angles, split, st, &launched, &chunks, &ctas);
+    if (rc != TRH_OK) return rc;
   } else if (!wide) {
     TRH_CUDA(trh::launch_integrate_fp64(ip, split, st, &launched));
   } else {
@@ -846,6 +890,8 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   S.ms_gradient = 0.0;
   S.wide_tile = tile;
   S.column_split = split ? 1 : 0;
+  S.ctas_per_pair = ctas;
+  S.set_chunks = chunks;
   S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
                   .count();
   if (S.n_bad) return bad_pairs_error(c);
@@ -971,7 +1017,9 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   if (c->precision == TRH_MIXED) {
     // mixed forward: curve and checkpoints from the double-float state; every segment is then
     // recomputed on the binary64 path from its checkpoint, so the reverse map stays consistent
-    // with the trajectory it differentiates
+    // with the trajectory it differentiates (images of every set at once)
+    rc = ensure_images(c, 0, c->n_sets, st, launched);
+    if (rc != TRH_OK) return rc;
     split = use_split(c, pairs);
     TRH_CUDA(trh::launch_integrate_mixed(mixed_params(c, ip), split, st, launched));
     c->stats.column_split = split ? 1 : 0;
@@ -1226,6 +1274,9 @@ struct trh_batch {
   size_t slot_elems = 0;
   std::vector<trh::IntegrateParams> params;
   std::vector<trh::MixedParams> mparams;
+  // mixed jobs with 64 < N <= 128: one cluster launch and one assembly launch each
+  std::vector<trh::MixedWideParams> wparams;
+  std::vector<size_t> wjob;
   DevBuf<trh::IntegrateParams> d_params;
   DevBuf<trh::MixedParams> d_mparams;
   DevBuf<int4> d_items;                  // small items, then wide items
@@ -1273,7 +1324,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   struct Item {
     double cost;
     int4 w;
-    int family;   // 0: FP64 N <= 64, 1: FP64 wide or RK4, 2: mixed precision
+    int family;   // 0: FP64 N <= 64, 1: FP64 wide or RK4, 2: mixed precision N <= 64
   };
   std::vector<Item> items;
   int max_n_wide = 0;
@@ -1296,6 +1347,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
                      c->integrator == TRH_CONVENTIONAL);
     const int family = c->precision == TRH_MIXED ? 2 : (wide ? 1 : 0);
     const double cost = (double)c->N * c->N * c->N * c->L * c->scheme.s;
+    if (c->precision == TRH_MIXED && c->N > trh::kMaxBeamsMixed) continue;  // cluster launches
     for (int set = 0; set < c->n_sets; ++set)
       for (int a = 0; a < J.n_angles; ++a)
         items.push_back({cost, make_int4((int)j, set, a, 0), family});
@@ -1313,10 +1365,29 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   // statuses of job j live at offset[j] (and n_rhst at total_pairs + offset[j])
   TRH_CUDA(b->d_status.ensure(2 * b->total_pairs));
   b->mparams.clear();
+  b->wparams.clear();
+  b->wjob.clear();
   for (size_t j = 0; j < b->jobs.size(); ++j) {
     b->params[j].out.status = b->d_status.p + b->offset[j];
     b->params[j].out.n_rhst = b->d_status.p + b->total_pairs + b->offset[j];
-    b->mparams.push_back(mixed_params(b->jobs[j].c, b->params[j]));
+    trh_ctx* c = b->jobs[j].c;
+    b->mparams.push_back(mixed_params(c, b->params[j]));
+    if (c->precision == TRH_MIXED && c->N > trh::kMaxBeamsMixed) {
+      const size_t lp = (size_t)c->n_sets * b->jobs[j].n_angles, N = (size_t)c->N;
+      const int n_cta = (c->N + 31) / 32;
+      TRH_CUDA(c->d_wide.ensure(lp * 2 * N * N));
+      TRH_CUDA(c->d_zg.ensure(lp * 4 * N * 2 * N));
+      TRH_CUDA(c->d_cst.ensure(lp * n_cta));
+      trh::MixedWideParams wp{};
+      wp.m = b->mparams.back();
+      wp.scale = c->d_scale.p;
+      wp.fstate = c->d_wide.p;
+      wp.zg = c->d_zg.p;
+      wp.cta_status = c->d_cst.p;
+      wp.n_cta = n_cta;
+      b->wparams.push_back(wp);
+      b->wjob.push_back(j);
+    }
   }
   // longest-processing-time first within each kernel family
   std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
@@ -1376,6 +1447,12 @@ static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
     TRH_CUDA(trh::launch_integrate_mixed_items(b->d_mparams.p,
                                                b->d_items.p + b->n_small + b->n_wide, b->n_mixed,
                                                b->d_counter.p + 2, b->mixed_ctas, st, launched));
+  for (size_t w = 0; w < b->wparams.size(); ++w) {
+    const trh::MixedWideParams& wp = b->wparams[w];
+    TRH_CUDA(trh::launch_integrate_mixed_wide(wp, st, launched));
+    TRH_CUDA(trh::launch_assemble_wide(b->params[b->wjob[w]], 0, wp.fstate, wp.cta_status,
+                                       wp.n_cta, st, launched));
+  }
   return TRH_OK;
 }
 
@@ -1392,6 +1469,10 @@ int trh_batch_run(trh_batch* b, void* stream) {
     bool rebuilt = false;
     int rc = build_tables(J.c, st, &launched, &rebuilt);
     if (rc != TRH_OK) return rc;
+    if (J.c->precision == TRH_MIXED) {  // a batch holds the images of all of a job's sets
+      rc = ensure_images(J.c, 0, J.c->n_sets, st, &launched);
+      if (rc != TRH_OK) return rc;
+    }
     if (J.c->bulk_n > 0) {
       for (size_t i = 0; i < j; ++i)
         if (b->jobs[i].c == J.c)
@@ -1456,8 +1537,9 @@ int trh_batch_run(trh_batch* b, void* stream) {
       }
     }
   }
-  S.kernels_launched =
-      replayed ? (b->n_small > 0) + (b->n_wide > 0) + (b->n_mixed > 0) : launched;
+  S.kernels_launched = replayed ? (b->n_small > 0) + (b->n_wide > 0) + (b->n_mixed > 0) +
+                                      2 * (int)b->wparams.size()
+                                : launched;
   S.ms_integrate = elapsed_ms(b->ev[0], b->ev[1]);
   S.wide_tile = b->wide_tile;
   S.graph_replay = replayed ? 1 : 0;

@@ -427,6 +427,63 @@ __device__ __forceinline__ void wide_gauss_jordan(WideSmem& S, double2* X, doubl
   }
 }
 
+// Row A1 for one angle: sin(theta0), Gamma^2, Gamma (evanescent branch Im <= 0) into S; a beam
+// on the Ewald circle sets S.status = kGrazing. Ends with a barrier.
+__device__ __forceinline__ void wide_gamma(WideSmem& S, const IntegrateParams& p, int angle) {
+  const int tid = threadIdx.x, N = p.N;
+  const double t0 = p.ang.theta0[angle] * (kPiW / 180.0);
+  const double phi = p.ang.phi_a1 + p.ang.theta1[angle] * (kPiW / 180.0);
+  const double bmag = p.ang.gamma * cos(t0);
+  const double b0x = bmag * cos(phi), b0y = bmag * sin(phi);
+  if (tid == 0) S.sin_t0 = sin(t0);
+  for (int j = tid; j < N; j += WT) {
+    const double qx = b0x + p.ang.kvec[j].x, qy = b0y + p.ang.kvec[j].y;
+    const double g2 = p.ang.gamma * p.ang.gamma - (qx * qx + qy * qy);
+    double gr = 0.0, gi = 0.0;
+    if (g2 >= 0.0) gr = sqrt(g2);
+    else gi = -sqrt(-g2);
+    if (fabs(g2) < 1e-12 * p.ang.gamma * p.ang.gamma) S.status = kGrazing;
+    S.gam2[j] = g2;
+    S.Gr[j] = gr;
+    S.Gi[j] = gi;
+  }
+  __syncthreads();
+}
+
+// rho(0) = B A^{-1} e_1 with A = Gamma Q - i P, B = Gamma Q + i P (Eq. vrhocomp) from the final
+// Q, P (overwritten), and eta (Section 2.1); NaN outputs unless S.status is kOk.
+__device__ __forceinline__ void wide_assemble(WideSmem& S, const IntegrateParams& p, size_t pair,
+                                              double2* Q, double2* P) {
+  const int tid = threadIdx.x, N = p.N;
+  const size_t NN = (size_t)N * N;
+  if (S.status == kOk) {
+    for (size_t e = tid; e < NN; e += WT) {
+      const int j = (int)(e / N);
+      const double2 q = Q[e], pp = P[e];
+      const double gqr = S.Gr[j] * q.x - S.Gi[j] * q.y, gqi = S.Gr[j] * q.y + S.Gi[j] * q.x;
+      Q[e] = make_double2(gqr + pp.y, gqi - pp.x);
+      P[e] = make_double2(gqr - pp.y, gqi + pp.x);
+    }
+    __syncthreads();
+    wide_gauss_jordan(S, Q, P, N);   // P <- B A^{-1}; rho = its first column
+  }
+  __syncthreads();
+  const double g1 = sqrt(S.gam2[0]);
+  for (int j = tid; j < N; j += WT) {
+    double2 rho = make_double2(NAN, NAN);
+    double eta = NAN;
+    if (S.status == kOk) {
+      rho = P[(size_t)j * N];
+      const double g2 = S.gam2[j];
+      eta = (g2 > 0.0) ? (rho.x * rho.x + rho.y * rho.y) * S.sin_t0 * g1 / sqrt(g2) : 0.0;
+    }
+    p.out.rho[pair * N + j] = rho;
+    p.out.eta[pair * N + j] = eta;
+  }
+  if (tid == 0) p.out.status[pair] = S.status;
+  __syncthreads();
+}
+
 // The conventional multi-slice method (Section 2.2) as the comparison point for Algorithm 1:
 // per slice i, the exponential of h B at the slice midpoint m_i = z_i + h/2 (node 2i+1),
 //   exp(h B) = [[C, Sn], [-M Sn, C]],  C = cos(h sqrt M), Sn = sin(h sqrt M) / sqrt M,
@@ -548,24 +605,8 @@ __device__ __forceinline__ void wide_pair(WideSmem& S, double2* tbl, const Integ
     S.status = kOk;
     S.n_rhst = 0;
   }
-  const double t0 = p.ang.theta0[angle] * (kPiW / 180.0);
-  const double phi = p.ang.phi_a1 + p.ang.theta1[angle] * (kPiW / 180.0);
-  const double bmag = p.ang.gamma * cos(t0);
-  const double b0x = bmag * cos(phi), b0y = bmag * sin(phi);
   __syncthreads();
-  if (tid == 0) S.sin_t0 = sin(t0);
-  for (int j = tid; j < N; j += WT) {
-    const double qx = b0x + p.ang.kvec[j].x, qy = b0y + p.ang.kvec[j].y;
-    const double g2 = p.ang.gamma * p.ang.gamma - (qx * qx + qy * qy);
-    double gr = 0.0, gi = 0.0;
-    if (g2 >= 0.0) gr = sqrt(g2);
-    else gi = -sqrt(-g2);
-    if (fabs(g2) < 1e-12 * p.ang.gamma * p.ang.gamma) S.status = kGrazing;
-    S.gam2[j] = g2;
-    S.Gr[j] = gr;
-    S.Gi[j] = gi;
-  }
-  __syncthreads();
+  wide_gamma(S, p, angle);
   if (p.method == kMethodConventional) {
     if (S.status == kOk) wide_conventional<TB>(S, tbl, p, set, Z);
     __syncthreads();
@@ -629,34 +670,9 @@ __device__ __forceinline__ void wide_pair(WideSmem& S, double2* tbl, const Integ
       __syncthreads();
       wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * p.sch.b[s], 0.0, false);
     }
-    // A = Gamma Q - i P into Q's storage, B = Gamma Q + i P into P's
-    for (size_t e = tid; e < NN; e += WT) {
-      const int j = (int)(e / N);
-      const double2 q = Q[e], pp = P[e];
-      const double gqr = S.Gr[j] * q.x - S.Gi[j] * q.y, gqi = S.Gr[j] * q.y + S.Gi[j] * q.x;
-      Q[e] = make_double2(gqr + pp.y, gqi - pp.x);
-      P[e] = make_double2(gqr - pp.y, gqi + pp.x);
-    }
-    __syncthreads();
-    wide_gauss_jordan(S, Q, P, N);   // P <- B A^{-1}; rho = its first column
   }
-  __syncthreads();
-  const double g1 = sqrt(S.gam2[0]);
-  for (int j = tid; j < N; j += WT) {
-    double2 rho = make_double2(NAN, NAN);
-    double eta = NAN;
-    if (S.status == kOk) {
-      rho = P[(size_t)j * N];
-      const double g2 = S.gam2[j];
-      eta = (g2 > 0.0) ? (rho.x * rho.x + rho.y * rho.y) * S.sin_t0 * g1 / sqrt(g2) : 0.0;
-    }
-    p.out.rho[pair * N + j] = rho;
-    p.out.eta[pair * N + j] = eta;
-  }
-  if (tid == 0) {
-    p.out.status[pair] = S.status;
-    p.out.n_rhst[pair] = S.n_rhst;
-  }
+  wide_assemble(S, p, pair, Q, P);
+  if (tid == 0) p.out.n_rhst[pair] = S.n_rhst;
   __syncthreads();
 }
 
@@ -694,7 +710,42 @@ __global__ void __launch_bounds__(WT, 1) k_integrate_fp64_wide_items(
   }
 }
 
+// The assembly of the mixed path for 64 < N <= 128 (integrate_mixed_wide.cu), one CTA per pair:
+// the cluster kernel leaves [Q; P] in binary64 in `state` and each of its CTAs' status.
+__global__ void __launch_bounds__(WT, 1) k_assemble_wide(IntegrateParams p, int set0,
+                                                         double2* state, const int* cta_status,
+                                                         int n_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
+  const int angle = blockIdx.x;
+  const size_t lp = (size_t)blockIdx.y * p.ang.n_angles + angle;     // launch pair
+  const size_t pair = (size_t)(set0 + blockIdx.y) * p.ang.n_angles + angle;
+  const size_t NN = (size_t)p.N * p.N;
+  if (threadIdx.x == 0) {
+    int st = kOk;
+    for (int c = 0; c < n_cta && st == kOk; ++c) st = cta_status[lp * n_cta + c];
+    S.status = st;
+  }
+  __syncthreads();
+  wide_gamma(S, p, angle);
+  wide_assemble(S, p, pair, state + lp * 2 * NN, state + lp * 2 * NN + NN);
+}
+
 }  // namespace
+
+cudaError_t launch_assemble_wide(const IntegrateParams& p, int set0, double2* state,
+                                 const int* cta_status, int n_cta, cudaStream_t st,
+                                 int* n_launched) {
+  if (p.N > NW) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(WideSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_assemble_wide,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(p.ang.n_angles, p.n_sets);
+  k_assemble_wide<<<grid, WT, smem, st>>>(p, set0, state, cta_status, n_cta);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
 
 size_t integrate_fp64_wide_state_bytes(int N, int method) {
   return (method == kMethodBAB ? 2 : 6) * (size_t)N * N * sizeof(double2);

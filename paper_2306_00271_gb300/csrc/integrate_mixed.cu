@@ -43,6 +43,7 @@
 // step of iterative refinement.
 #include "dense_fp64.cuh"
 #include "internal.h"
+#include "mixed_digits.cuh"
 #include "umma.cuh"
 
 namespace trh {
@@ -50,13 +51,13 @@ namespace trh {
 namespace {
 
 using namespace umma;
+using namespace mixed;
 
 constexpr int NT = 512;
 constexpr int MT = 128;
 constexpr int KT = 128;
 constexpr int NC = 64;
 constexpr int A_LBO = 128;                   // K-blocks of 8 elements, 128 B apart
-constexpr int NDIG = 4;                      // fixed-point digits per operand
 constexpr int A_DIGITS = NDIG * MT * KT * 2;  // 128 KB: the largest image (K = 128)
 constexpr int A_SCALES = MT * 4;             // row scales
 // The digit image of a node holds only the K = 16 KS columns the products read: in each 8-row
@@ -75,9 +76,7 @@ constexpr int TS = NC + 1;                   // row stride (float2) of T = Q^{-1
                                              // column walks hit 16 distinct bank pairs per phase
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TM_QH = 256, TM_QL = 320, TM_PH = 384, TM_PL = 448;  // full rows, RHST
-constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 constexpr double kPi = 3.14159265358979323846;
-constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23: x + M - M rounds x to an integer
 
 // Columns per thread (CP) and per CTA (NCOL): one CTA covers all 64 columns with 16 per thread,
 // or each CTA of a two-CTA cluster covers 32 columns with 8 per thread (column split). The
@@ -122,48 +121,6 @@ struct __align__(128) Smem {
 
 static_assert(sizeof(Smem) + sizeof(MixedParams) + 16 + 1024 <= 232448,
               "shared memory above the 227 KB a CTA may use");
-
-// Error-free transformations. The explicit _rn intrinsics are never contracted into FMAs: a
-// contraction would make the rounded sum differ from the one the error term assumes.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-__device__ __forceinline__ float rint_magic(float x) {  // |x| < 2^22, round to nearest even
-  return __fsub_rn(__fadd_rn(x, kMagic), kMagic);
-}
-
-// Smallest power of two >= x (x > 0 finite); 1 for x == 0.
-__device__ __forceinline__ float pow2_ceil(float x) {
-  if (!(x > 0.0f)) return 1.0f;
-  const uint32_t b = __float_as_uint(x);
-  uint32_t e = b & 0x7F800000u;
-  if (b & 0x007FFFFFu) e += 0x00800000u;
-  return __uint_as_float(e);
-}
-// 1 / g for a normal power of two g, from its exponent bits.
-__device__ __forceinline__ float pow2_inv(float g) {
-  return __uint_as_float((254u << 23) - (__float_as_uint(g) & 0x7F800000u));
-}
-
-// Fixed-point digits of v = x / scale (|v| <= 1): BF16 bit patterns of d0..d3. The remainders
-// are exact in FP32 (power-of-two scalings and differences of nearby values).
-__device__ __forceinline__ void digits4(float x, float inv_scale, uint16_t (&b)[NDIG]) {
-  float v = __fmul_rn(__fmul_rn(x, inv_scale), 128.0f);
-#pragma unroll
-  for (int i = 0; i < NDIG; ++i) {
-    const float d = rint_magic(v);
-    // integers of magnitude <= 256 have zero low halves: the BF16 pattern is the top 16 bits
-    b[i] = (uint16_t)(__float_as_uint(d) >> 16);
-    v = __fmul_rn(__fsub_rn(v, d), 256.0f);
-  }
-}
 
 // Column maxima of this warp's 32 rows of |Qh|, one lane per column, into colmax[par][c][qd].
 template <int CP>
@@ -214,66 +171,6 @@ __device__ __forceinline__ void write_b_exact(Smem& S, const float (&qh)[CP], in
   column_maxima<CP>(S, qh, c0, qd, lane, par);
   __syncthreads();
   digits_b<CP>(S, qh, m, c0, qd, lane, par, par);
-}
-
-// Two 32x32b.x8 loads, one wait.
-__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, float (&va)[8], uint32_t tb,
-                                           float (&vb)[8]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(ta), "r"(tb)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    va[i] = __uint_as_float(r[i]);
-    vb[i] = __uint_as_float(r[8 + i]);
-  }
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Four 32x32b.x8 loads, one wait (the four accumulators of the column-split epilogue).
-__device__ __forceinline__ void tmem_ld8x4(uint32_t ta, float (&va)[8], uint32_t tb,
-                                           float (&vb)[8], uint32_t tc, float (&vc)[8],
-                                           uint32_t td, float (&vd)[8]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(ta), "r"(tb), "r"(tc), "r"(td)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    va[i] = __uint_as_float(r[i]);
-    vb[i] = __uint_as_float(r[8 + i]);
-    vc[i] = __uint_as_float(r[16 + i]);
-    vd[i] = __uint_as_float(r[24 + i]);
-  }
 }
 
 template <int CP>
@@ -592,7 +489,7 @@ __device__ __forceinline__ void mixed_pair(Smem& S, const MixedParams& p, int an
   const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   using Img = ImgCfg<KS>;
-  const unsigned char* img_set = p.img + (size_t)set * p.n_nodes * Img::BYTES;
+  const unsigned char* img_set = p.img + (size_t)(set - p.img_set0) * p.n_nodes * Img::BYTES;
 
   if (tid == 0) {
     S.status = kOk;
@@ -1041,7 +938,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed(MixedParams p) {
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
   const uint32_t tmem = mixed_prologue(S);
   uint32_t ph_tma = 0, ph_mma = 0, xk = 0;
-  mixed_pair<KS, false>(S, p, blockIdx.x, blockIdx.y, tmem, ph_tma, ph_mma, xk);
+  mixed_pair<KS, false>(S, p, blockIdx.x, p.set0 + blockIdx.y, tmem, ph_tma, ph_mma, xk);
   mixed_epilogue(S, tmem);
 }
 
@@ -1054,7 +951,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 1)
   const uint32_t tmem = mixed_prologue(S);
   cluster_sync();  // both CTAs' mbarriers are initialised before any remote arrival
   uint32_t ph_tma = 0, ph_mma = 0, xk = 0;
-  mixed_pair<KS, true>(S, p, blockIdx.x >> 1, blockIdx.y, tmem, ph_tma, ph_mma, xk);
+  mixed_pair<KS, true>(S, p, blockIdx.x >> 1, p.set0 + blockIdx.y, tmem, ph_tma, ph_mma, xk);
   cluster_sync();  // no CTA exits while the other may still write to its shared memory
   mixed_epilogue(S, tmem);
 }

@@ -7,7 +7,9 @@ namespace trh {
 
 constexpr int kMaxStages = 12;       // kicks per step of the longest splitting scheme (SRKN_11^b)
 constexpr int kMaxBeamsFp64 = 64;    // FP64 path: state resident in shared memory up to N = 64
-constexpr int kMaxBeamsMixed = 64;   // mixed path: one 128-row UMMA tile holds [Re; Im] of N <= 64
+constexpr int kMaxBeamsMixed = 64;   // mixed path, one cluster of <= 2 CTAs: one 128-row UMMA
+                                     // tile holds [Re; Im] of N <= 64
+constexpr int kMaxBeamsMixedWide = 128;  // mixed path with two row tiles and ceil(N / 32) CTAs
 constexpr int kMaxBeamsWide = 256;   // FP64 path with the state in global memory (64 < N <= 256)
 
 // Integration methods of the kernels (IntegrateParams::method).
@@ -98,6 +100,8 @@ struct MixedParams {
   double2* ckpt;               // optional checkpoints as in IntegrateParams (binary64 values of
   int ckpt_every, n_ckpt;      // the double-float state), or nullptr
   int N, n_nodes, n_sets, L;
+  int set0;                    // grid launches: blockIdx.y = set - set0 (sets in chunks)
+  int img_set0;                // the set whose digit image starts at img
   int n_mma;                   // UMMA N: N rounded up to 16
   int k_slices;                // UMMA K slices of 16: ceil(2N / 16)
   double h;
@@ -107,6 +111,30 @@ struct MixedParams {
   // s = merged last/first kick (b_s + b_0), s+1 = final kick (b_s); drift index r = a_r.
   float kick_hi[kMaxStages + 2], kick_lo[kMaxStages + 2];
   float drift_hi[kMaxStages], drift_lo[kMaxStages];
+};
+
+// Mixed path for 64 < N <= 128 (integrate_mixed_wide.cu): a cluster of n_cta = ceil(N / 32) CTAs
+// per (set, angle) pair, each owning 32 columns of Q and P. The digit image of U(tau) per node
+// has one power-of-two scale per node (every row of U holds u_0 on its diagonal, so the node's
+// largest entry bounds every row) and is laid out in streaming stages; see integrate_mixed_wide.cu.
+struct MixedWideParams {
+  MixedParams m;               // scheme coefficients, angles, outputs, p0, N, n_nodes, n_sets, L,
+                               // k_slices (ceil(2N / 16)), threshold; m.img = wide images
+  const float* scale;          // [sets][n_nodes] the scale of each node's image (from img_set0)
+  // per-launch scratch, indexed by the launch's own pair (set - m.set0) * n_angles + angle:
+  double2* fstate;             // [pairs][2][N][N] final Q, P in binary64 for the assembly kernel
+  float* zg;                   // [pairs][4][N][2N] RHST gather buffer: Qh, Ql, Ph, Pl by column
+  int* cta_status;             // [pairs][n_cta] status of each CTA of the pair
+  int n_cta;                   // CTAs per pair (cluster size)
+};
+
+struct MixedWideImageParams {
+  const double2* u;            // FP64 table [n_sets][n_nodes][M]
+  const int* lmap;             // [N][N]
+  unsigned char* img;          // [n_sets][n_nodes][mixed_wide_image_bytes_per_node(k_slices)]
+  float* scale;                // [n_sets][n_nodes]
+  int N, M, n_nodes, n_sets;
+  int k_slices;                // ceil(2N / 16)
 };
 
 // Reverse sweep of the FP64 path (adjoint_fp64.cu): gradients of the specular intensity with
@@ -165,6 +193,34 @@ cudaError_t launch_integrate_mixed_items(const MixedParams* jobs, const int4* it
                                          int* n_launched);
 // Bytes of one node's digit image: four planes of 128 rows x 16 k_slices BF16 plus 128 row scales.
 size_t mixed_image_bytes_per_node(int k_slices);
+// Position of kick node n (node s i + r at z_i + c_r h with c_r = a_0 + ... + a_{r-1}; the last
+// node, s L, at z_e + L h): the one formula of the host tables and of the no-allocation entry's
+// device kernel, summed in the same order on both.
+__host__ __device__ inline double node_position(const Scheme& sch, long long n, int L, double z_e,
+                                                double h) {
+  if (n == (long long)sch.s * L) return z_e + L * h;
+  const long long i = n / sch.s;
+  const int r = (int)(n - i * sch.s);
+  double c = 0.0;
+  for (int q = 0; q < r; ++q) c += sch.a[q];
+  return z_e + (double)i * h + c * h;
+}
+
+// Host geometry (geometry.cpp), shared by every entry point; nothing here allocates.
+// The splitting scheme of a trh_integrator value (SRKN_6^b for sp4, SRKN_11^b for sp6, two
+// nodes per step for RK4 and the conventional method).
+void bab_scheme(int integrator, Scheme* s);
+// Reciprocal rods kvec [2N], distinct differences g_j - g_k into gdiff [2 N^2] (the first 2 *M
+// entries used, ids in order of first appearance over j, then k) and the index map lmap [N^2]
+// of Eq. sch2, with a caller-provided hash table of `slots` entries (geometry_slots(N)).
+// Returns -1, or the index of a beam that repeats an earlier one.
+int build_geometry(const int* beams, int N, const double a1[2], const double a2[2], double* kvec,
+                   double* gdiff, int* lmap, int* M, long long* ws_keys, int* ws_ids, int slots);
+int geometry_slots(int N);
+// gamma = sqrt(E^2 + 2 E mc^2) / (hbar c) in 1/A for kinetic energy E (eV).
+double vacuum_wavenumber(double energy_ev);
+// (s - i absorption) 4 pi gamma_L / A_cell, the prefactor of u_g (the potential model).
+double2 potential_prefactor(int particle, double energy_ev, double absorption, double area);
 // Records the message trh_last_error() returns on this thread.
 void set_last_error(const char* msg);
 // split: two CTAs (a cluster) per pair, each owning 32 columns; needs N > 32.
@@ -192,5 +248,19 @@ cudaError_t launch_integrate_fp64_wide_items(const IntegrateParams* jobs, const 
                                              cudaStream_t st, int* n_launched);
 size_t integrate_fp64_wide_state_bytes(int N, int method);
 bool mixed_available();
+// Mixed path for 64 < N <= 128: node images, the cluster kernel, and (integrate_fp64_wide.cu) the
+// binary64 assembly of rho and eta from the final state the cluster kernel leaves in fstate.
+size_t mixed_wide_image_bytes_per_node(int k_slices);
+cudaError_t launch_umma_images_wide(const MixedWideImageParams& p, cudaStream_t st,
+                                    int* n_launched);
+cudaError_t launch_integrate_mixed_wide(const MixedWideParams& p, cudaStream_t st,
+                                        int* n_launched);
+// rho, eta, status of the pairs of sets set0 .. set0 + n_sets - 1 of `p` (p.n_sets of them) from
+// [Q; P] in `state` ([launch pair][2][N][N], launch pair = (set - set0) * n_angles + angle); a
+// pair whose cta_status[launch pair][0 .. n_cta-1] holds a failure gets NaN outputs and that
+// status.
+cudaError_t launch_assemble_wide(const IntegrateParams& p, int set0, double2* state,
+                                 const int* cta_status, int n_cta, cudaStream_t st,
+                                 int* n_launched);
 
 }  // namespace trh

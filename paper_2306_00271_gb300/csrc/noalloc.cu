@@ -1,13 +1,13 @@
-// trh_rocking_curve_noalloc: the binary64 rocking curve for one structure without any device
+// trh_rocking_curve_noalloc: the binary64 rocking curve of one structure without any device
 // allocation.
 //
-// Who needs it: callers that cannot call cudaMalloc at the point where they want a rocking curve,
-// e.g. code running inside a stream capture (an allocation there is not capturable), code with a
-// fixed memory budget that must not grow the device heap, or plug-in hosts that own all device
-// memory themselves. They pass device buffers for inputs and outputs; everything else the
-// computation needs (potential table, scattering factors, geometry tables, status words) lives
-// in one file-scope device array of fixed size, kNoallocScratchBytes, which every GPU that loads
-// this library keeps until the process exits.
+// Who needs it: callers that cannot call cudaMalloc at the point where they want a rocking curve:
+// code that runs under a fixed device-memory budget which must not grow, plug-ins whose host
+// application owns and hands out all device memory itself, and loops where cudaMalloc's implicit
+// device synchronisation is not acceptable. They pass device buffers for the angles and the
+// outputs; everything else the computation needs (potential table, scattering factors, geometry
+// tables, status words) lives in one file-scope device array of fixed size,
+// kNoallocScratchBytes, which every GPU that loads this library keeps until the process exits.
 //
 // Contract (also stated in include/trheed.h):
 //   - The first call on a device looks up the array's device address with cudaGetSymbolAddress
@@ -18,6 +18,9 @@
 //     start at zero: every byte a kernel reads is written earlier in the same call. Calls whose
 //     work overlaps on the GPU (different streams, or different host threads) race on the array.
 //   - Problems whose tables do not fit are rejected with TRH_EINVAL before any device work.
+//   - The geometry (rods, differences, index map), the splitting coefficients, the kick
+//     positions and the constants come from the same code as trh_create's (geometry.cpp,
+//     trh::node_position), so the results equal trh_rocking_curve's with TRH_FP64.
 #include "trheed.h"
 #include "internal.h"
 
@@ -29,9 +32,7 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(16) << 20;  // 16 MiB
 constexpr int kMaxDevices = 64;
-constexpr double kPi = 3.14159265358979323846;
-constexpr double kHbarC = 1973.269804;   // eV * Angstrom
-constexpr double kMc2 = 510998.95;       // electron rest energy, eV
+constexpr int kMaxN = trh::kMaxBeamsFp64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -44,19 +45,11 @@ int fail(int code, const char* msg) {
   return code;
 }
 
-// Node positions z_i + c_r h of a BAB scheme (node s*i + r; last node at 0).
-__global__ void k_noalloc_nodes(double* node_z, int n_nodes, int s, double z_e, double h, int L,
+// Kick positions (the same formula as the host tables of trh_create).
+__global__ void k_noalloc_nodes(double* node_z, int n_nodes, double z_e, double h, int L,
                                 trh::Scheme sch) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= n_nodes) return;
-  if (n == s * L) {
-    node_z[n] = z_e + L * h;
-    return;
-  }
-  const int i = n / s, r = n - i * s;
-  double c = 0.0;
-  for (int q = 0; q < r; ++q) c += sch.a[q];
-  node_z[n] = z_e + i * h + c * h;
+  if (n < n_nodes) node_z[n] = trh::node_position(sch, n, L, z_e, h);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -90,68 +83,19 @@ extern "C" int trh_rocking_curve_noalloc(const trh_problem* p, int n_angles, con
     for (int i = 0; i < 4; ++i)
       if (!(p->sf[8 * sp + 4 + i] > 0)) return fail(TRH_EINVAL, "scattering b must be > 0");
 
-  // host geometry in fixed-size arrays: rods, distinct differences, index map
-  double kvec[2 * 64], gvec[2 * 64 * 64];
-  int lmap[64 * 64], dm1[64 * 64], dm2[64 * 64];
-  const double b1x = 2 * kPi * p->a2[1] / det, b1y = -2 * kPi * p->a2[0] / det;
-  const double b2x = -2 * kPi * p->a1[1] / det, b2y = 2 * kPi * p->a1[0] / det;
-  for (int j = 0; j < N; ++j) {
-    const int m1 = p->beams[2 * j], m2 = p->beams[2 * j + 1];
-    for (int k = 0; k < j; ++k)
-      if (p->beams[2 * k] == m1 && p->beams[2 * k + 1] == m2)
-        return fail(TRH_EINVAL, "duplicate beam");
-    kvec[2 * j] = m1 * b1x + m2 * b2x;
-    kvec[2 * j + 1] = m1 * b1y + m2 * b2y;
-  }
+  // host geometry in fixed-size arrays (no heap): rods, distinct differences, index map
+  double kvec[2 * kMaxN], gvec[2 * kMaxN * kMaxN];
+  int lmap[kMaxN * kMaxN];
+  long long hkeys[2 * kMaxN * kMaxN];
+  int hids[2 * kMaxN * kMaxN];
+  static_assert(2 * kMaxN * kMaxN >= 16, "hash table");
   int M = 0;
-  for (int j = 0; j < N; ++j)
-    for (int k = 0; k < N; ++k) {
-      const int d1 = p->beams[2 * j] - p->beams[2 * k], d2 = p->beams[2 * j + 1] - p->beams[2 * k + 1];
-      int id = -1;
-      for (int q = 0; q < M; ++q)
-        if (dm1[q] == d1 && dm2[q] == d2) {
-          id = q;
-          break;
-        }
-      if (id < 0) {
-        id = M++;
-        dm1[id] = d1;
-        dm2[id] = d2;
-        gvec[2 * id] = d1 * b1x + d2 * b2x;
-        gvec[2 * id + 1] = d1 * b1y + d2 * b2y;
-      }
-      lmap[j * N + k] = id;
-    }
-
+  const int slots = trh::geometry_slots(N);
+  if (slots > 2 * kMaxN * kMaxN) return fail(TRH_EINVAL, "need 1 <= N <= 64");
+  if (trh::build_geometry(p->beams, N, p->a1, p->a2, kvec, gvec, lmap, &M, hkeys, hids, slots) >= 0)
+    return fail(TRH_EINVAL, "duplicate beam");
   trh::Scheme sch{};
-  if (p->integrator == TRH_SP4) {
-    const double a1 = 0.209515106613362, a2 = -0.143851773179818, a3 = 0.5 - a1 - a2;
-    const double b1 = 0.0792036964311957, b2 = 0.353172906049774, b3 = -0.0420650803577195;
-    const double b4 = 1.0 - 2.0 * (b1 + b2 + b3);
-    const double a[6] = {a1, a2, a3, a3, a2, a1}, b[7] = {b1, b2, b3, b4, b3, b2, b1};
-    sch.s = 6;
-    for (int i = 0; i < 6; ++i) sch.a[i] = a[i];
-    for (int i = 0; i < 7; ++i) sch.b[i] = b[i];
-  } else {
-    const double aa[5] = {0.123229775946271, 0.290553797799558, -0.127049212625417,
-                          -0.246331761062075, 0.357208872795928};
-    const double bb[5] = {0.0414649985182624, 0.198128671918067, -0.0400061921041533,
-                          0.0752539843015807, -0.0115113874206879};
-    double sa = 0, sb = 0;
-    for (int i = 0; i < 5; ++i) {
-      sa += aa[i];
-      sb += bb[i];
-    }
-    sch.s = 11;
-    for (int i = 0; i < 5; ++i) {
-      sch.a[i] = aa[i];
-      sch.a[10 - i] = aa[i];
-      sch.b[i] = bb[i];
-      sch.b[11 - i] = bb[i];
-    }
-    sch.a[5] = 1.0 - 2.0 * sa;
-    sch.b[5] = sch.b[6] = 0.5 - sb;
-  }
+  trh::bab_scheme(p->integrator, &sch);
   const int L = p->n_steps, s = sch.s;
   const double h = -p->z_e / L;
   const long long n_nodes = (long long)s * L + 1;
@@ -224,7 +168,7 @@ extern "C" int trh_rocking_curve_noalloc(const trh_problem* p, int n_angles, con
   NA_CUDA(cudaMemcpyAsync(base + o_sf, p->sf, (size_t)p->n_species * 64, cudaMemcpyHostToDevice,
                           st));
   k_noalloc_nodes<<<(unsigned)((n_nodes + 255) / 256), 256, 0, st>>>(
-      reinterpret_cast<double*>(base + o_nodes), (int)n_nodes, s, p->z_e, h, L, sch);
+      reinterpret_cast<double*>(base + o_nodes), (int)n_nodes, p->z_e, h, L, sch);
   NA_CUDA(cudaGetLastError());
 
   trh::PotentialParams pp{};
@@ -234,8 +178,7 @@ extern "C" int trh_rocking_curve_noalloc(const trh_problem* p, int n_angles, con
   pp.species = reinterpret_cast<const int*>(base + o_sp);
   pp.sf = reinterpret_cast<const double*>(base + o_sf);
   pp.node_z = reinterpret_cast<const double*>(base + o_nodes);
-  const double scale = 4.0 * kPi * (1.0 + p->energy_ev / kMc2) / std::fabs(det);
-  pp.pref = make_double2(p->particle * scale, -p->absorption * scale);
+  pp.pref = trh::potential_prefactor(p->particle, p->energy_ev, p->absorption, std::fabs(det));
   pp.M = M;
   pp.n_atoms = p->n_atoms;
   pp.n_nodes = (int)n_nodes;
@@ -251,8 +194,7 @@ extern "C" int trh_rocking_curve_noalloc(const trh_problem* p, int n_angles, con
   ip.ang.theta0 = theta0;
   ip.ang.theta1 = theta1;
   ip.ang.kvec = reinterpret_cast<const double2*>(base + o_k);
-  const double E = p->energy_ev;
-  ip.ang.gamma = std::sqrt(E * E + 2.0 * E * kMc2) / kHbarC;
+  ip.ang.gamma = trh::vacuum_wavenumber(p->energy_ev);
   ip.ang.phi_a1 = std::atan2(p->a1[1], p->a1[0]);
   ip.ang.n_angles = n_angles;
   ip.out.rho = static_cast<double2*>(rho_out);

@@ -169,6 +169,66 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, float (&va)[16], uint32
     vb[i] = __uint_as_float(r[16 + i]);
   }
 }
+// Two 32x32b.x8 loads, one wait.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, float (&va)[8], uint32_t tb,
+                                           float (&vb)[8]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(r[8 + i]);
+  }
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Four 32x32b.x8 loads, one wait (the four accumulators of the column-split epilogue).
+__device__ __forceinline__ void tmem_ld8x4(uint32_t ta, float (&va)[8], uint32_t tb,
+                                           float (&vb)[8], uint32_t tc, float (&vc)[8],
+                                           uint32_t td, float (&vd)[8]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb), "r"(tc), "r"(td)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(r[8 + i]);
+    vc[i] = __uint_as_float(r[16 + i]);
+    vd[i] = __uint_as_float(r[24 + i]);
+  }
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
@@ -280,6 +340,25 @@ __device__ __forceinline__ bool cluster_exchange(uint64_t* bars, uint32_t peer, 
   __syncthreads();
   const int slot = (int)(xk & 1u);
   if (threadIdx.x == 0) mbar_arrive_remote(mapa_u32(smem_u32(&bars[slot]), peer));
+  const bool ok = mbar_wait_cluster(&bars[slot], (xk >> 1) & 1u, max_cycles);
+  ++xk;
+  return __syncthreads_and(ok) != 0;
+}
+
+// One exchange among the n_cta CTAs of a cluster (each mbarrier of bars[] initialised with count
+// n_cta - 1): every CTA has written its part of the payload into the others' shared memory (or
+// into global memory); thread q < n_cta (q != rank) makes a release arrival on CTA q's
+// bars[xk % 2], then every thread waits (bounded, acquire) on this CTA's. A CTA passes exchange
+// e only after every other CTA has arrived at e, so no CTA can arrive at e + 2 before all have
+// passed e: two alternating mbarriers suffice, as for two CTAs. Returns false for every thread
+// after a timed-out wait (the CTAs are then out of step).
+__device__ __forceinline__ bool cluster_exchange_n(uint64_t* bars, uint32_t n_cta, uint32_t rank,
+                                                   uint32_t& xk, long long max_cycles) {
+  fence_acq_rel_cluster();
+  __syncthreads();
+  const int slot = (int)(xk & 1u);
+  if (threadIdx.x < n_cta && threadIdx.x != rank)
+    mbar_arrive_remote(mapa_u32(smem_u32(&bars[slot]), threadIdx.x));
   const bool ok = mbar_wait_cluster(&bars[slot], (xk >> 1) & 1u, max_cycles);
   ++xk;
   return __syncthreads_and(ok) != 0;

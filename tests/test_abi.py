@@ -84,7 +84,7 @@ def test_create_rejects_nonzero_first_beam(lib):
 
 
 def test_large_beam_sets_are_unsupported_not_wrong(lib):
-    """FP64 takes N <= 256, the mixed path N <= 64; both limits are checked before any device
+    """FP64 takes N <= 256, the mixed path N <= 128; both limits are checked before any device
     work, so they are reported here without a GPU."""
     a1, a2 = W.hex_lattice(3.84)
     wl = W.trhepd_n61()
@@ -92,7 +92,7 @@ def test_large_beam_sets_are_unsupported_not_wrong(lib):
     p, keep = _problem(wl)
     ctx = C.c_void_p()
     assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
-    wl.beams = W.beam_shell(a1, a2, 31.0)
+    wl.beams = W.beam_disk(a1, a2, 129)
     p, keep = _problem(wl, precision=1)
     assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
     # RK4 runs on the FP64 path only
