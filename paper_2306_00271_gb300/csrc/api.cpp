@@ -369,9 +369,10 @@ static double2 potential_prefactor(const trh_ctx* c) {
 constexpr size_t kDefaultImageBudget = size_t(40) << 30;
 
 static size_t mixed_image_bytes_per_set(const trh_ctx* c) {
-  const int ks = (2 * c->N + 15) / 16;
-  const size_t per_node = c->N > trh::kMaxBeamsMixed ? trh::mixed_wide_image_bytes_per_node(ks)
-                                                     : trh::mixed_image_bytes_per_node(ks);
+  const size_t per_node =
+      c->N > trh::kMaxBeamsMixed
+          ? trh::mixed_wide_image_bytes_per_node(trh::mixed_wide_k_slices(c->N))
+          : trh::mixed_image_bytes_per_node((2 * c->N + 15) / 16);
   return per_node * (size_t)c->n_nodes;
 }
 
@@ -382,19 +383,28 @@ static int mixed_chunk_sets(const trh_ctx* c) {
   return (int)std::min<size_t>(k, (size_t)c->n_sets);
 }
 
-// Digit images of sets s0 .. s0 + ns - 1 on the mixed path from the binary64 potential table:
-// one image per node with row scales (N <= 64, integrate_mixed.cu) or in streaming stages with
-// one scale per node (N > 64, integrate_mixed_wide.cu); nothing to do if d_img holds them.
-static int ensure_images(trh_ctx* c, int s0, int ns, cudaStream_t st, int* launched) {
-  if (c->img_valid && c->img_s0 == s0 && c->img_ns == ns) return TRH_OK;
-  const int ks = (2 * c->N + 15) / 16;
+// Image buffers of the mixed path sized for ns sets (d_img, and d_scale for N > 64); a buffer
+// that moves invalidates batch plans, which hold the pointers.
+static int alloc_images(trh_ctx* c, int ns) {
   const unsigned char* old = c->d_img.p;
   TRH_CUDA(c->d_img.ensure((size_t)ns * mixed_image_bytes_per_set(c)));
-  const double2* u = c->d_u.p + (size_t)s0 * c->n_nodes * c->M;
+  if (c->d_img.p != old) c->generation++;
   if (c->N > trh::kMaxBeamsMixed) {
     const float* olds = c->d_scale.p;
     TRH_CUDA(c->d_scale.ensure((size_t)ns * c->n_nodes));
     if (c->d_scale.p != olds) c->generation++;
+  }
+  return TRH_OK;
+}
+
+// Enqueues the digit images of sets s0 .. s0 + ns - 1 from the binary64 potential table into
+// d_img (allocated for at least ns sets): one image per node with row scales (N <= 64,
+// integrate_mixed.cu) or in streaming stages with one scale per node (N > 64,
+// integrate_mixed_wide.cu).
+static int launch_images(trh_ctx* c, int s0, int ns, cudaStream_t st, int* launched) {
+  const int ks = (2 * c->N + 15) / 16;
+  const double2* u = c->d_u.p + (size_t)s0 * c->n_nodes * c->M;
+  if (c->N > trh::kMaxBeamsMixed) {
     trh::MixedWideImageParams mp{};
     mp.u = u;
     mp.lmap = c->d_lmap.p;
@@ -404,7 +414,7 @@ static int ensure_images(trh_ctx* c, int s0, int ns, cudaStream_t st, int* launc
     mp.M = c->M;
     mp.n_nodes = c->n_nodes;
     mp.n_sets = ns;
-    mp.k_slices = ks;
+    mp.k_slices = trh::mixed_wide_k_slices(c->N);
     TRH_CUDA(trh::launch_umma_images_wide(mp, st, launched));
   } else {
     trh::MixedImageParams mp{};
@@ -418,16 +428,27 @@ static int ensure_images(trh_ctx* c, int s0, int ns, cudaStream_t st, int* launc
     mp.n_sets = ns;
     TRH_CUDA(trh::launch_umma_images(mp, st, launched));
   }
-  if (c->d_img.p != old) c->generation++;  // batch plans hold the image pointer
+  return TRH_OK;
+}
+
+// The images of sets s0 .. s0 + ns - 1 in d_img, built unless d_img already holds exactly those.
+static int ensure_images(trh_ctx* c, int s0, int ns, cudaStream_t st, int* launched) {
+  if (c->img_valid && c->img_s0 == s0 && c->img_ns == ns) return TRH_OK;
+  int rc = alloc_images(c, ns);
+  if (rc != TRH_OK) return rc;
+  rc = launch_images(c, s0, ns, st, launched);
+  if (rc != TRH_OK) return rc;
   c->img_valid = true;
   c->img_s0 = s0;
   c->img_ns = ns;
   return TRH_OK;
 }
 
-// Potential tables (and, on the mixed path when all sets' images fit the budget, the
-// tensor-core images) if the structure changed; events ev[0], ev[1] bracket them. Sets *rebuilt.
-static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuilt) {
+// Potential tables (and, with `images` on the mixed path when all sets' images fit the budget,
+// the tensor-core images) if the structure changed; events ev[0], ev[1] bracket them. Sets
+// *rebuilt.
+static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuilt,
+                        bool images = true) {
   *rebuilt = c->tables_dirty;
   if (!c->tables_dirty) return TRH_OK;
   TRH_CUDA(cudaEventRecord(c->ev[0], st));
@@ -449,7 +470,7 @@ static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuil
   TRH_CUDA(trh::launch_potential(pp, st, launched));
   c->img_valid = false;
   c->tables_dirty = false;
-  if (c->precision == TRH_MIXED && mixed_chunk_sets(c) >= c->n_sets) {
+  if (images && c->precision == TRH_MIXED && mixed_chunk_sets(c) >= c->n_sets) {
     const int rc = ensure_images(c, 0, c->n_sets, st, launched);
     if (rc != TRH_OK) return rc;
   }
@@ -518,7 +539,8 @@ static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParam
   mp.n_sets = c->n_sets;
   mp.L = c->L;
   mp.n_mma = (c->N + 15) / 16 * 16;
-  mp.k_slices = (2 * c->N + 15) / 16;
+  mp.k_slices = c->N > trh::kMaxBeamsMixed ? trh::mixed_wide_k_slices(c->N)
+                                           : (2 * c->N + 15) / 16;
   mp.h = c->h;
   mp.threshold = c->threshold;
   const int sc = c->scheme.s;
@@ -1265,21 +1287,32 @@ struct trh_batch {
     double* eta;
     unsigned long long generation;
   };
+  // A chunk of the mixed jobs' parameter sets whose digit images are resident together: for job
+  // j the sets s0[j] .. s0[j] + ns[j] - 1 (ns = 0 for FP64 jobs and jobs with no set in it).
+  struct Chunk {
+    std::vector<int> s0, ns;
+    size_t item_off = 0;     // its mixed items (N <= 64) in d_items
+    int n_items = 0, ctas = 0;
+  };
   std::vector<Job> jobs;
   bool prepared = false;
   std::vector<size_t> offset;            // first pair of each job in the status array
   size_t total_pairs = 0;
-  int n_small = 0, n_wide = 0, n_mixed = 0, wide_tile = 0, wide_ctas = 0, small_ctas = 0,
-      mixed_ctas = 0, max_m_wide = 0;
+  int n_small = 0, n_wide = 0, wide_tile = 0, wide_ctas = 0, small_ctas = 0, max_m_wide = 0;
+  int launches_per_run = 0;
   size_t slot_elems = 0;
+  bool chunked = false;                  // images are built per chunk in the launch sequence
+  std::vector<Chunk> chunks;
   std::vector<trh::IntegrateParams> params;
-  std::vector<trh::MixedParams> mparams;
-  // mixed jobs with 64 < N <= 128: one cluster launch and one assembly launch each
+  std::vector<trh::MixedParams> mparams;       // [chunk][job]
+  // launches of mixed jobs with 64 < N <= 128 (a cluster kernel and the assembly each), in chunk
+  // order, with their chunk and job
   std::vector<trh::MixedWideParams> wparams;
+  std::vector<int> wchunk;
   std::vector<size_t> wjob;
   DevBuf<trh::IntegrateParams> d_params;
   DevBuf<trh::MixedParams> d_mparams;
-  DevBuf<int4> d_items;                  // small items, then wide items
+  DevBuf<int4> d_items;                  // FP64 N <= 64 items, FP64 wide items, mixed by chunk
   DevBuf<int> d_status, d_counter;
   DevBuf<double2> d_state;
   cudaGraph_t graph = nullptr;
@@ -1314,7 +1347,26 @@ int trh_batch_add(trh_batch* b, trh_ctx* c, int n_angles, const double* theta0,
   return TRH_OK;
 }
 
-// Work lists, job parameters and scratch for the current jobs and tables.
+// Chunks the mixed jobs' sets need: their digit images together against the largest image
+// budget among them; 1 when they fit at once.
+static int batch_image_chunks(const trh_batch* b) {
+  size_t total = 0, budget = 0;
+  int max_sets = 1;
+  for (const auto& J : b->jobs)
+    if (J.c->precision == TRH_MIXED) {
+      total += (size_t)J.c->n_sets * mixed_image_bytes_per_set(J.c);
+      budget = std::max(budget, J.c->img_budget);
+      max_sets = std::max(max_sets, J.c->n_sets);
+    }
+  if (total <= budget || budget == 0) return 1;
+  return (int)std::min<size_t>((total + budget - 1) / budget, (size_t)max_sets);
+}
+
+// Work lists, job parameters and scratch for the current jobs and tables. FP64 items run in
+// two persistent launches (N <= 64; wide and RK4); the mixed jobs' sets are split into chunks
+// (batch_image_chunks) and each chunk runs one persistent launch of its N <= 64 items and one
+// cluster launch (plus assembly) per job with 64 < N <= 128, after its images are built (in the
+// launch sequence when there is more than one chunk).
 static int batch_prepare(trh_batch* b, cudaStream_t st) {
   b->drop_graph();
   b->offset.clear();
@@ -1324,13 +1376,14 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   struct Item {
     double cost;
     int4 w;
-    int family;   // 0: FP64 N <= 64, 1: FP64 wide or RK4, 2: mixed precision N <= 64
+    int family;   // 0: FP64 N <= 64, 1: FP64 wide or RK4
   };
   std::vector<Item> items;
   int max_n_wide = 0;
   trh_ctx* tune_ctx = nullptr;
   b->max_m_wide = 0;
-  for (size_t j = 0; j < b->jobs.size(); ++j) {
+  const size_t nj = b->jobs.size();
+  for (size_t j = 0; j < nj; ++j) {
     trh_batch::Job& J = b->jobs[j];
     trh_ctx* c = J.c;
     const size_t pairs = (size_t)c->n_sets * J.n_angles;
@@ -1342,15 +1395,13 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
     b->params.push_back(ip);
     J.generation = c->generation;
     b->total_pairs += pairs;
-    const bool wide = c->precision == TRH_FP64 &&
-                      (c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4 ||
-                     c->integrator == TRH_CONVENTIONAL);
-    const int family = c->precision == TRH_MIXED ? 2 : (wide ? 1 : 0);
+    if (c->precision == TRH_MIXED) continue;  // chunked below
+    const bool wide = c->N > trh::kMaxBeamsFp64 || c->integrator == TRH_RK4 ||
+                      c->integrator == TRH_CONVENTIONAL;
     const double cost = (double)c->N * c->N * c->N * c->L * c->scheme.s;
-    if (c->precision == TRH_MIXED && c->N > trh::kMaxBeamsMixed) continue;  // cluster launches
     for (int set = 0; set < c->n_sets; ++set)
       for (int a = 0; a < J.n_angles; ++a)
-        items.push_back({cost, make_int4((int)j, set, a, 0), family});
+        items.push_back({cost, make_int4((int)j, set, a, 0), wide ? 1 : 0});
     if (wide) {
       if (c->N > max_n_wide) {
         max_n_wide = c->N;
@@ -1364,48 +1415,99 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   }
   // statuses of job j live at offset[j] (and n_rhst at total_pairs + offset[j])
   TRH_CUDA(b->d_status.ensure(2 * b->total_pairs));
-  b->mparams.clear();
-  b->wparams.clear();
-  b->wjob.clear();
-  for (size_t j = 0; j < b->jobs.size(); ++j) {
+  for (size_t j = 0; j < nj; ++j) {
     b->params[j].out.status = b->d_status.p + b->offset[j];
     b->params[j].out.n_rhst = b->d_status.p + b->total_pairs + b->offset[j];
-    trh_ctx* c = b->jobs[j].c;
-    b->mparams.push_back(mixed_params(c, b->params[j]));
-    if (c->precision == TRH_MIXED && c->N > trh::kMaxBeamsMixed) {
-      const size_t lp = (size_t)c->n_sets * b->jobs[j].n_angles, N = (size_t)c->N;
-      const int n_cta = (c->N + 31) / 32;
-      TRH_CUDA(c->d_wide.ensure(lp * 2 * N * N));
-      TRH_CUDA(c->d_zg.ensure(lp * 4 * N * 2 * N));
-      TRH_CUDA(c->d_cst.ensure(lp * n_cta));
-      trh::MixedWideParams wp{};
-      wp.m = b->mparams.back();
-      wp.scale = c->d_scale.p;
-      wp.fstate = c->d_wide.p;
-      wp.zg = c->d_zg.p;
-      wp.cta_status = c->d_cst.p;
-      wp.n_cta = n_cta;
-      b->wparams.push_back(wp);
-      b->wjob.push_back(j);
-    }
   }
-  // longest-processing-time first within each kernel family
+  // longest-processing-time first within each FP64 family
   std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
     if (x.family != y.family) return x.family < y.family;
     return x.cost > y.cost;
   });
   std::vector<int4> w;
-  b->n_small = b->n_wide = b->n_mixed = 0;
+  b->n_small = b->n_wide = 0;
   for (const Item& it : items) {
     w.push_back(it.w);
-    (it.family == 0 ? b->n_small : (it.family == 1 ? b->n_wide : b->n_mixed))++;
+    (it.family == 0 ? b->n_small : b->n_wide)++;
   }
   int dev = 0, n_sm = 0;
   TRH_CUDA(cudaGetDevice(&dev));
   TRH_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   b->small_ctas = std::min(b->n_small, n_sm);
   b->wide_ctas = std::min(b->n_wide, n_sm);
-  b->mixed_ctas = std::min(b->n_mixed, n_sm);
+
+  // mixed jobs: chunk k holds sets [k n_sets / K, (k + 1) n_sets / K) of every mixed job
+  const int K = batch_image_chunks(b);
+  b->chunked = K > 1;
+  b->chunks.assign(K, trh_batch::Chunk{});
+  b->mparams.assign((size_t)K * nj, trh::MixedParams{});
+  b->wparams.clear();
+  b->wchunk.clear();
+  b->wjob.clear();
+  std::vector<int> ns_max(nj, 0);
+  for (int k = 0; k < K; ++k) {
+    trh_batch::Chunk& ch = b->chunks[k];
+    ch.s0.assign(nj, 0);
+    ch.ns.assign(nj, 0);
+    for (size_t j = 0; j < nj; ++j) {
+      trh_ctx* c = b->jobs[j].c;
+      if (c->precision != TRH_MIXED) continue;
+      ch.s0[j] = (int)((long long)k * c->n_sets / K);
+      ch.ns[j] = (int)((long long)(k + 1) * c->n_sets / K) - ch.s0[j];
+      ns_max[j] = std::max(ns_max[j], ch.ns[j]);
+    }
+  }
+  for (size_t j = 0; j < nj; ++j) {
+    trh_ctx* c = b->jobs[j].c;
+    if (c->precision != TRH_MIXED || ns_max[j] == 0) continue;
+    if (b->chunked) {
+      int rc = alloc_images(c, ns_max[j]);
+      if (rc != TRH_OK) return rc;
+      b->jobs[j].generation = c->generation;
+    }
+    if (c->N > trh::kMaxBeamsMixed) {
+      const size_t lp = (size_t)ns_max[j] * b->jobs[j].n_angles, N = (size_t)c->N;
+      TRH_CUDA(c->d_wide.ensure(lp * 2 * N * N));
+      TRH_CUDA(c->d_zg.ensure(lp * 4 * N * 2 * N));
+      TRH_CUDA(c->d_cst.ensure(lp * ((c->N + 31) / 32)));
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    trh_batch::Chunk& ch = b->chunks[k];
+    std::vector<Item> mi;
+    for (size_t j = 0; j < nj; ++j) {
+      trh_ctx* c = b->jobs[j].c;
+      trh::MixedParams& mp = b->mparams[(size_t)k * nj + j];
+      mp = mixed_params(c, b->params[j]);
+      if (c->precision != TRH_MIXED || ch.ns[j] == 0) continue;
+      mp.img_set0 = ch.s0[j];
+      if (c->N > trh::kMaxBeamsMixed) {
+        trh::MixedWideParams wp{};
+        wp.m = mp;
+        wp.m.set0 = ch.s0[j];
+        wp.m.n_sets = ch.ns[j];
+        wp.scale = c->d_scale.p;
+        wp.fstate = c->d_wide.p;
+        wp.zg = c->d_zg.p;
+        wp.cta_status = c->d_cst.p;
+        wp.n_cta = (c->N + 31) / 32;
+        b->wparams.push_back(wp);
+        b->wchunk.push_back(k);
+        b->wjob.push_back(j);
+        continue;
+      }
+      const double cost = (double)c->N * c->N * c->N * c->L * c->scheme.s;
+      for (int set = ch.s0[j]; set < ch.s0[j] + ch.ns[j]; ++set)
+        for (int a = 0; a < b->jobs[j].n_angles; ++a)
+          mi.push_back({cost, make_int4((int)j, set, a, 0), 2});
+    }
+    std::stable_sort(mi.begin(), mi.end(),
+                     [](const Item& x, const Item& y) { return x.cost > y.cost; });
+    ch.item_off = w.size();
+    ch.n_items = (int)mi.size();
+    ch.ctas = std::min(ch.n_items, n_sm);
+    for (const Item& it : mi) w.push_back(it.w);
+  }
   TRH_CUDA(b->d_params.ensure(b->params.size()));
   TRH_CUDA(cudaMemcpy(b->d_params.p, b->params.data(),
                       b->params.size() * sizeof(trh::IntegrateParams), cudaMemcpyHostToDevice));
@@ -1415,12 +1517,12 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   TRH_CUDA(b->d_items.ensure(w.size() > 0 ? w.size() : 1));
   if (!w.empty())
     TRH_CUDA(cudaMemcpy(b->d_items.p, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  TRH_CUDA(b->d_counter.ensure(3));
+  TRH_CUDA(b->d_counter.ensure(2 + (size_t)K));
   b->wide_tile = 0;
   if (b->n_wide > 0) {
     TRH_CUDA(b->d_state.ensure(b->wide_ctas * b->slot_elems));
     // the tuner probes the largest wide job with its own parameters and scratch
-    for (size_t j = 0; j < b->jobs.size(); ++j)
+    for (size_t j = 0; j < nj; ++j)
       if (b->jobs[j].c == tune_ctx) {
         int rc = tune_wide_tile(tune_ctx, b->params[j], b->d_state.p, st, &b->wide_tile);
         if (rc != TRH_OK) return rc;
@@ -1433,9 +1535,12 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
   return TRH_OK;
 }
 
-// The batch's device work: counters reset, then the persistent launches of the three families.
+// The batch's device work: counters reset, the two FP64 persistent launches, then chunk by
+// chunk the mixed jobs' images (when chunked), the persistent launch of the chunk's N <= 64
+// mixed items and the cluster launches (with their assembly) of its 64 < N <= 128 mixed jobs.
 static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
-  TRH_CUDA(cudaMemsetAsync(b->d_counter.p, 0, 3 * sizeof(int), st));
+  const size_t nj = b->jobs.size();
+  TRH_CUDA(cudaMemsetAsync(b->d_counter.p, 0, (2 + b->chunks.size()) * sizeof(int), st));
   if (b->n_small > 0)
     TRH_CUDA(trh::launch_integrate_fp64_items(b->d_params.p, b->d_items.p, b->n_small,
                                               b->d_counter.p, b->small_ctas, st, launched));
@@ -1443,15 +1548,27 @@ static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
     TRH_CUDA(trh::launch_integrate_fp64_wide_items(
         b->d_params.p, b->d_items.p + b->n_small, b->n_wide, b->d_counter.p + 1, b->d_state.p,
         b->slot_elems, b->max_m_wide, b->wide_tile, b->wide_ctas, st, launched));
-  if (b->n_mixed > 0)
-    TRH_CUDA(trh::launch_integrate_mixed_items(b->d_mparams.p,
-                                               b->d_items.p + b->n_small + b->n_wide, b->n_mixed,
-                                               b->d_counter.p + 2, b->mixed_ctas, st, launched));
-  for (size_t w = 0; w < b->wparams.size(); ++w) {
-    const trh::MixedWideParams& wp = b->wparams[w];
-    TRH_CUDA(trh::launch_integrate_mixed_wide(wp, st, launched));
-    TRH_CUDA(trh::launch_assemble_wide(b->params[b->wjob[w]], 0, wp.fstate, wp.cta_status,
-                                       wp.n_cta, st, launched));
+  size_t w = 0;
+  for (size_t k = 0; k < b->chunks.size(); ++k) {
+    const trh_batch::Chunk& ch = b->chunks[k];
+    if (b->chunked)
+      for (size_t j = 0; j < nj; ++j)
+        if (ch.ns[j] > 0) {
+          const int rc = launch_images(b->jobs[j].c, ch.s0[j], ch.ns[j], st, launched);
+          if (rc != TRH_OK) return rc;
+        }
+    if (ch.n_items > 0)
+      TRH_CUDA(trh::launch_integrate_mixed_items(b->d_mparams.p + k * nj,
+                                                 b->d_items.p + ch.item_off, ch.n_items,
+                                                 b->d_counter.p + 2 + k, ch.ctas, st, launched));
+    for (; w < b->wparams.size() && b->wchunk[w] == (int)k; ++w) {
+      const trh::MixedWideParams& wp = b->wparams[w];
+      TRH_CUDA(trh::launch_integrate_mixed_wide(wp, st, launched));
+      trh::IntegrateParams ipc = b->params[b->wjob[w]];
+      ipc.n_sets = wp.m.n_sets;
+      TRH_CUDA(trh::launch_assemble_wide(ipc, wp.m.set0, wp.fstate, wp.cta_status, wp.n_cta, st,
+                                         launched));
+    }
   }
   return TRH_OK;
 }
@@ -1467,12 +1584,8 @@ int trh_batch_run(trh_batch* b, void* stream) {
     if (!J.c->ev[0])
       for (int i = 0; i < 6; ++i) TRH_CUDA(cudaEventCreate(&J.c->ev[i]));
     bool rebuilt = false;
-    int rc = build_tables(J.c, st, &launched, &rebuilt);
+    int rc = build_tables(J.c, st, &launched, &rebuilt, false);
     if (rc != TRH_OK) return rc;
-    if (J.c->precision == TRH_MIXED) {  // a batch holds the images of all of a job's sets
-      rc = ensure_images(J.c, 0, J.c->n_sets, st, &launched);
-      if (rc != TRH_OK) return rc;
-    }
     if (J.c->bulk_n > 0) {
       for (size_t i = 0; i < j; ++i)
         if (b->jobs[i].c == J.c)
@@ -1482,9 +1595,22 @@ int trh_batch_run(trh_batch* b, void* stream) {
                         &p0);
       if (rc != TRH_OK) return rc;
     }
-    if (J.c->generation != J.generation) stale = true;
   }
-  if (stale) {
+  // mixed jobs' images: all of them now when they fit the budget, else chunk by chunk in the
+  // launch sequence
+  const bool chunked = batch_image_chunks(b) > 1;
+  for (auto& J : b->jobs)
+    if (J.c->precision == TRH_MIXED) {
+      if (chunked) {
+        J.c->img_valid = false;  // the run leaves the last chunk's images in d_img
+      } else {
+        const int rc = ensure_images(J.c, 0, J.c->n_sets, st, &launched);
+        if (rc != TRH_OK) return rc;
+      }
+    }
+  for (auto& J : b->jobs)
+    if (J.c->generation != J.generation) stale = true;
+  if (stale || chunked != b->chunked) {
     int rc = batch_prepare(b, st);
     if (rc != TRH_OK) return rc;
   }
@@ -1496,8 +1622,11 @@ int trh_batch_run(trh_batch* b, void* stream) {
   } else {
     // eager run (sets every kernel attribute), then capture the same sequence for next time on
     // the batch's own stream (capturing records the work without running it)
-    int rc = batch_launch(b, st, &launched);
+    int n_run = 0;
+    int rc = batch_launch(b, st, &n_run);
     if (rc != TRH_OK) return rc;
+    launched += n_run;
+    b->launches_per_run = n_run;
     if (!b->capture_stream)
       TRH_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
     int ignored = 0;
@@ -1537,9 +1666,8 @@ int trh_batch_run(trh_batch* b, void* stream) {
       }
     }
   }
-  S.kernels_launched = replayed ? (b->n_small > 0) + (b->n_wide > 0) + (b->n_mixed > 0) +
-                                      2 * (int)b->wparams.size()
-                                : launched;
+  S.kernels_launched = replayed ? b->launches_per_run : launched;
+  S.set_chunks = (int)b->chunks.size();
   S.ms_integrate = elapsed_ms(b->ev[0], b->ev[1]);
   S.wide_tile = b->wide_tile;
   S.graph_replay = replayed ? 1 : 0;

@@ -9,15 +9,19 @@
 // it is 64 floats per thread, held in registers for the whole integration; the kick and the drift
 // act column by column (W_c = U Q_c, Section 3.4), so the CTAs run their kicks without talking.
 //
-// U(tau) streaming. The node's digit image (2 row tiles x 16 KS KB at K = 16 KS) is too large to
-// keep in shared memory, so it is cut into stages of (row tile, KC K-slices), 32 KB each, and
-// streamed through NBUF = 4 stage buffers by bulk copies (TMA engine): thread 0 consumes a stage
-// (waits for its bytes, issues its MMAs, commits them to the buffer's "empty" mbarrier) and
-// refills the buffer the previous stage used with the stage NBUF - 1 ahead, so copies overlap
-// the MMAs; the first stages of the next node are fetched during the current kick's MMAs and
-// land during its epilogue. All rows of a node share one power-of-two scale (every row of U holds
-// u_0 on its diagonal and |u_g| <= |u_0| for a non-negative potential, so the node's largest
-// entry bounds every row to within a factor of two), which the epilogue reads from a small table.
+// U(tau) streaming. The node's digit image (2 row tiles x 16 KSP KB, K = 16 KSP with KSP =
+// ceil(2N / 16) rounded up to a multiple of 4; the padding slices are zero) is too large to keep
+// in shared memory, so it is cut into stages of (row tile, KC = 2 K-slices), 32 KB each, and
+// streamed through NBUF = 4 stage buffers by bulk copies (TMA engine). Warp 0 runs the stages of
+// a kick, unrolled at compile time: it waits for a stage's bytes, lane 0 issues its MMAs and
+// commits them to the buffer's "empty" mbarrier, and the buffer the previous stage used is
+// refilled with the stage NBUF - 1 ahead, so copies overlap the MMAs; within a step the first
+// stages of the next node are fetched during the current kick's MMAs and land during its
+// epilogue. (The scalar work of the one issuing thread per MMA must stay below the tensor core's
+// time per MMA, about 50-130 cycles here: hence the compile-time descriptors.) All rows of a node
+// share one power-of-two scale (every row of U holds u_0 on its diagonal and |u_g| <= |u_0| for a
+// non-negative potential, so the node's largest entry bounds every row to within a factor of
+// two), which the epilogue reads from a small table.
 //
 // Per kick, per row tile r and digit a of U: one MMA per K-slice against the B planes b = 3-a..0
 // of this CTA's columns (stored in reverse plane order, so the planes are contiguous), into the
@@ -79,19 +83,6 @@ constexpr double kPi = 3.14159265358979323846;
 // SBO = 256 ks_c, so one stage is one contiguous bulk copy.
 __host__ __device__ inline size_t wide_node_bytes(int ks) { return (size_t)R * ks * SLICE_BYTES; }
 
-// The stage pipeline of one CTA, driven by thread 0 alone. Stage g (counted over the whole
-// integration) is row tile r = (g % SPK) / nch and K-chunk c = (g % SPK) % nch of node g / SPK
-// (kick g / SPK uses node g / SPK). full[b]: the bytes of the stage in buffer b have landed;
-// empty[b]: the MMAs that read buffer b have completed (committed by thread 0).
-struct Pipe {
-  long long g_issue, g_cons, total;
-  uint32_t pf, pe, busy;       // parities of full[b] and empty[b]; busy: a commit to empty[b] is
-                               // outstanding (not yet waited for)
-  int spk, nch, ks;
-  const unsigned char* img_set;
-  size_t node_bytes;
-};
-
 struct __align__(1024) WSmem {
   unsigned char A[A_BYTES];     // NBUF stage buffers; T = Q^{-1} (FP32 complex) during the RHST
   unsigned char B[B_BYTES];     // digit planes of this CTA's columns of Q; Z staging in the RHST
@@ -111,7 +102,6 @@ struct __align__(1024) WSmem {
   float2 gstage[2][NW];         // Gauss-Jordan: column k at the start of step k, by parity
   int gpr[2];                   // ... and its pivot row
   int piv[NW], ipiv[NW];
-  Pipe pipe;                    // thread 0's stage pipeline
 };
 static_assert(sizeof(WSmem) + 1024 <= 232448, "shared memory above the 227 KB a CTA may use");
 
@@ -199,75 +189,112 @@ __global__ void __launch_bounds__(256) k_umma_images_wide(MixedWideImageParams p
   }
 }
 
-__device__ __forceinline__ bool pipe_issue(WSmem& S, Pipe& q) {
-  const long long g = q.g_issue;
-  const int b = (int)(g % NBUF);
+// The stage pipeline of one CTA, run by the 32 lanes of warp 0 together: every lane waits on the
+// same mbarrier (the outcome made warp-uniform), lane 0 alone issues copies and MMAs. A kick's
+// SPK = 2 KSP / KC stages (row tile r = st / NCH, K-chunk c = st % NCH) are unrolled at compile
+// time, so buffer indices and descriptor offsets are constants: the one issuing thread must not
+// spend more per MMA than the tensor core does. Stage st always uses buffer st % NBUF (NBUF
+// divides SPK). The parities of full[b] and empty[b] and the "a commit to empty[b] is not yet
+// waited for" flags are bit b of pf, pe and busy; "a copy into b is not yet consumed" is bit b of
+// inflight (drained before exit).
+struct PipeBits {
+  uint32_t pf = 0, pe = 0, busy = 0, inflight = 0;
+};
+
+__device__ __forceinline__ bool wait_warp(uint64_t* bar, uint32_t parity) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, kWaitCycles)) != 0;
+}
+
+// Copies stage st of the node image `img` into buffer st % NBUF once its previous MMAs are done.
+template <int KSP>
+__device__ __forceinline__ bool stage_issue(WSmem& S, PipeBits& q, int st,
+                                            const unsigned char* img, int lane) {
+  constexpr int NCH = KSP / KC;
+  const int b = st % NBUF, r = st / NCH, c = st % NCH;
   if ((q.busy >> b) & 1u) {
-    if (!mbar_wait(&S.empty[b], (q.pe >> b) & 1u, kWaitCycles)) return false;
+    if (!wait_warp(&S.empty[b], (q.pe >> b) & 1u)) return false;
     q.pe ^= 1u << b;
     q.busy &= ~(1u << b);
   }
-  const long long node = g / q.spk;
-  const int st = (int)(g - node * q.spk);
-  const int r = st / q.nch, c = st - r * q.nch;
-  const int ks_c = min(KC, q.ks - KC * c);
-  const uint32_t bytes = (uint32_t)ks_c * SLICE_BYTES;
-  const unsigned char* src = q.img_set + (size_t)node * q.node_bytes +
-                             (size_t)r * q.ks * SLICE_BYTES + (size_t)c * KC * SLICE_BYTES;
-  mbar_arrive_expect_tx(&S.full[b], bytes);
-  bulk_g2s(S.A + b * STAGE_BYTES, src, bytes, &S.full[b]);
-  q.g_issue = g + 1;
+  if (lane == 0) {
+    mbar_arrive_expect_tx(&S.full[b], STAGE_BYTES);
+    bulk_g2s(S.A + b * STAGE_BYTES, img + (size_t)(r * KSP + c * KC) * SLICE_BYTES, STAGE_BYTES,
+             &S.full[b]);
+  }
+  q.inflight |= 1u << b;
+  __syncwarp();
   return true;
 }
 
-// Keep NBUF - 1 stages issued ahead of consumption: the stage issued after consuming g goes to
-// the buffer of stage g - 1, whose MMAs run ahead of g's.
-__device__ __forceinline__ bool pipe_fill(WSmem& S, Pipe& q) {
-  while (q.g_issue < q.total && q.g_issue < q.g_cons + NBUF - 1)
-    if (!pipe_issue(S, q)) return false;
-  return true;
-}
-
-// Waits for the next stage and issues its MMAs: for each digit a of U and K-slice of the stage,
-// one MMA of N = 32 (4 - a) columns (B planes b = 3 - a .. 0 of this CTA) into the order
-// accumulators of the stage's row tile (the first MMA of a tile clears all four).
-__device__ __forceinline__ bool pipe_consume(WSmem& S, Pipe& q, uint32_t tmem, uint32_t b_base) {
-  const long long g = q.g_cons;
-  const int b = (int)(g % NBUF);
-  if (!mbar_wait(&S.full[b], (q.pf >> b) & 1u, kWaitCycles)) return false;
-  q.pf ^= 1u << b;
-  tc_fence_after();
-  const int st = (int)(g % q.spk);
-  const int r = st / q.nch, c = st - r * q.nch;
-  const int ks_c = min(KC, q.ks - KC * c);
-  const uint32_t a_base = smem_u32(S.A + b * STAGE_BYTES);
+// The MMAs of one kick (warp 0): for each stage, wait for its bytes, then for each digit a of U
+// and K-slice of the stage one MMA of N = 32 (4 - a) columns (B planes b = 3 - a .. 0 of this
+// CTA) into the order accumulators of the stage's row tile (the first MMA of a tile clears all
+// four), a commit that frees the buffer, and the copy of the stage NBUF - 1 ahead (of this node,
+// or of `next` when the next kick's node may be prefetched). `prefetched`: stages
+// 0 .. NBUF - 2 of this kick were issued by the previous kick. Ends with a commit to bar_mma.
+template <int KSP>
+__device__ __forceinline__ bool kick_mma(WSmem& S, PipeBits& q, const unsigned char* img,
+                                         const unsigned char* next, bool prefetched,
+                                         uint32_t tmem, uint32_t b_base, int lane) {
+  constexpr int NCH = KSP / KC;
+  constexpr int SPK = R * NCH;
+  static_assert(SPK % NBUF == 0, "stages of a kick must fill whole buffer rounds");
+  bool ok = true;
+  if (!prefetched) {
 #pragma unroll
-  for (int a = 0; a < NDIG; ++a) {
-    const uint64_t ad = smem_desc(a_base + a * ks_c * PLANE_SLICE, 128, 256 * ks_c);
-    const uint64_t bd = smem_desc(b_base + a * BT, B_LBO, B_SBO);
-    const uint32_t id = idesc_bf16_f32(MT, CW * (NDIG - a));
-    for (int qq = 0; qq < ks_c; ++qq) {
-      const int ksg = KC * c + qq;
-      mma_bf16(tmem + (uint32_t)(MT * r), ad + (uint64_t)((qq * 256) >> 4),
-               bd + (uint64_t)((ksg * 2 * B_LBO) >> 4), id, !(a == 0 && ksg == 0));
-    }
+    for (int st = 0; st < NBUF - 1; ++st)
+      if (ok) ok = stage_issue<KSP>(S, q, st, img, lane);
   }
-  mma_commit(&S.empty[b]);
-  q.busy |= 1u << b;
-  q.g_cons = g + 1;
-  return true;
+#pragma unroll
+  for (int st = 0; st < SPK; ++st) {
+    if (!ok) break;
+    const int b = st % NBUF, r = st / NCH, c = st % NCH;
+    if (!wait_warp(&S.full[b], (q.pf >> b) & 1u)) {
+      ok = false;
+      break;
+    }
+    q.pf ^= 1u << b;
+    q.inflight &= ~(1u << b);
+    if (lane == 0) {
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(S.A + b * STAGE_BYTES);
+#pragma unroll
+      for (int a = 0; a < NDIG; ++a) {
+        const uint64_t ad = smem_desc(a_base + a * KC * PLANE_SLICE, 128, 256 * KC);
+        const uint64_t bd = smem_desc(b_base + a * BT, B_LBO, B_SBO);
+        const uint32_t id = idesc_bf16_f32(MT, CW * (NDIG - a));
+#pragma unroll
+        for (int qq = 0; qq < KC; ++qq) {
+          const int ksg = KC * c + qq;
+          mma_bf16(tmem + (uint32_t)(MT * r), ad + (uint64_t)((qq * 256) >> 4),
+                   bd + (uint64_t)((ksg * 2 * B_LBO) >> 4), id, !(a == 0 && ksg == 0));
+        }
+      }
+      mma_commit(&S.empty[b]);
+    }
+    q.busy |= 1u << b;
+    __syncwarp();
+    const int ahead = st + NBUF - 1;
+    if (ahead < SPK) ok = stage_issue<KSP>(S, q, ahead, img, lane);
+    else if (next) ok = stage_issue<KSP>(S, q, ahead - SPK, next, lane);
+  }
+  if (lane == 0) mma_commit(&S.bar_mma);
+  __syncwarp();
+  return ok;
 }
 
-// Waits for every issued but unconsumed stage (their data is dropped; they are issued again by
-// the next pipe_fill), so that no copy is in flight into the stage buffers.
-__device__ __forceinline__ bool pipe_drain(WSmem& S, Pipe& q) {
-  for (long long g = q.g_cons; g < q.g_issue; ++g) {
-    const int b = (int)(g % NBUF);
-    if (!mbar_wait(&S.full[b], (q.pf >> b) & 1u, kWaitCycles)) return false;
-    q.pf ^= 1u << b;
-  }
-  q.g_issue = q.g_cons;
-  return true;
+// Waits for every copy issued and not consumed (after a timed-out wait), so that none lands after
+// the CTA has moved on.
+__device__ __forceinline__ bool pipe_drain(WSmem& S, PipeBits& q) {
+  bool ok = true;
+#pragma unroll
+  for (int b = 0; b < NBUF; ++b)
+    if ((q.inflight >> b) & 1u) {
+      if (!wait_warp(&S.full[b], (q.pf >> b) & 1u)) ok = false;
+      q.pf ^= 1u << b;
+    }
+  q.inflight = 0;
+  return ok;
 }
 
 // Column maxima of |Qh| over this thread's rows of both tiles, reduced over the warp's 32 lanes
@@ -499,7 +526,10 @@ __device__ __forceinline__ void wapply(WSmem& S, const float* zg, const float2* 
     }
 }
 
-// One (set, angle) pair per cluster of n_cta CTAs (blockIdx.x = n_cta angle + rank).
+// One (set, angle) pair per cluster of n_cta CTAs (blockIdx.x = n_cta angle + rank). KSP: the
+// K-slices of the images (ceil(2N / 16) rounded up to a multiple of 4, so that a kick's stages
+// fill whole rounds of the NBUF buffers; the padding slices are zero).
+template <int KSP>
 __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_wide(const MixedWideParams wp) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   WSmem& S = *reinterpret_cast<WSmem*>(smem_raw);
@@ -509,7 +539,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_wide(const MixedWideP
   const uint32_t n_cta = (uint32_t)wp.n_cta;
   const uint32_t rank = cluster_ctarank();
   const int angle = blockIdx.x / n_cta, set = p.set0 + blockIdx.y;
-  const int N = p.N, KS = p.k_slices;
+  const int N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;             // outputs
   const size_t lp = (size_t)blockIdx.y * p.ang.n_angles + angle;        // launch scratch
   const int cbase = CW * (int)rank + CP * cq;  // this thread's first column (of all N)
@@ -593,26 +623,15 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_wide(const MixedWideP
   fence_proxy_async_smem();
 
   const int s = p.sch.s;
-  const int nch = (KS + KC - 1) / KC;
-  Pipe& q = S.pipe;
-  if (tid == 0) {
-    q = Pipe{};
-    q.spk = R * nch;
-    q.nch = nch;
-    q.ks = KS;
-    q.node_bytes = wide_node_bytes(KS);
-    q.img_set = p.img + (size_t)(set - p.img_set0) * p.n_nodes * q.node_bytes;
-    q.total = (long long)q.spk * ((long long)s * p.L + 1);
-  }
-  const int spk = R * nch;
+  PipeBits q;                          // meaningful in warp 0 only
+  const size_t node_bytes = wide_node_bytes(KSP);
+  const unsigned char* img_set = p.img + (size_t)(set - p.img_set0) * p.n_nodes * node_bytes;
   const float* scale_set = wp.scale + (size_t)(set - p.img_set0) * p.n_nodes;
   const uint32_t b_base = smem_u32(S.B);
-  int abort = (S.status != kOk);
-  if (tid == 0 && !abort && !pipe_fill(S, q)) S.status = kTimeout;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  abort = (S.status != kOk);
+  int abort = (S.status != kOk);
 
   uint32_t ph_mma = 0, xk = 0;
   int kick_no = 0;
@@ -623,14 +642,14 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_wide(const MixedWideP
       const int kidx = last ? s + 1 : (r > 0 ? r : (i == 0 ? 0 : s));
       const float alpha = __ldg(scale_set + kick_no);
       int to = 0;
-      if (tid == 0) {
-        bool ok = true;
-        for (int st = 0; st < spk && ok; ++st) {
-          ok = pipe_consume(S, q, tmem, b_base);
-          if (ok) ok = pipe_fill(S, q);
-        }
-        if (!ok) to = 1;
-        mma_commit(&S.bar_mma);
+      if (warp == 0) {
+        // the next kick's first stages are fetched now unless it starts a new step (an RHST may
+        // come first and use the stage buffers)
+        const unsigned char* img = img_set + (size_t)kick_no * node_bytes;
+        const bool more = !last && r + 1 < nk;
+        if (!kick_mma<KSP>(S, q, img, more ? img + node_bytes : nullptr, r > 0, tmem, b_base,
+                           lane))
+          to = 1;
       }
       if (!mbar_wait(&S.bar_mma, ph_mma, kWaitCycles)) to = 1;
       ph_mma ^= 1;
@@ -795,12 +814,9 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_wide(const MixedWideP
           zg[((size_t)3 * N + col) * n2 + m] = Pl[rt][c];
         }
       }
-      // the prefetched stages would land where T goes: wait for them (issued again below)
-      int dto = 0;
-      if (tid == 0 && !pipe_drain(S, q)) dto = 1;
+      // (no copy is in flight: the last kick of a step fetches nothing ahead)
       __threadfence();
-      if (__syncthreads_or(dto) ||
-          !cluster_exchange_n(S.bar_x, n_cta, rank, xk, kWaitCycles)) {
+      if (!cluster_exchange_n(S.bar_x, n_cta, rank, xk, kWaitCycles)) {
         if (tid == 0) S.status = kTimeout;
         abort = 1;
         break;
@@ -835,17 +851,11 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_wide(const MixedWideP
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      if (tid == 0 && !pipe_fill(S, q)) S.status = kTimeout;
-      __syncthreads();
-      if (S.status != kOk) {
-        abort = 1;
-        break;
-      }
     }
   }
 
-  // drain: copies issued but never consumed must land before the CTA exits
-  if (tid == 0 && !pipe_drain(S, q)) S.status = kTimeout;
+  // drain: copies issued but never consumed (after a timed-out wait) land before the CTA exits
+  if (warp == 0 && !pipe_drain(S, q) && lane == 0) S.status = kTimeout;
   __syncthreads();
   if (abort && tid == 0 && S.status == kOk) S.status = kTimeout;
   __syncthreads();
@@ -900,8 +910,11 @@ cudaError_t launch_integrate_mixed_wide(const MixedWideParams& p, cudaStream_t s
       CW * n_cta < p.m.N || p.m.ckpt)
     return cudaErrorInvalidValue;
   const size_t smem = sizeof(WSmem) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_integrate_mixed_wide,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*fn)(const MixedWideParams) = nullptr;
+  if (p.m.k_slices == 12) fn = k_integrate_mixed_wide<12>;
+  else if (p.m.k_slices == 16) fn = k_integrate_mixed_wide<16>;
+  else return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(n_cta * p.m.ang.n_angles), (unsigned)p.m.n_sets, 1);
@@ -915,7 +928,7 @@ cudaError_t launch_integrate_mixed_wide(const MixedWideParams& p, cudaStream_t s
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_integrate_mixed_wide, p);
+  e = cudaLaunchKernelEx(&cfg, fn, p);
   if (n_launched) *n_launched += 1;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -251,6 +251,9 @@ bool mixed_available();
 // Mixed path for 64 < N <= 128: node images, the cluster kernel, and (integrate_fp64_wide.cu) the
 // binary64 assembly of rho and eta from the final state the cluster kernel leaves in fstate.
 size_t mixed_wide_image_bytes_per_node(int k_slices);
+// K-slices of the wide images: ceil(2N / 16) rounded up to a multiple of 4 (12 or 16 for
+// 64 < N <= 128), so a kick's streamed stages fill whole rounds of the stage buffers.
+inline int mixed_wide_k_slices(int N) { return ((2 * N + 15) / 16 + 3) / 4 * 4; }
 cudaError_t launch_umma_images_wide(const MixedWideImageParams& p, cudaStream_t st,
                                     int* n_launched);
 cudaError_t launch_integrate_mixed_wide(const MixedWideParams& p, cudaStream_t st,
