@@ -322,52 +322,161 @@ def run_gradient(local: int, slices: int = 0, warmup: int = 1, path: str = "fp64
 
 
 def run_batches(slices: int = 0):
-    """Batched-workload lines (parameter sets of uneven beam counts, 60 angles each), each batch
-    one persistent launch per kernel family replayed from its CUDA graph, timed with CUDA events
-    around the replay (after one eager run that also captures the graph).
-
-    mixed: 8 perturbed structures, 4 with 31 and 4 with 61 beams, mixed path, 2000 slices.
-    fp64_wide: 2 structures with 121 beams on the FP64 path (N > 64), 250 slices (an FP64 step
-    at this N costs ~8 ms per angle on one SM, so the full 2000 slices would take minutes)."""
+    """A small batched line: 8 perturbed structures (4 with 31 and 4 with 61 beams) x 60 angles
+    on the mixed path at 2000 slices, one persistent launch replayed from its CUDA graph, timed
+    with CUDA events around the replay (after one eager run that also captures the graph); the
+    per-curve error of each batched curve against the FP64 GPU path is reported beside it."""
     import torch
+    from oracle.curve import curve_error
     from paper_2306_00271_gb300 import api
     sets = W.batch_sets(12)
-    out = {}
-    plans = {"mixed": ("mixed", {31: [], 61: []}, slices or 2000),
-             "fp64_wide": ("fp64", {121: []}, slices or 250)}
+    classes = {31: [], 61: []}
     for s_ in sets:
-        for name, (_, classes, _) in plans.items():
-            n = s_.beams.shape[0]
-            if n in classes and len(classes[n]) < (4 if name == "mixed" else 2):
-                classes[n].append(s_)
-    for name, (path, classes, L) in plans.items():
-        batch = api.Batch()
-        engines, n_angles = [], 0
-        for n, members in classes.items():
-            wl = members[0].with_steps(L)
-            eng = api.Engine(wl, path, "sp4")
-            eng.set_structures(np.stack([m.atoms for m in members]))
-            batch.add(eng, wl.theta0, wl.theta1)
-            engines.append(eng)
-            n_angles += len(members) * len(wl.theta0)
-        batch.run()                      # eager run + capture
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record()
-        batch.run()                      # graph replay
-        ev1.record()
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        st = batch.stats()
-        out[name] = {"value": n_angles / (ms / 1e3), "unit": "angles/s", "ms": ms,
-                     "angles": n_angles, "slices": L, "path": path,
-                     "beam_classes": {str(n): len(m) for n, m in classes.items()},
+        n = s_.beams.shape[0]
+        if n in classes and len(classes[n]) < 4:
+            classes[n].append(s_)
+    L = slices or 2000
+    batch = api.Batch()
+    engines, outs, n_angles = {}, {}, 0
+    for n, members in classes.items():
+        wl = members[0].with_steps(L)
+        eng = api.Engine(wl, "mixed", "sp4")
+        eng.set_structures(np.stack([m.atoms for m in members]))
+        outs[n] = batch.add(eng, wl.theta0, wl.theta1)
+        engines[n] = (eng, wl, members)
+        n_angles += len(members) * len(wl.theta0)
+    batch.run()                      # eager run + capture
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    batch.run()                      # graph replay
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = batch.stats()
+    errs = []
+    for n, (eng, wl, members) in engines.items():
+        ref = api.Engine(wl, "fp64", "sp4")
+        ref.set_structures(np.stack([m.atoms for m in members]))
+        _, eta_f = ref.rocking_curve(wl.theta0, wl.theta1)
+        eta_b = outs[n][1].cpu().numpy()
+        eta_f = eta_f.cpu().numpy()
+        errs += [curve_error(eta_b[k], eta_f[k]) for k in range(len(members))]
+        ref.close()
+    out = {"mixed": {"value": n_angles / (ms / 1e3), "unit": "angles/s", "ms": ms,
+                     "angles": n_angles, "slices": L, "path": "mixed",
+                     "beam_classes": {str(n): len(m[2]) for n, m in engines.items()},
                      "graph_replay": st["graph_replay"], "launches": st["kernels_launched"],
-                     "wide_tile": st["wide_tile"]}
-        batch.close()
-        for e in engines:
-            e.close()
+                     "per_curve_error_vs_fp64_gpu": {"max": float(np.max(errs)),
+                                                     "median": float(np.median(errs)),
+                                                     "curves": len(errs)}}}
+    batch.close()
+    for eng, _, _ in engines.values():
+        eng.close()
+    return out
+
+
+def run_wide_121(slices: int = 0):
+    """One 121-beam structure of the batched workload (set 2: 10 keV positrons, hexagonal 3.84 A,
+    2000 slices, 60 angles) on the mixed path (a 4-CTA cluster per angle) and on the FP64 wide
+    kernel at the same full depth: angles/s of each and the curve error between them."""
+    import torch
+    from oracle.curve import curve_error
+    from paper_2306_00271_gb300 import api
+    wl = [s for s in W.batch_sets(3) if s.beams.shape[0] == 121][0]
+    if slices:
+        wl = wl.with_steps(slices)
+    out, etas = {}, {}
+    for path in ("mixed", "fp64"):
+        # one call each (the FP64 curve takes half a minute): the library's own CUDA events
+        # around its integration launches (mixed: the cluster kernel and the assembly), the
+        # potential tables and digit images outside them
+        eng = api.Engine(wl, path, "sp4")
+        _, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+        torch.cuda.synchronize()
+        st = eng.stats()
+        ms = st["ms_integrate"]
+        etas[path] = eta.cpu().numpy()[0]
+        out[path] = {"value": len(wl.theta0) / (ms / 1e3), "unit": "angles/s", "ms": ms,
+                     "ms_tables": st["ms_potential"], "ctas_per_angle": st["ctas_per_pair"],
+                     "rhst_per_curve": st["rhst_total"]}
+        eng.close()
+    out["mixed_vs_fp64_curve_error"] = curve_error(etas["mixed"], etas["fp64"])
+    out["speedup_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["workload"] = (f"121 beams (hexagonal shell), {wl.n_steps} slices of "
+                       f"{-wl.z_e / wl.n_steps:.3f} A, 60 angles 0.5..6.4 deg, sp4")
+    out["_eta_fp64"] = etas["fp64"]
+    return out
+
+
+def run_config2(n_sets: int = 512, slices: int = 0, eta_121_fp64=None, oracle_angles=(7, 41)):
+    """The batching + precision recipe at its stated size: 512 parameter sets (surface z of the
+    61-beam structure perturbed by N(0, 0.3^2) A, seeds 3000 + k), beam counts 31 / 61 / 121 round
+    robin, 60 angles each, 2000 slices, all on the mixed path in one batch: the three beam
+    classes as three jobs, their sets in chunks whose digit images fit the image budget, every
+    chunk's image builds and launches in one captured launch sequence. The timed run is the
+    batch's eager run (the same kernels the graph replays; the graph itself is captured during
+    it without running). Per-curve errors: every curve of the first set of each class against
+    the FP64 GPU path (all 60 angles), and two sampled angles of those sets against the oracle."""
+    import torch
+    from oracle.curve import curve_error, rocking_curve_parallel
+    from paper_2306_00271_gb300 import api
+    sets = W.batch_sets(n_sets)
+    L = slices or 2000
+    classes = {}
+    for s_ in sets:
+        classes.setdefault(s_.beams.shape[0], []).append(s_)
+    batch = api.Batch()
+    jobs = {}
+    for n in sorted(classes):
+        members = classes[n]
+        wl = members[0].with_steps(L)
+        eng = api.Engine(wl, "mixed", "sp4")
+        eng.set_image_budget(96 << 30)
+        eng.set_structures(np.stack([m.atoms for m in members]))
+        rho, eta = batch.add(eng, wl.theta0, wl.theta1)
+        jobs[n] = (eng, wl, members, eta)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t = time.perf_counter()
+    ev0.record()
+    batch.run()
+    ev1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    ms = ev0.elapsed_time(ev1)
+    st = batch.stats()
+    n_angles = sum(len(j[2]) * len(j[1].theta0) for j in jobs.values())
+    per_class = {}
+    for n, (eng, wl, members, eta) in jobs.items():
+        e_mixed = eta[0].cpu().numpy()
+        if n == 121 and eta_121_fp64 is not None and L == 2000:
+            e_ref = eta_121_fp64
+        else:
+            ref = api.Engine(members[0].with_steps(L), "fp64", "sp4")
+            _, e_ref = ref.rocking_curve(wl.theta0, wl.theta1)
+            e_ref = e_ref.cpu().numpy()[0]
+            ref.close()
+        rec = {"sets": len(members), "curve_error_vs_fp64_gpu_set0": curve_error(e_mixed, e_ref)}
+        if oracle_angles:
+            _, eta_o, _, _ = rocking_curve_parallel(members[0].with_steps(L), "sp4",
+                                                    angles=list(oracle_angles),
+                                                    processes=len(oracle_angles))
+            rec["error_vs_oracle_set0_sampled_angles"] = curve_error(
+                e_mixed[list(oracle_angles)], eta_o)
+            rec["oracle_angles"] = list(oracle_angles)
+        per_class[str(n)] = rec
+    out = {"value": n_angles / (ms / 1e3), "unit": "angles/s", "ms": ms, "wall_s": wall,
+           "sets": n_sets, "angles": n_angles, "slices": L, "path": "mixed",
+           "set_chunks": st["set_chunks"], "launches": st["kernels_launched"],
+           "per_class": per_class,
+           "note": "timed run = the batch's eager run; errors: eacc-style curve error, FP64 GPU "
+                   "path on all 60 angles of each class's first set, oracle on two angles"}
+    batch.close()
+    for j in jobs.values():
+        j[0].close()
     return out
 
 
@@ -384,6 +493,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload lines")
+    ap.add_argument("--no-config2", action="store_true",
+                    help="skip the 512-set batching + precision recipe")
+    ap.add_argument("--config2-sets", type=int, default=512,
+                    help="parameter sets of the batching recipe (512 = its stated size)")
     ap.add_argument("--column-split", default="auto", choices=["auto", "on", "off"],
                     help="mixed path: two CTAs per angle (auto: when the angles fit on half "
                          "the SMs)")
@@ -481,6 +594,12 @@ def main():
                                                      args.slices, path="mixed")
     if not args.no_batch:
         out["batches"] = run_batches(args.slices)
+        wide = run_wide_121(args.slices)
+        eta_ref = wide.pop("_eta_fp64")
+        out["wide_121"] = wide
+        if not args.no_config2:
+            out["config2_full"] = run_config2(args.config2_sets, args.slices,
+                                              eta_121_fp64=eta_ref)
         out["large_n255_sample"] = run_large_sample()
         out["rheed_row_latency"] = rheed_row_latency()
     out["paper_context"] = PAPER_CONTEXT
