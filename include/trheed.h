@@ -129,7 +129,7 @@ typedef struct trh_stats {
                              (trh_set_column_split), else 0                                    */
   int ctas_per_pair;      /* CTAs (one thread-block cluster) that integrated each pair in the
                              last call: 1 or 2 (N <= 64), ceil(N / 32) on the mixed path for
-                             N > 64                                                            */
+                             64 < N <= 128, ceil(N / 16) for 128 < N <= 256                   */
   int set_chunks;         /* mixed path: chunks of parameter sets the last call ran in (the
                              sets' digit images are built for one chunk at a time, at most
                              40 GiB of them; 1 when every set fits)                            */
@@ -139,8 +139,10 @@ typedef struct trh_stats {
  * its arrays afterwards), allocates device tables for one parameter set (the default structure
  * p->atoms, p->dw) and builds the host-side geometry (reciprocal rods, difference map U_jk ->
  * u_{g_j - g_k}, kick positions of the integrator).
- * Errors: TRH_EINVAL (see field comments), TRH_EUNSUPPORTED (N > 256 on the FP64 path, N > 64
- * on the mixed path, RK4 or the conventional method on the mixed path), TRH_ENOMEM, TRH_ECUDA.
+ * Errors: TRH_EINVAL (see field comments), TRH_EUNSUPPORTED (N > 256 on either path; on the
+ * mixed path above 128 beams a beam set whose grid of differences (m1_j - m1_k, m2_j - m2_k)
+ * has a bounding box of more than 1536 entries, or a device that cannot hold a cluster of
+ * ceil(N / 16) CTAs; RK4 or the conventional method on the mixed path), TRH_ENOMEM, TRH_ECUDA.
  * On error *out is NULL. */
 int trh_create(trh_ctx** out, const trh_problem* p);
 

@@ -121,6 +121,11 @@ struct trh_ctx {
                                   // mixed cluster kernel (N > 64)
   DevBuf<float> d_zg;             // mixed path, N > 64: RHST gather buffer
   DevBuf<int> d_cst;              // mixed path, N > 64: status of each CTA of each pair
+  // mixed path, N > 128: the difference grid (G entries; entry (j, k) at bj[j] - bk[k], gmap:
+  // its index into the M distinct differences or -1) and the RHST's eliminated-matrix buffer
+  int G = 0;
+  DevBuf<int> d_gmap, d_bj, d_bk;
+  DevBuf<float2> d_tg;
   int split_mode = TRH_SPLIT_AUTO;  // mixed path: two CTAs per pair (trh_set_column_split)
   std::vector<int> h_status;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -197,8 +202,8 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
     return fail(TRH_EUNSUPPORTED, "mixed path is not built in this library");
   if (p->precision == TRH_FP64 && p->n_beams > trh::kMaxBeamsWide)
     return fail(TRH_EUNSUPPORTED, "FP64 path supports N <= %d", trh::kMaxBeamsWide);
-  if (p->precision == TRH_MIXED && p->n_beams > trh::kMaxBeamsMixedWide)
-    return fail(TRH_EUNSUPPORTED, "mixed path supports N <= %d", trh::kMaxBeamsMixedWide);
+  if (p->precision == TRH_MIXED && p->n_beams > trh::kMaxBeamsMixedXwide)
+    return fail(TRH_EUNSUPPORTED, "mixed path supports N <= %d", trh::kMaxBeamsMixedXwide);
   const double det = p->a1[0] * p->a2[1] - p->a1[1] * p->a2[0];
   if (!(std::fabs(det) > 0)) return fail(TRH_EINVAL, "lattice vectors are parallel");
   for (int a = 0; a < p->n_atoms; ++a) {
@@ -243,6 +248,37 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
       return fail(TRH_EINVAL, "beam %d duplicates another", dup);
     }
     c->gdiff.assign(gd.begin(), gd.begin() + 2 * (size_t)c->M);
+  }
+  // mixed path above 128 beams: the grid of beam differences (m1_j - m1_k, m2_j - m2_k) over
+  // its bounding box, row keys bj and column keys bk with entry (j, k) at bj[j] - bk[k]
+  std::vector<int> gmap, bjv, bkv;
+  if (c->precision == TRH_MIXED && c->N > trh::kMaxBeamsMixedWide) {
+    int lo1 = p->beams[0], hi1 = p->beams[0], lo2 = p->beams[1], hi2 = p->beams[1];
+    for (int j = 1; j < c->N; ++j) {
+      lo1 = std::min(lo1, p->beams[2 * j]);
+      hi1 = std::max(hi1, p->beams[2 * j]);
+      lo2 = std::min(lo2, p->beams[2 * j + 1]);
+      hi2 = std::max(hi2, p->beams[2 * j + 1]);
+    }
+    const long long w1 = 2LL * (hi1 - lo1) + 1, w2 = 2LL * (hi2 - lo2) + 1;
+    if (w1 * w2 > trh::kMaxDigitGrid) {
+      delete c;
+      return fail(TRH_EUNSUPPORTED,
+                  "mixed path above %d beams: the beam set's difference grid has %lld entries, "
+                  "at most %d fit in shared memory",
+                  trh::kMaxBeamsMixedWide, w1 * w2, trh::kMaxDigitGrid);
+    }
+    c->G = (int)(w1 * w2);
+    const int off = (lo1 - hi1) * (int)w2 + (lo2 - hi2);  // key of the smallest difference
+    bjv.resize(c->N);
+    bkv.resize(c->N);
+    for (int j = 0; j < c->N; ++j) {
+      bkv[j] = p->beams[2 * j] * (int)w2 + p->beams[2 * j + 1];
+      bjv[j] = bkv[j] - off;
+    }
+    gmap.assign(c->G, -1);
+    for (int j = 0; j < c->N; ++j)
+      for (int k = 0; k < c->N; ++k) gmap[bjv[j] - bkv[k]] = c->lmap[(size_t)j * c->N + k];
   }
   // kick positions (trh::node_position)
   trh::bab_scheme(c->integrator, &c->scheme);
@@ -289,6 +325,19 @@ int trh_create(trh_ctx** out, const trh_problem* p) {
   TRY(cudaMemcpy(c->d_sf.p, c->sf.data(), c->sf.size() * 8, cudaMemcpyHostToDevice));
   TRY(cudaMemcpy(c->d_species.p, c->species.data(), c->species.size() * 4,
                  cudaMemcpyHostToDevice));
+  if (c->G > 0) {
+    TRY(c->d_gmap.ensure(c->G));
+    TRY(c->d_bj.ensure(c->N));
+    TRY(c->d_bk.ensure(c->N));
+    TRY(cudaMemcpy(c->d_gmap.p, gmap.data(), gmap.size() * 4, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(c->d_bj.p, bjv.data(), bjv.size() * 4, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(c->d_bk.p, bkv.data(), bkv.size() * 4, cudaMemcpyHostToDevice));
+    if (trh::mixed_xwide_max_clusters((c->N + 15) / 16) < 1) {
+      rc = fail(TRH_EUNSUPPORTED, "mixed path: clusters of %d CTAs cannot be resident on this "
+                "device", (c->N + 15) / 16);
+      goto failed;
+    }
+  }
 #undef TRY
   rc = upload_sets(c);
   if (rc != TRH_OK) goto failed;
@@ -370,7 +419,8 @@ constexpr size_t kDefaultImageBudget = size_t(40) << 30;
 
 static size_t mixed_image_bytes_per_set(const trh_ctx* c) {
   const size_t per_node =
-      c->N > trh::kMaxBeamsMixed
+      c->N > trh::kMaxBeamsMixedWide ? (size_t)c->G * 16
+      : c->N > trh::kMaxBeamsMixed
           ? trh::mixed_wide_image_bytes_per_node(trh::mixed_wide_k_slices(c->N))
           : trh::mixed_image_bytes_per_node((2 * c->N + 15) / 16);
   return per_node * (size_t)c->n_nodes;
@@ -404,7 +454,18 @@ static int alloc_images(trh_ctx* c, int ns) {
 static int launch_images(trh_ctx* c, int s0, int ns, cudaStream_t st, int* launched) {
   const int ks = (2 * c->N + 15) / 16;
   const double2* u = c->d_u.p + (size_t)s0 * c->n_nodes * c->M;
-  if (c->N > trh::kMaxBeamsMixed) {
+  if (c->N > trh::kMaxBeamsMixedWide) {
+    trh::DigitGridParams dp{};
+    dp.u = u;
+    dp.gmap = c->d_gmap.p;
+    dp.dtab = reinterpret_cast<uint4*>(c->d_img.p);
+    dp.scale = c->d_scale.p;
+    dp.M = c->M;
+    dp.G = c->G;
+    dp.n_nodes = c->n_nodes;
+    dp.n_sets = ns;
+    TRH_CUDA(trh::launch_digit_grid(dp, st, launched));
+  } else if (c->N > trh::kMaxBeamsMixed) {
     trh::MixedWideImageParams mp{};
     mp.u = u;
     mp.lmap = c->d_lmap.p;
@@ -539,8 +600,9 @@ static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParam
   mp.n_sets = c->n_sets;
   mp.L = c->L;
   mp.n_mma = (c->N + 15) / 16 * 16;
-  mp.k_slices = c->N > trh::kMaxBeamsMixed ? trh::mixed_wide_k_slices(c->N)
-                                           : (2 * c->N + 15) / 16;
+  mp.k_slices = c->N > trh::kMaxBeamsMixedWide ? trh::mixed_xwide_k_slices(c->N)
+                : c->N > trh::kMaxBeamsMixed    ? trh::mixed_wide_k_slices(c->N)
+                                                : (2 * c->N + 15) / 16;
   mp.h = c->h;
   mp.threshold = c->threshold;
   const int sc = c->scheme.s;
@@ -556,21 +618,99 @@ static trh::MixedParams mixed_params(const trh_ctx* c, const trh::IntegrateParam
   return mp;
 }
 
+// CTAs per (set, angle) pair of the mixed path: one or two for N <= 64 (column split), a cluster
+// of ceil(N / 32) for 64 < N <= 128 and of ceil(N / 16) for 128 < N <= 256.
+static int mixed_ctas(const trh_ctx* c, bool split) {
+  if (c->N > trh::kMaxBeamsMixedWide) return (c->N + 15) / 16;
+  if (c->N > trh::kMaxBeamsMixed) return (c->N + 31) / 32;
+  return split ? 2 : 1;
+}
+
+// Device scratch the cluster kernels (N > 64) keep per (set, angle) pair of a launch: the final
+// state for the assembly, the RHST gather buffer and (N > 128) the eliminated matrix.
+static size_t mixed_pair_scratch_bytes(const trh_ctx* c) {
+  if (c->N <= trh::kMaxBeamsMixed) return 0;
+  const size_t N = (size_t)c->N;
+  size_t b = 2 * N * N * sizeof(double2) + 4 * N * 2 * N * sizeof(float);
+  if (c->N > trh::kMaxBeamsMixedWide) b += N * N * sizeof(float2);
+  return b;
+}
+constexpr size_t kPairScratchBudget = size_t(8) << 30;
+
+// Scratch of the cluster kernels for `lp` pairs at once; a buffer that moves invalidates batch
+// plans, which hold the pointers.
+static int ensure_pair_scratch(trh_ctx* c, size_t lp) {
+  if (c->N <= trh::kMaxBeamsMixed) return TRH_OK;
+  const size_t N = (size_t)c->N;
+  const void* old[4] = {c->d_wide.p, c->d_zg.p, c->d_cst.p, c->d_tg.p};
+  TRH_CUDA(c->d_wide.ensure(lp * 2 * N * N));
+  TRH_CUDA(c->d_zg.ensure(lp * 4 * N * 2 * N));
+  TRH_CUDA(c->d_cst.ensure(lp * mixed_ctas(c, false)));
+  if (c->N > trh::kMaxBeamsMixedWide) TRH_CUDA(c->d_tg.ensure(lp * N * N));
+  if (old[0] != c->d_wide.p || old[1] != c->d_zg.p || old[2] != c->d_cst.p ||
+      old[3] != c->d_tg.p)
+    c->generation++;
+  return TRH_OK;
+}
+
+// Parameters of one cluster launch of the mixed path (N > 64) over sets s0 .. s0 + ns - 1. For
+// 64 < N <= 128 the fields of MixedWideParams are filled and R stays 0.
+static trh::MixedXwideParams cluster_params(const trh_ctx* c, const trh::MixedParams& mp, int s0,
+                                            int ns) {
+  trh::MixedXwideParams xp{};
+  xp.m = mp;
+  xp.m.set0 = s0;
+  xp.m.img_set0 = s0;
+  xp.m.n_sets = ns;
+  xp.scale = c->d_scale.p;
+  xp.fstate = c->d_wide.p;
+  xp.zg = c->d_zg.p;
+  xp.cta_status = c->d_cst.p;
+  xp.n_cta = mixed_ctas(c, false);
+  if (c->N > trh::kMaxBeamsMixedWide) {
+    xp.dtab = reinterpret_cast<const uint4*>(c->d_img.p);
+    xp.bj = c->d_bj.p;
+    xp.bk = c->d_bk.p;
+    xp.G = c->G;
+    xp.R = (2 * c->N + 127) / 128;
+    xp.tg = c->d_tg.p;
+  }
+  return xp;
+}
+
+static cudaError_t launch_cluster(const trh::MixedXwideParams& xp, cudaStream_t st,
+                                  int* launched) {
+  if (xp.R > 0) return trh::launch_integrate_mixed_xwide(xp, st, launched);
+  trh::MixedWideParams wp{};
+  wp.m = xp.m;
+  wp.scale = xp.scale;
+  wp.fstate = xp.fstate;
+  wp.zg = xp.zg;
+  wp.cta_status = xp.cta_status;
+  wp.n_cta = xp.n_cta;
+  return trh::launch_integrate_mixed_wide(wp, st, launched);
+}
+
 // The mixed path over every set of the call, in chunks of sets whose digit images fit the
-// budget: N <= 64 on integrate_mixed.cu (one or two CTAs per pair), 64 < N <= 128 on the cluster
-// kernel of integrate_mixed_wide.cu followed by the binary64 assembly.
+// budget (and, for N > 128, whose per-pair scratch stays within 8 GiB): N <= 64 on
+// integrate_mixed.cu (one or two CTAs per pair), 64 < N <= 128 on the cluster kernel of
+// integrate_mixed_wide.cu and 128 < N <= 256 on that of integrate_mixed_xwide.cu, each followed
+// by the binary64 assembly.
 static int run_mixed(trh_ctx* c, const trh::IntegrateParams& ip, int n_angles, bool split,
                      cudaStream_t st, int* launched, int* chunks, int* ctas) {
-  const int cs = mixed_chunk_sets(c);
+  int cs = mixed_chunk_sets(c);
   const bool wide = c->N > trh::kMaxBeamsMixed;
-  const int n_cta = wide ? (c->N + 31) / 32 : (split ? 2 : 1);
+  const bool xwide = c->N > trh::kMaxBeamsMixedWide;
+  if (xwide) {
+    const size_t per_set = (size_t)n_angles * mixed_pair_scratch_bytes(c);
+    cs = (int)std::max<size_t>(1, std::min<size_t>(cs, kPairScratchBudget / per_set));
+  }
+  const int n_cta = mixed_ctas(c, split);
   *ctas = n_cta;
   *chunks = 0;
   if (wide) {
-    const size_t lp = (size_t)cs * n_angles, N = (size_t)c->N;
-    TRH_CUDA(c->d_wide.ensure(lp * 2 * N * N));
-    TRH_CUDA(c->d_zg.ensure(lp * 4 * N * 2 * N));
-    TRH_CUDA(c->d_cst.ensure(lp * n_cta));
+    const int rc = ensure_pair_scratch(c, (size_t)cs * n_angles);
+    if (rc != TRH_OK) return rc;
   }
   for (int s0 = 0; s0 < c->n_sets; s0 += cs) {
     const int ns = std::min(cs, c->n_sets - s0);
@@ -583,14 +723,7 @@ static int run_mixed(trh_ctx* c, const trh::IntegrateParams& ip, int n_angles, b
     if (!wide) {
       TRH_CUDA(trh::launch_integrate_mixed(mp, split, st, launched));
     } else {
-      trh::MixedWideParams wp{};
-      wp.m = mp;
-      wp.scale = c->d_scale.p;
-      wp.fstate = c->d_wide.p;
-      wp.zg = c->d_zg.p;
-      wp.cta_status = c->d_cst.p;
-      wp.n_cta = n_cta;
-      TRH_CUDA(trh::launch_integrate_mixed_wide(wp, st, launched));
+      TRH_CUDA(launch_cluster(cluster_params(c, mp, s0, ns), st, launched));
       trh::IntegrateParams ipc = ip;
       ipc.n_sets = ns;
       TRH_CUDA(trh::launch_assemble_wide(ipc, s0, c->d_wide.p, c->d_cst.p, n_cta, st, launched));
@@ -1241,7 +1374,14 @@ void trh_destroy(trh_ctx* c) {
   c->d_lmap.release();
   c->d_status.release();
   c->d_img.release();
+  c->d_scale.release();
   c->d_wide.release();
+  c->d_zg.release();
+  c->d_cst.release();
+  c->d_tg.release();
+  c->d_gmap.release();
+  c->d_bj.release();
+  c->d_bk.release();
   c->d_bulk_u.release();
   c->d_bulk_F.release();
   c->d_xbulk.release();
@@ -1305,9 +1445,9 @@ struct trh_batch {
   std::vector<Chunk> chunks;
   std::vector<trh::IntegrateParams> params;
   std::vector<trh::MixedParams> mparams;       // [chunk][job]
-  // launches of mixed jobs with 64 < N <= 128 (a cluster kernel and the assembly each), in chunk
+  // launches of mixed jobs with N > 64 (a cluster kernel and the assembly each), in chunk
   // order, with their chunk and job
-  std::vector<trh::MixedWideParams> wparams;
+  std::vector<trh::MixedXwideParams> wparams;
   std::vector<int> wchunk;
   std::vector<size_t> wjob;
   DevBuf<trh::IntegrateParams> d_params;
@@ -1365,7 +1505,7 @@ static int batch_image_chunks(const trh_batch* b) {
 // Work lists, job parameters and scratch for the current jobs and tables. FP64 items run in
 // two persistent launches (N <= 64; wide and RK4); the mixed jobs' sets are split into chunks
 // (batch_image_chunks) and each chunk runs one persistent launch of its N <= 64 items and one
-// cluster launch (plus assembly) per job with 64 < N <= 128, after its images are built (in the
+// cluster launch (plus assembly) per job with N > 64, after its images are built (in the
 // launch sequence when there is more than one chunk).
 static int batch_prepare(trh_batch* b, cudaStream_t st) {
   b->drop_graph();
@@ -1466,10 +1606,9 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
       b->jobs[j].generation = c->generation;
     }
     if (c->N > trh::kMaxBeamsMixed) {
-      const size_t lp = (size_t)ns_max[j] * b->jobs[j].n_angles, N = (size_t)c->N;
-      TRH_CUDA(c->d_wide.ensure(lp * 2 * N * N));
-      TRH_CUDA(c->d_zg.ensure(lp * 4 * N * 2 * N));
-      TRH_CUDA(c->d_cst.ensure(lp * ((c->N + 31) / 32)));
+      const int rc = ensure_pair_scratch(c, (size_t)ns_max[j] * b->jobs[j].n_angles);
+      if (rc != TRH_OK) return rc;
+      b->jobs[j].generation = c->generation;
     }
   }
   for (int k = 0; k < K; ++k) {
@@ -1482,16 +1621,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
       if (c->precision != TRH_MIXED || ch.ns[j] == 0) continue;
       mp.img_set0 = ch.s0[j];
       if (c->N > trh::kMaxBeamsMixed) {
-        trh::MixedWideParams wp{};
-        wp.m = mp;
-        wp.m.set0 = ch.s0[j];
-        wp.m.n_sets = ch.ns[j];
-        wp.scale = c->d_scale.p;
-        wp.fstate = c->d_wide.p;
-        wp.zg = c->d_zg.p;
-        wp.cta_status = c->d_cst.p;
-        wp.n_cta = (c->N + 31) / 32;
-        b->wparams.push_back(wp);
+        b->wparams.push_back(cluster_params(c, mp, ch.s0[j], ch.ns[j]));
         b->wchunk.push_back(k);
         b->wjob.push_back(j);
         continue;
@@ -1537,7 +1667,7 @@ static int batch_prepare(trh_batch* b, cudaStream_t st) {
 
 // The batch's device work: counters reset, the two FP64 persistent launches, then chunk by
 // chunk the mixed jobs' images (when chunked), the persistent launch of the chunk's N <= 64
-// mixed items and the cluster launches (with their assembly) of its 64 < N <= 128 mixed jobs.
+// mixed items and the cluster launches (with their assembly) of its N > 64 mixed jobs.
 static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
   const size_t nj = b->jobs.size();
   TRH_CUDA(cudaMemsetAsync(b->d_counter.p, 0, (2 + b->chunks.size()) * sizeof(int), st));
@@ -1562,8 +1692,8 @@ static int batch_launch(trh_batch* b, cudaStream_t st, int* launched) {
                                                  b->d_items.p + ch.item_off, ch.n_items,
                                                  b->d_counter.p + 2 + k, ch.ctas, st, launched));
     for (; w < b->wparams.size() && b->wchunk[w] == (int)k; ++w) {
-      const trh::MixedWideParams& wp = b->wparams[w];
-      TRH_CUDA(trh::launch_integrate_mixed_wide(wp, st, launched));
+      const trh::MixedXwideParams& wp = b->wparams[w];
+      TRH_CUDA(launch_cluster(wp, st, launched));
       trh::IntegrateParams ipc = b->params[b->wjob[w]];
       ipc.n_sets = wp.m.n_sets;
       TRH_CUDA(trh::launch_assemble_wide(ipc, wp.m.set0, wp.fstate, wp.cta_status, wp.n_cta, st,

@@ -10,6 +10,9 @@ constexpr int kMaxBeamsFp64 = 64;    // FP64 path: state resident in shared memo
 constexpr int kMaxBeamsMixed = 64;   // mixed path, one cluster of <= 2 CTAs: one 128-row UMMA
                                      // tile holds [Re; Im] of N <= 64
 constexpr int kMaxBeamsMixedWide = 128;  // mixed path with two row tiles and ceil(N / 32) CTAs
+constexpr int kMaxBeamsMixedXwide = 256;  // mixed path with up to four row tiles and
+                                          // ceil(N / 16) CTAs (a non-portable cluster size)
+constexpr int kMaxDigitGrid = 1536;  // entries of the difference grid of the N > 128 mixed path
 constexpr int kMaxBeamsWide = 256;   // FP64 path with the state in global memory (64 < N <= 256)
 
 // Integration methods of the kernels (IntegrateParams::method).
@@ -137,6 +140,35 @@ struct MixedWideImageParams {
   int k_slices;                // ceil(2N / 16)
 };
 
+// Mixed path for 128 < N <= 256 (integrate_mixed_xwide.cu): a cluster of n_cta = ceil(N / 16)
+// CTAs per pair, each owning 16 columns of Q and P. Instead of a materialised image per node, each
+// node has a digit table on the grid of beam differences: entry idx(j, k) = bj[j] - bk[k] holds
+// the four BF16 digits of Re and Im of u_{g_j - g_k} (zero where the difference is no beam
+// difference), and the CTAs build the real-ified tensor-core tiles from it in shared memory.
+struct MixedXwideParams {
+  MixedParams m;               // scheme coefficients, angles, outputs, p0, N, n_nodes, L, k_slices
+  const uint4* dtab;           // [sets][n_nodes][G] digit tables (from m.img_set0)
+  const float* scale;          // [sets][n_nodes] the power-of-two scale of each node's table
+  const int* bj;               // [N] row keys of the difference grid
+  const int* bk;               // [N] column keys
+  int G;                       // entries per node table (<= kMaxDigitGrid)
+  int R;                       // 128-row tiles of the real-ified product: ceil(2N / 128)
+  // per-launch scratch, indexed by the launch's own pair (set - m.set0) * n_angles + angle:
+  double2* fstate;             // [pairs][2][N][N] final Q, P in binary64 for the assembly kernel
+  float* zg;                   // [pairs][4][N][2N] RHST gather buffer: Qh, Ql, Ph, Pl by column
+  float2* tg;                  // [pairs][N][N] RHST: the eliminated matrix, by column
+  int* cta_status;             // [pairs][n_cta]
+  int n_cta;
+};
+
+struct DigitGridParams {
+  const double2* u;            // FP64 table [n_sets][n_nodes][M]
+  const int* gmap;             // [G] index into the M distinct differences, or -1
+  uint4* dtab;                 // [n_sets][n_nodes][G]
+  float* scale;                // [n_sets][n_nodes]
+  int M, G, n_nodes, n_sets;
+};
+
 // Reverse sweep of the FP64 path (adjoint_fp64.cu): gradients of the specular intensity with
 // respect to atomic z coordinates and Debye-Waller factors. Pair = (set, angle), pair-major.
 struct GradParams {
@@ -258,6 +290,14 @@ cudaError_t launch_umma_images_wide(const MixedWideImageParams& p, cudaStream_t 
                                     int* n_launched);
 cudaError_t launch_integrate_mixed_wide(const MixedWideParams& p, cudaStream_t st,
                                         int* n_launched);
+// Mixed path for 128 < N <= 256: the per-node digit tables and the cluster kernel (the assembly
+// is launch_assemble_wide's). K-slices: ceil(2N / 16) rounded up to an even count.
+inline int mixed_xwide_k_slices(int N) { return ((2 * N + 15) / 16 + 1) / 2 * 2; }
+cudaError_t launch_digit_grid(const DigitGridParams& p, cudaStream_t st, int* n_launched);
+cudaError_t launch_integrate_mixed_xwide(const MixedXwideParams& p, cudaStream_t st,
+                                         int* n_launched);
+// Clusters of n_cta CTAs of the xwide kernel that can be resident at once (0: cannot launch).
+int mixed_xwide_max_clusters(int n_cta);
 // rho, eta, status of the pairs of sets set0 .. set0 + n_sets - 1 of `p` (p.n_sets of them) from
 // [Q; P] in `state` ([launch pair][2][N][N], launch pair = (set - set0) * n_angles + angle); a
 // pair whose cta_status[launch pair][0 .. n_cta-1] holds a failure gets NaN outputs and that

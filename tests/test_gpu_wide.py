@@ -67,7 +67,7 @@ def test_limits(api):
     with pytest.raises(api.TrhError) as e:
         api.Engine(wl, "fp64", "sp4")
     assert e.value.code == api.TRH_EUNSUPPORTED
-    wl = W.tiny(n_beams=129, seed=1, n_steps=4)
+    wl = W.tiny(n_beams=257, seed=1, n_steps=4)
     with pytest.raises(api.TrhError) as e:
         api.Engine(wl, "mixed", "sp4")
     assert e.value.code == api.TRH_EUNSUPPORTED
