@@ -154,10 +154,9 @@ def rheed_row_latency():
 
 
 def run_large_sample(slices: int = 30):
-    """The 255-beam recipe (one structure, 120 angles) on the FP64 path at a few slices: time per
-    slice, extrapolated to its 3000 slices and 64 structures (FP64 only; the mixed path and the
-    reverse sweep take N <= 64)."""
-    import torch
+    """The FP64 wide kernel on the 255-beam recipe (one structure, 120 angles) at a few slices:
+    its measured time per slice-angle, the FP64 reference rate beside the mixed path's full-size
+    line (at 3000 slices one FP64 curve takes about ten minutes)."""
     from paper_2306_00271_gb300 import api
     wl = W.large_n255(1)[0].with_steps(slices)
     eng = api.Engine(wl, "fp64", "sp4")
@@ -165,11 +164,48 @@ def run_large_sample(slices: int = 30):
     ms = eng.stats()["ms_integrate"]
     tile = eng.stats()["wide_tile"]
     eng.close()
-    per_slice = ms / slices
-    return {"value": 120 / (ms / 1e3), "unit": "angles/s", "slices": slices, "ms": ms,
-            "wide_tile": tile,
-            "extrapolated_full_forward_s": per_slice * 3000 * 64 / 1e3,
-            "note": "FP64 wide kernel, 120 angles on 120 SMs; full recipe = 3000 slices x 64 sets"}
+    return {"value": 120 * slices / (ms / 1e3), "unit": "angle-slices/s", "slices": slices,
+            "ms": ms, "wide_tile": tile,
+            "note": "FP64 wide kernel, 120 angles on 120 SMs, measured at this slice count"}
+
+
+def run_large(n_sets: int = 2, slices: int = 0):
+    """The 255-beam recipe (square 5.4 A cell, 3000 slices of 0.01 A, 120 angles 0.2..6.2 deg)
+    on the mixed path for its first n_sets structures in one call: angles/s over the whole call,
+    and the error of the first structure's curve against the oracle at the sampled angles of
+    tests/golden/large_n255_sp4_sampled.npz (written by tests/golden/make_golden.py, which calls
+    only the oracle)."""
+    import torch
+    from oracle.curve import curve_error
+    from paper_2306_00271_gb300 import api
+    sets = W.large_n255(n_sets)
+    wl = sets[0].with_steps(slices) if slices else sets[0]
+    eng = api.Engine(wl, "mixed", "sp4")
+    eng.set_structures(np.stack([s.atoms for s in sets]))
+    eng.rocking_curve(wl.theta0[:1], wl.theta1[:1])  # tables and images outside the timing
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    st = eng.stats()
+    eng.close()
+    n_ang = n_sets * len(wl.theta0)
+    out = {"value": n_ang / (st["ms_integrate"] / 1e3), "unit": "angles/s",
+           "ms_integrate": st["ms_integrate"], "wall_s": wall, "sets": n_sets,
+           "angles": n_ang, "slices": wl.n_steps, "ctas_per_angle": st["ctas_per_pair"],
+           "rhst_per_angle": st["rhst_total"] / n_ang,
+           "workload": "255 beams (square 5.4 A disk), %d slices of %.3f A, 120 angles "
+                       "0.2..6.2 deg, sp4, mixed path, %d of the recipe's 64 structures" % (
+                           wl.n_steps, -wl.z_e / wl.n_steps, n_sets)}
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "large_n255_sp4_sampled.npz")
+    if not slices and os.path.exists(gold):
+        g = np.load(gold)
+        e = eta.cpu().numpy()[0][g["angles"]]
+        out["curve_error_vs_oracle_sampled"] = curve_error(e, g["eta"])
+        out["oracle_angles"] = [int(a) for a in g["angles"]]
+    return out
 
 
 # DRAM bytes per kick node of the integration kernels, from one ncu capture each (dram__bytes_read
@@ -261,22 +297,31 @@ def run_ours(args):
         total_ms = D.max_over_ranks(total_ms)
         # end to end through the public API with host buffers: H2D of the step's inputs and
         # D2H of its outputs inside the timed region
+        # (asynchronous calls into pinned host buffers: the steps queue back to back and the
+        # host waits once, after the last; every step's copies are inside the timed region)
         atoms_h = np.ascontiguousarray(wl.atoms)
         dw_h = np.ascontiguousarray(wl.dw)
-        rho_h = np.empty((1, A, wl.n_beams), np.complex128)
-        eta_h = np.empty((1, A, wl.n_beams), np.float64)
-        e2e_steps = max(1, min(args.steps, 3))
+        rho_t = torch.empty((1, A, wl.n_beams), dtype=torch.complex128, pin_memory=True)
+        eta_t = torch.empty((1, A, wl.n_beams), dtype=torch.float64, pin_memory=True)
+        rho_h, eta_h = rho_t.numpy(), eta_t.numpy()
+        e2e_steps = max(10, args.steps)
+        eng.set_async(True)
         torch.cuda.synchronize()
         t = time.perf_counter()
         for _ in range(e2e_steps):
             eng.set_structures(atoms_h, dw_h)
             eng.rocking_curve_host(wl.theta0, wl.theta1, rho_h, eta_h)
+        torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t) / e2e_steps
+        e2e_bad = eng.stats()["n_bad"]
+        eng.set_async(False)
         results[path] = dict(ms_per_step=total_ms / args.steps, ms_integrate=float(np.mean(ms_int)),
                              ms_potential=float(np.mean(ms_pot)), launches=launches,
                              rhst_per_step=rhst / args.steps, clocks=clk, column_split=split,
                              value=ws * A * args.steps / (total_ms / 1e3),
-                             e2e=dict(value=ws * A / e2e_s, unit=UNIT,
+                             e2e=dict(value=ws * A / e2e_s, unit=UNIT, steps=e2e_steps,
+                                      n_bad=e2e_bad, mode="asynchronous calls, pinned host "
+                                      "buffers, one wait after the last step",
                                       h2d_bytes_per_step=int(atoms_h.nbytes + dw_h.nbytes
                                                              + 2 * A * 8),
                                       d2h_bytes_per_step=int(rho_h.nbytes + eta_h.nbytes)),
@@ -600,7 +645,8 @@ def main():
         if not args.no_config2:
             out["config2_full"] = run_config2(args.config2_sets, args.slices,
                                               eta_121_fp64=eta_ref)
-        out["large_n255_sample"] = run_large_sample()
+        out["large_n255"] = run_large(2, args.slices)
+        out["large_n255_fp64_sample"] = run_large_sample()
         out["rheed_row_latency"] = rheed_row_latency()
     out["paper_context"] = PAPER_CONTEXT
     if ws == 1 and not args.no_cpu:

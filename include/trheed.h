@@ -149,8 +149,10 @@ int trh_create(trh_ctx** out, const trh_problem* p);
 /* Replace the context's parameter sets: n_sets structures sharing the beam set, species table
  * and slab. `atoms` is [n_sets][n_atoms][3] and `dw` is [n_sets][n_atoms], host or device
  * memory (both on the same side); `dw` may be NULL (every set uses the problem's dw). Host
- * inputs are validated (z <= 0, dw >= 0); device inputs are copied as given (stream order on
- * the legacy default stream, synchronised before return). Builds nothing yet: the potential
+ * inputs are validated (z <= 0, dw >= 0); device inputs are copied as given. The copies are
+ * enqueued on the stream of the context's last call (the legacy default stream before the
+ * first), after that call's work, without synchronising; the next call's stream waits for them.
+ * A device input must therefore be ready in that stream's order. Builds nothing yet: the potential
  * tables are rebuilt by the next trh_rocking_curve (Section 3.4: one U(z) serves every angle
  * of a set), so calling this with unchanged data forces a rebuild.
  * Errors: TRH_EINVAL (n_sets < 1, z > 0, dw < 0), TRH_ENOMEM, TRH_ECUDA. */
@@ -210,6 +212,22 @@ int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* d
  * Errors: TRH_EINVAL (mode not one of the three). */
 enum trh_split_mode { TRH_SPLIT_AUTO = 0, TRH_SPLIT_OFF = 1, TRH_SPLIT_ON = 2 };
 int trh_set_column_split(trh_ctx* ctx, int mode);
+
+/* ---- asynchronous calls ------------------------------------------------------------------------
+ * Not a step of the method (the paper's program is synchronous): a host-side convenience. With
+ * on != 0, trh_rocking_curve returns as soon as its work is enqueued on `stream` instead of
+ * waiting for it to read the per-pair status words, so that back-to-back calls queue on the
+ * device without a host stall per call. Outputs in device memory, or in pinned host memory
+ * (copied with cudaMemcpyAsync), are ready in stream order; outputs in pageable host memory still
+ * make the call wait for its copies. The per-pair counters of trh_stats (rhst_total, n_bad,
+ * first_bad_*), and ms_potential and ms_integrate, belong to the last call and are completed by
+ * trh_query, which waits for that call's work; a failing pair is then reported only there
+ * (n_bad, first_bad_status, and trh_last_error()), not by the call's return code, which covers
+ * argument and enqueue errors. A later call replaces the counters of an earlier one that was not
+ * queried. on = 0 (the default) restores the synchronous behaviour: the call waits and returns
+ * the first failing pair's code. The gradient calls are synchronous in either mode.
+ * Errors: TRH_EINVAL (NULL context), TRH_ECUDA. */
+int trh_set_async(trh_ctx* ctx, int on);
 
 /* ---- device memory of the mixed path ---------------------------------------------------------
  * The mixed path multiplies by U(tau) on the tensor cores from fixed-point digit images of U at
@@ -307,7 +325,9 @@ int trh_batch_query(const trh_batch* batch, trh_stats* out);
 /* Free the batch (not its contexts). NULL is accepted. Synchronises the device. */
 void trh_batch_destroy(trh_batch* batch);
 
-/* Counters of the last call (see trh_stats). Errors: TRH_EINVAL (NULL arguments). */
+/* Counters of the last call (see trh_stats); after an asynchronous call (trh_set_async) this
+ * waits for that call's work and completes its per-pair counters. Errors: TRH_EINVAL (NULL
+ * arguments), TRH_ECUDA. */
 int trh_query(const trh_ctx* ctx, trh_stats* out);
 
 /* Static string naming a status code; never NULL. */

@@ -93,6 +93,7 @@ def load():
     lib.trh_set_bulk.argtypes = [vp, C.c_int, vp, vp, vp, C.c_double, C.c_int, C.c_int,
                                  C.c_double]
     lib.trh_set_column_split.argtypes = [vp, C.c_int]
+    lib.trh_set_async.argtypes = [vp, C.c_int]
     lib.trh_set_image_budget.argtypes = [vp, C.c_size_t]
     lib.trh_curve_jacobian.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     lib.trh_rfactor_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -103,7 +104,8 @@ def load():
     lib.trh_batch_destroy.argtypes = [vp]
     lib.trh_batch_destroy.restype = None
     for f in ("trh_create", "trh_set_structure", "trh_rocking_curve", "trh_query", "trh_set_fit",
-              "trh_curve_jacobian", "trh_rfactor_grad", "trh_set_bulk", "trh_set_column_split", "trh_set_image_budget",
+              "trh_curve_jacobian", "trh_rfactor_grad", "trh_set_bulk", "trh_set_column_split", "trh_set_async",
+              "trh_set_image_budget",
               "trh_batch_create",
               "trh_batch_add",
               "trh_batch_run", "trh_batch_query"):
@@ -278,6 +280,11 @@ class Engine:
         or two when the call's pairs fit on half the SMs ("auto", the default). Results are
         identical."""
         _check(self.lib.trh_set_column_split(self.ctx, SPLIT_MODES[mode]))
+
+    def set_async(self, on: bool = True):
+        """Calls return once their work is enqueued; stats() waits for the last call and
+        completes its per-pair counters (a failing pair shows there, not as an exception)."""
+        _check(self.lib.trh_set_async(self.ctx, 1 if on else 0))
 
     def set_image_budget(self, nbytes: int = 0):
         """Mixed path: device bytes of digit images kept at once (0: the default, 40 GiB); sets

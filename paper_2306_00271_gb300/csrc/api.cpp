@@ -127,6 +127,19 @@ struct trh_ctx {
   DevBuf<int> d_gmap, d_bj, d_bk;
   DevBuf<float2> d_tg;
   int split_mode = TRH_SPLIT_AUTO;  // mixed path: two CTAs per pair (trh_set_column_split)
+  // trh_set_async: calls return once their work is enqueued; the status words of the last call
+  // travel to pinned host memory behind its work (event ev_done) and trh_query reads them
+  bool async_mode = false, pending = false, pend_rebuilt = false;
+  int pend_angles = 0;
+  size_t pend_pairs = 0;
+  int* h_pinned = nullptr;
+  size_t pinned_n = 0;
+  cudaEvent_t ev_done = nullptr;
+  // structure uploads are ordered on the stream of the last call (last_stream) and the next
+  // call's stream waits for them (ev_upload)
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev_upload = nullptr;
+  bool upload_fence = false;
   std::vector<int> h_status;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   trh_stats stats{};
@@ -162,18 +175,35 @@ const char* trh_strerror(int status) {
 
 const char* trh_last_error(void) { return g_last_error.c_str(); }
 
-static int upload_sets(trh_ctx* c) {
-  TRH_CUDA(c->d_atoms.ensure((size_t)c->n_sets * c->n_atoms * 3));
-  TRH_CUDA(c->d_dw.ensure((size_t)c->n_sets * c->n_atoms));
-  TRH_CUDA(cudaMemcpy(c->d_atoms.p, c->atoms.data(), c->atoms.size() * sizeof(double),
-                      cudaMemcpyHostToDevice));
-  TRH_CUDA(cudaMemcpy(c->d_dw.p, c->dw.data(), c->dw.size() * sizeof(double),
-                      cudaMemcpyHostToDevice));
-  TRH_CUDA(c->d_u.ensure((size_t)c->n_sets * c->n_nodes * c->M));
-  TRH_CUDA(c->d_F.ensure((size_t)c->n_sets * c->M * 4 * c->n_atoms));
+// Structure uploads are enqueued on the stream of the last call that read the structure
+// (last_stream), after that call's work and without stalling the host; an event behind them
+// orders the next call's stream after them (order_uploads).
+static int fence_uploads(trh_ctx* c) {
+  if (!c->ev_upload) TRH_CUDA(cudaEventCreateWithFlags(&c->ev_upload, cudaEventDisableTiming));
+  TRH_CUDA(cudaEventRecord(c->ev_upload, c->last_stream));
+  c->upload_fence = true;
   c->tables_dirty = true;
   c->generation++;
   return TRH_OK;
+}
+
+static int order_uploads(trh_ctx* c, cudaStream_t st) {
+  if (c->upload_fence && st != c->last_stream) TRH_CUDA(cudaStreamWaitEvent(st, c->ev_upload, 0));
+  c->upload_fence = false;
+  c->last_stream = st;
+  return TRH_OK;
+}
+
+static int upload_sets(trh_ctx* c) {
+  TRH_CUDA(c->d_atoms.ensure((size_t)c->n_sets * c->n_atoms * 3));
+  TRH_CUDA(c->d_dw.ensure((size_t)c->n_sets * c->n_atoms));
+  TRH_CUDA(cudaMemcpyAsync(c->d_atoms.p, c->atoms.data(), c->atoms.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, c->last_stream));
+  TRH_CUDA(cudaMemcpyAsync(c->d_dw.p, c->dw.data(), c->dw.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, c->last_stream));
+  TRH_CUDA(c->d_u.ensure((size_t)c->n_sets * c->n_nodes * c->M));
+  TRH_CUDA(c->d_F.ensure((size_t)c->n_sets * c->M * 4 * c->n_atoms));
+  return fence_uploads(c);
 }
 
 int trh_create(trh_ctx** out, const trh_problem* p) {
@@ -359,21 +389,22 @@ int trh_set_structure(trh_ctx* c, int n_sets, const double* atoms, const double*
     if (dw && !is_device_ptr(dw)) return fail(TRH_EINVAL, "atoms and dw must be on one side");
     TRH_CUDA(c->d_atoms.ensure(na * 3));
     TRH_CUDA(c->d_dw.ensure(na));
-    TRH_CUDA(cudaMemcpy(c->d_atoms.p, atoms, na * 3 * sizeof(double), cudaMemcpyDeviceToDevice));
+    TRH_CUDA(cudaMemcpyAsync(c->d_atoms.p, atoms, na * 3 * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c->last_stream));
     if (dw) {
-      TRH_CUDA(cudaMemcpy(c->d_dw.p, dw, na * sizeof(double), cudaMemcpyDeviceToDevice));
+      TRH_CUDA(cudaMemcpyAsync(c->d_dw.p, dw, na * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->last_stream));
     } else {
-      std::vector<double> dwv(na);
+      std::vector<double> dwv(na);  // pageable: staged before the call returns
       for (size_t a = 0; a < na; ++a) dwv[a] = c->dw[a % c->n_atoms];
-      TRH_CUDA(cudaMemcpy(c->d_dw.p, dwv.data(), na * sizeof(double), cudaMemcpyHostToDevice));
+      TRH_CUDA(cudaMemcpyAsync(c->d_dw.p, dwv.data(), na * sizeof(double),
+                               cudaMemcpyHostToDevice, c->last_stream));
     }
     c->n_sets = n_sets;
     c->stats.n_sets = n_sets;
     TRH_CUDA(c->d_u.ensure((size_t)n_sets * c->n_nodes * c->M));
     TRH_CUDA(c->d_F.ensure((size_t)n_sets * c->M * 4 * c->n_atoms));
-    c->tables_dirty = true;
-    c->generation++;
-    return TRH_OK;
+    return fence_uploads(c);
   }
   for (size_t a = 0; a < na; ++a) {
     if (!(atoms[3 * a + 2] <= 0)) return fail(TRH_EINVAL, "atom %zu above the surface", a);
@@ -512,6 +543,8 @@ static int build_tables(trh_ctx* c, cudaStream_t st, int* launched, bool* rebuil
                         bool images = true) {
   *rebuilt = c->tables_dirty;
   if (!c->tables_dirty) return TRH_OK;
+  const int orc = order_uploads(c, st);
+  if (orc != TRH_OK) return orc;
   TRH_CUDA(cudaEventRecord(c->ev[0], st));
   trh::PotentialParams pp{};
   pp.g = c->d_g.p;
@@ -733,12 +766,13 @@ static int run_mixed(trh_ctx* c, const trh::IntegrateParams& ip, int n_angles, b
   return TRH_OK;
 }
 
-// Reads back the per-pair status words (the stream is synchronised) and fills the counters.
-static int collect_status(trh_ctx* c, int n_angles, size_t pairs, cudaStream_t st) {
-  c->h_status.resize(2 * pairs);
-  TRH_CUDA(cudaMemcpyAsync(c->h_status.data(), c->d_status.p, 2 * pairs * sizeof(int),
-                           cudaMemcpyDeviceToHost, st));
-  TRH_CUDA(cudaStreamSynchronize(st));
+static float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.f;
+}
+
+// Fills the per-pair counters from the status words h ([pairs] status, then [pairs] RHST counts).
+static void tally_status(trh_ctx* c, int n_angles, size_t pairs, const int* h) {
   trh_stats& S = c->stats;
   S.n_angles = n_angles;
   S.rhst_total = 0;
@@ -747,7 +781,7 @@ static int collect_status(trh_ctx* c, int n_angles, size_t pairs, cudaStream_t s
   S.first_bad_set = S.first_bad_angle = -1;
   S.first_bad_status = TRH_OK;
   for (size_t q = 0; q < pairs; ++q) {
-    const int stq = c->h_status[q], nr = c->h_status[pairs + q];
+    const int stq = h[q], nr = h[pairs + q];
     S.rhst_total += nr;
     if (nr > S.rhst_max) S.rhst_max = nr;
     if (stq != 0) {
@@ -759,6 +793,54 @@ static int collect_status(trh_ctx* c, int n_angles, size_t pairs, cudaStream_t s
       S.n_bad++;
     }
   }
+}
+
+// Reads back the per-pair status words (the stream is synchronised) and fills the counters.
+static int collect_status(trh_ctx* c, int n_angles, size_t pairs, cudaStream_t st) {
+  c->pending = false;
+  c->h_status.resize(2 * pairs);
+  TRH_CUDA(cudaMemcpyAsync(c->h_status.data(), c->d_status.p, 2 * pairs * sizeof(int),
+                           cudaMemcpyDeviceToHost, st));
+  TRH_CUDA(cudaStreamSynchronize(st));
+  tally_status(c, n_angles, pairs, c->h_status.data());
+  return TRH_OK;
+}
+
+// Asynchronous form: the status words go to pinned host memory behind the call's work and the
+// counters are filled by finish_pending (trh_query), which waits for that copy only.
+static int queue_status(trh_ctx* c, int n_angles, size_t pairs, cudaStream_t st) {
+  if (c->pinned_n < 2 * pairs) {
+    if (c->h_pinned) {
+      TRH_CUDA(cudaStreamSynchronize(st));  // an earlier call may still copy into the old one
+      cudaFreeHost(c->h_pinned);
+      c->h_pinned = nullptr;
+      c->pinned_n = 0;
+    }
+    TRH_CUDA(cudaMallocHost(&c->h_pinned, 2 * pairs * sizeof(int)));
+    c->pinned_n = 2 * pairs;
+  }
+  if (!c->ev_done) TRH_CUDA(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
+  TRH_CUDA(cudaMemcpyAsync(c->h_pinned, c->d_status.p, 2 * pairs * sizeof(int),
+                           cudaMemcpyDeviceToHost, st));
+  TRH_CUDA(cudaEventRecord(c->ev_done, st));
+  c->pending = true;
+  c->pend_angles = n_angles;
+  c->pend_pairs = pairs;
+  return TRH_OK;
+}
+
+static int bad_pairs_error(const trh_ctx* c);
+
+// Counters of a pending asynchronous call: waits for its status copy, then tallies; a failing
+// pair is reported through the counters and trh_last_error().
+static int finish_pending(trh_ctx* c) {
+  if (!c->pending) return TRH_OK;
+  c->pending = false;
+  TRH_CUDA(cudaEventSynchronize(c->ev_done));
+  tally_status(c, c->pend_angles, c->pend_pairs, c->h_pinned);
+  c->stats.ms_potential = c->pend_rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
+  c->stats.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
+  if (c->stats.n_bad) bad_pairs_error(c);
   return TRH_OK;
 }
 
@@ -766,11 +848,6 @@ static int bad_pairs_error(const trh_ctx* c) {
   const trh_stats& S = c->stats;
   return fail(S.first_bad_status, "%d (set, angle) pairs failed; first: set %d angle %d (%s)",
               S.n_bad, S.first_bad_set, S.first_bad_angle, trh_strerror(S.first_bad_status));
-}
-
-static float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
-  float ms = 0.f;
-  return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.f;
 }
 
 // Autotuner for the wide FP64 kernel's tile edge (64 or 32): times each candidate on a probe
@@ -818,6 +895,14 @@ static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* s
 int trh_set_image_budget(trh_ctx* c, size_t bytes) {
   if (!c) return fail(TRH_EINVAL, "ctx is NULL");
   c->img_budget = bytes > 0 ? bytes : kDefaultImageBudget;
+  return TRH_OK;
+}
+
+int trh_set_async(trh_ctx* c, int on) {
+  if (!c) return fail(TRH_EINVAL, "ctx is NULL");
+  const int rc = finish_pending(c);
+  if (rc != TRH_OK) return rc;
+  c->async_mode = on != 0;
   return TRH_OK;
 }
 
@@ -1036,12 +1121,22 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   if (eta_out && !dev_eta)
     TRH_CUDA(cudaMemcpyAsync(eta_out, eta, pairs * c->N * sizeof(double),
                              cudaMemcpyDeviceToHost, st));
-  rc = collect_status(c, n_angles, pairs, st);
-  if (rc != TRH_OK) return rc;
   trh_stats& S = c->stats;
+  if (c->async_mode) {
+    // no host wait: the counters that need the device (status words, RHST counts, event
+    // times) are completed by trh_query
+    rc = queue_status(c, n_angles, pairs, st);
+    if (rc != TRH_OK) return rc;
+    c->pend_rebuilt = rebuilt;
+    S.ms_potential = 0.0;
+    S.ms_integrate = 0.0;
+  } else {
+    rc = collect_status(c, n_angles, pairs, st);
+    if (rc != TRH_OK) return rc;
+    S.ms_potential = rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
+    S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
+  }
   S.kernels_launched = launched;
-  S.ms_potential = rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
-  S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
   S.ms_gradient = 0.0;
   S.wide_tile = tile;
   S.column_split = split ? 1 : 0;
@@ -1350,6 +1445,10 @@ int trh_rfactor_grad(trh_ctx* c, int n_angles, const double* theta0, const doubl
 
 int trh_query(const trh_ctx* c, trh_stats* out) {
   if (!c || !out) return fail(TRH_EINVAL, "bad arguments");
+  // the context was created mutable (trh_create); reading the counters of a pending
+  // asynchronous call completes them
+  const int rc = finish_pending(const_cast<trh_ctx*>(c));
+  if (rc != TRH_OK) return rc;
   *out = c->stats;
   return TRH_OK;
 }
@@ -1373,6 +1472,12 @@ void trh_destroy(trh_ctx* c) {
   c->d_species.release();
   c->d_lmap.release();
   c->d_status.release();
+  if (c->h_pinned) {
+    cudaDeviceSynchronize();  // a pending call may still copy its status words into it
+    cudaFreeHost(c->h_pinned);
+  }
+  if (c->ev_done) cudaEventDestroy(c->ev_done);
+  if (c->ev_upload) cudaEventDestroy(c->ev_upload);
   c->d_img.release();
   c->d_scale.release();
   c->d_wide.release();

@@ -4,6 +4,7 @@ Calls only ``oracle/`` (Algorithm 1, sp4, threshold 1000, FP64) on the seeded wo
 ``paper_2306_00271_gb300.workloads``; nothing here comes from the CUDA path.
 
     python tests/golden/make_golden.py            # writes tests/golden/trhepd_n61_sp4.npz
+    python tests/golden/make_golden.py large      # writes tests/golden/large_n255_sp4_sampled.npz
 """
 import os
 import sys
@@ -28,5 +29,22 @@ def main():
     print(f"wrote {out} in {time.time() - t:.1f}s; rhst per angle {n_rhst.min()}..{n_rhst.max()}")
 
 
+# sampled angles of the 255-beam recipe's first structure (of its 120 angles 0.2 .. 6.2 deg)
+LARGE_ANGLES = (10, 40, 70, 100)
+
+
+def large():
+    """The 255-beam square-cell recipe (3000 slices of 0.01 A, sp4) of its first parameter set at
+    LARGE_ANGLES, one process per angle."""
+    wl = W.large_n255(1)[0]
+    t = time.time()
+    rho, eta, flux, n_rhst = rocking_curve_parallel(wl, "sp4", 1000.0, angles=LARGE_ANGLES)
+    out = os.path.join(HERE, "large_n255_sp4_sampled.npz")
+    np.savez_compressed(out, angles=np.array(LARGE_ANGLES), theta0=wl.theta0[list(LARGE_ANGLES)],
+                        theta1=wl.theta1[list(LARGE_ANGLES)], rho=rho, eta=eta, n_rhst=n_rhst,
+                        n_steps=wl.n_steps, z_e=wl.z_e)
+    print(f"wrote {out} in {time.time() - t:.1f}s; rhst per angle {n_rhst.min()}..{n_rhst.max()}")
+
+
 if __name__ == "__main__":
-    main()
+    large() if sys.argv[1:] == ["large"] else main()

@@ -84,17 +84,23 @@ def test_create_rejects_nonzero_first_beam(lib):
 
 
 def test_large_beam_sets_are_unsupported_not_wrong(lib):
-    """FP64 takes N <= 256, the mixed path N <= 128; both limits are checked before any device
-    work, so they are reported here without a GPU."""
+    """Both paths take N <= 256, and the mixed path above 128 beams a difference grid of at most
+    1536 entries; these limits are checked before any device work, so they are reported here
+    without a GPU."""
     a1, a2 = W.hex_lattice(3.84)
     wl = W.trhepd_n61()
     wl.beams = W.beam_disk(a1, a2, 257)
     p, keep = _problem(wl)
     ctx = C.c_void_p()
     assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
-    wl.beams = W.beam_disk(a1, a2, 129)
     p, keep = _problem(wl, precision=1)
     assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
+    # 143 beams spread over a long row: the grid of their differences has 22,599 entries
+    wl.beams = np.array([[0, 0], [1, 0], [0, 1]] + [[m, 40] for m in range(-70, 70)],
+                        dtype=np.int32)
+    p, keep = _problem(wl, precision=1)
+    assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
+    assert b"difference grid" in lib.trh_last_error()
     # RK4 runs on the FP64 path only
     p, keep = _problem(W.rheed_row(), precision=1, integrator=2)
     assert lib.trh_create(C.byref(ctx), C.byref(p)) == api.TRH_EUNSUPPORTED
@@ -122,6 +128,7 @@ def test_binding_structs_match_the_header(name, cls):
 
 def test_null_arguments(lib):
     assert lib.trh_set_column_split(None, 0) == api.TRH_EINVAL
+    assert lib.trh_set_async(None, 1) == api.TRH_EINVAL
     assert lib.trh_create(None, None) == api.TRH_EINVAL
     assert lib.trh_query(None, None) == api.TRH_EINVAL
     assert lib.trh_rocking_curve(None, 1, None, None, None, None, None) == api.TRH_EINVAL

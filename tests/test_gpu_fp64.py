@@ -188,3 +188,45 @@ def test_azimuth_scan_and_all_beams(api):
     # the azimuth matters: curves at different theta1 differ beyond rounding
     e = eta.cpu().numpy()[0].reshape(3, 4, -1)
     assert np.max(np.abs(e[:, 0] - e[:, 2])) > 1e-6 * np.max(np.abs(e))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_asynchronous_calls(api, precision):
+    """trh_set_async: back-to-back calls with a structure change between them queue without a
+    host wait; device outputs and pinned host outputs equal the synchronous ones bitwise, the
+    counters of the last call are completed by the query, and a failing pair is reported there
+    instead of by the call."""
+    import torch
+    wl = W.tiny(n_beams=37, seed=21, n_steps=40, theta0=(0.8, 1.9, 3.3), depth=6.0)
+    atoms2 = wl.atoms + np.array([0.0, 0.0, -0.15])
+    ref = api.Engine(wl, precision, "sp4")
+    r1, e1 = ref.rocking_curve(wl.theta0, wl.theta1)
+    ref.set_structures(atoms2)
+    r2, e2 = ref.rocking_curve(wl.theta0, wl.theta1)
+    n_rhst = ref.stats()["rhst_total"]
+    eng = api.Engine(wl, precision, "sp4")
+    eng.set_async(True)
+    a1, b1 = eng.rocking_curve(wl.theta0, wl.theta1)
+    eng.set_structures(atoms2)
+    rho_h = torch.empty((1, 3, 37), dtype=torch.complex128, pin_memory=True)
+    eta_h = torch.empty((1, 3, 37), dtype=torch.float64, pin_memory=True)
+    eng.rocking_curve_host(wl.theta0, wl.theta1, rho_h.numpy(), eta_h.numpy())
+    st = eng.stats()  # waits for the last call
+    assert st["n_bad"] == 0 and st["rhst_total"] == n_rhst and st["ms_integrate"] > 0
+    torch.cuda.synchronize()
+    assert np.array_equal(a1.cpu().numpy(), r1.cpu().numpy())
+    assert np.array_equal(b1.cpu().numpy(), e1.cpu().numpy())
+    assert np.array_equal(rho_h.numpy(), r2.cpu().numpy())
+    assert np.array_equal(eta_h.numpy(), e2.cpu().numpy())
+    # a grazing beam: the call returns, the query reports it
+    gamma = model.vacuum_wavenumber(wl.energy_ev)
+    k = model.rods(wl.beams, wl.a1, wl.a2)
+    j = int(np.argmax(k[:, 0]))
+    theta = float(np.rad2deg(np.arccos((-k[j, 0] + np.sqrt(gamma ** 2 - k[j, 1] ** 2)) / gamma)))
+    eng.rocking_curve([2.0, theta], [0.0, 0.0])
+    st = eng.stats()
+    assert st["n_bad"] == 1 and st["first_bad_angle"] == 1
+    assert st["first_bad_status"] == api.TRH_EGRAZING
+    eng.set_async(False)
+    with pytest.raises(api.TrhError):
+        eng.rocking_curve([2.0, theta], [0.0, 0.0])

@@ -127,3 +127,19 @@ def test_limits(api):
     with pytest.raises(api.TrhError) as e:
         api.Engine(wl, "mixed", "sp4")
     assert e.value.code == api.TRH_EUNSUPPORTED
+
+
+def test_large_recipe_full_depth_sampled_angles(api):
+    """The 255-beam recipe's first structure at its full 3000 slices of 0.01 A, all 120 angles in
+    one call (the launch configuration of the bench line), against the oracle's curve at the
+    sampled angles stored in tests/golden (written by make_golden.py from the oracle alone)."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "large_n255_sp4_sampled.npz"))
+    wl = W.large_n255(1)[0]
+    assert wl.n_steps == int(g["n_steps"]) and len(wl.theta0) == 120
+    np.testing.assert_array_equal(wl.theta0[g["angles"]], g["theta0"])
+    eng = api.Engine(wl, "mixed", "sp4")
+    rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+    rho, eta = rho.cpu().numpy()[0], eta.cpu().numpy()[0]
+    assert np.all(np.isfinite(rho)) and eng.stats()["n_bad"] == 0
+    _check(rho[g["angles"]], eta[g["angles"]], g["rho"], g["eta"])
