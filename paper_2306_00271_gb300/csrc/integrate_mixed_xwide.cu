@@ -13,11 +13,14 @@
 // 2 MB (four 128-row tiles x K = 512 x four digit planes), 36 GB per structure at 3000 slices.
 // Instead each node has a digit table on the grid of beam differences: entry bj[j] - bk[k] holds
 // the four BF16 digits of Re u and Im u of u_{g_j - g_k} (16 B; 1369 entries for the 255-beam
-// square disk), one bulk copy per kick. Warps 1..15 (producers) build the real-ified tiles from
-// it in shared memory, stage by stage (a stage = one 128-row tile x 32 K columns x four digit
-// planes, 32 KB), into a ring of NBUF stage buffers; warp 0 (consumer) issues each stage's MMAs
-// as soon as its producers have arrived on the stage's "full" mbarrier, and the MMA completion
-// (tcgen05.commit) on the stage's "empty" mbarrier hands the buffer back. Entry (2j+p, 2k+q) of
+// square disk), one bulk copy per kick. Warps 4..15 (producers) build the real-ified tiles from
+// it in shared memory, stage by stage (a stage = one 128-row tile x 16 K columns x four digit
+// planes, 16 KB; the stages of a kick take the row tiles in turn), into a ring of NBUF stage
+// buffers; consumer warp r (r < 4) issues the MMAs of row tile r's stages as soon as their
+// producers have arrived on the stage's "full" mbarrier, and the MMA completion
+// (tcgen05.commit) on the stage's "empty" mbarrier hands the buffer back. The four issuing warps
+// run at once: with products this narrow (N <= 64) the time an issuing thread spends per MMA, not
+// the tensor core, sets the pace. Entry (2j+p, 2k+q) of
 // the real-ified A is [[Re u, -Im u], [Im u, Re u]][p][q]; the digits of -Im u are those of Im u
 // with the BF16 sign bit flipped. The node's scale (a power of two >= every |Re u|, |Im u|) makes
 // every digit product exact, as for N <= 128.
@@ -55,21 +58,21 @@ using namespace mixed;
 
 constexpr int NT = 512;
 constexpr int NWARP = NT / 32;
-constexpr int NPROD = NWARP - 1;     // producer warps 1 .. 15
 constexpr int MT = 128;              // rows of a UMMA tile
 constexpr int RMAX = 4;              // row tiles (2N <= 512 real-ified rows)
+constexpr int NCONS = RMAX;          // consumer warps 0 .. 3: warp r issues the MMAs of tile r
+constexpr int NPROD = NWARP - NCONS; // producer warps 4 .. 15
 constexpr int NW = 256;              // largest N
 constexpr int CW = 16;               // columns per CTA
 constexpr int CP = 4;                // columns per thread and row tile (4 column groups of 4)
 constexpr int KSMAX = 32;            // K-slices of 16 (K = 2N <= 512)
-constexpr int KC = 2;                // K-slices per stage
-constexpr int NBUF = 3;              // stage buffers
+constexpr int NBUF = 6;              // stage buffers
 constexpr int GROUPS = MT / 8;       // eight-row groups of a tile
-// Stage layout: digit plane d at d PLANE_STAGE, 8-row group g at g 512, K-block kb (8 elements)
-// at kb 128, row i of the group at i 16: the canonical no-swizzle K-major layout with LBO = 128
-// and SBO = 512 (K-slice qq of the stage at qq 256).
-constexpr int PLANE_STAGE = GROUPS * KC * 2 * 128;   // 8 KB
-constexpr int STAGE_BYTES = NDIG * PLANE_STAGE;      // 32 KB
+// A stage is one 128-row tile x one K-slice (16 K elements) of the four digit planes. Layout:
+// digit plane d at d PLANE_STAGE, 8-row group g at g 256, K-block kb (8 elements) at kb 128,
+// row i of the group at i 16: the canonical no-swizzle K-major layout with LBO = 128, SBO = 256.
+constexpr int PLANE_STAGE = GROUPS * 2 * 128;        // 4 KB
+constexpr int STAGE_BYTES = NDIG * PLANE_STAGE;      // 16 KB
 constexpr int A_BYTES = NBUF * STAGE_BYTES;          // 96 KB
 constexpr int B_LBO = 144;           // padded K-block stride: conflict-free digit stores
 constexpr int B_SBO = 2 * KSMAX * B_LBO;
@@ -161,15 +164,16 @@ __global__ void __launch_bounds__(256) k_digit_grid(DigitGridParams p) {
   }
 }
 
-// One 8-row group gg of row tile rt, K-chunk c of the real-ified U(tau) into a stage buffer, by
-// one warp: lane (i = lane % 8, kb = lane / 8) writes row 8 gg + i, K-block kb (elements
-// 32 c + 8 kb .. + 7, i.e. beams k = 16 c + 4 kb .. + 3 with both parts q) of the four planes.
-__device__ __forceinline__ void produce_group(const XSmem& S, unsigned char* stage, int rt, int c,
-                                              int gg, int lane, int N) {
-  const int i = lane & 7, kb = lane >> 3;
-  const int m = MT * rt + 8 * gg + i;
+// Two 8-row groups (2 gp, 2 gp + 1) of row tile rt, K-slice ks of the real-ified U(tau) into a
+// stage buffer, by one warp: lane (i = lane % 8, kb = lane / 8 % 2, group 2 gp + lane / 16)
+// writes row 8 g + i, K-block kb (elements 16 ks + 8 kb .. + 7, i.e. beams k = 8 ks + 4 kb .. + 3
+// with both parts q) of the four planes.
+__device__ __forceinline__ void produce_pair(const XSmem& S, unsigned char* stage, int rt, int ks,
+                                             int gp, int lane, int N) {
+  const int i = lane & 7, kb = (lane >> 3) & 1, g = 2 * gp + (lane >> 4);
+  const int m = MT * rt + 8 * g + i;
   const int j = m >> 1, p = m & 1;
-  const int k0 = 16 * c + 4 * kb;
+  const int k0 = 8 * ks + 4 * kb;
   const bool jl = j < N;
   const int bjv = jl ? S.bj[j] : 0;
   uint4 e[4];
@@ -181,23 +185,21 @@ __device__ __forceinline__ void produce_group(const XSmem& S, unsigned char* sta
   // plane d, word w = elements (2w, 2w + 1) = (q = 0, q = 1) of beam k0 + w:
   //   p = 0: (Re_d, -Im_d) ; p = 1: (Im_d, Re_d)
   const uint32_t neg = p ? 0u : 0x80000000u;
-  uint4 o[NDIG];
+  uint32_t o0[4], o1[4], o2[4], o3[4];
 #pragma unroll
   for (int w = 0; w < 4; ++w) {
     const uint32_t lo01 = p ? e[w].z : e[w].x, hi01 = p ? e[w].x : e[w].z;
     const uint32_t lo23 = p ? e[w].w : e[w].y, hi23 = p ? e[w].y : e[w].w;
-    const uint32_t d0 = __byte_perm(lo01, hi01, 0x5410) ^ neg;
-    const uint32_t d1 = __byte_perm(lo01, hi01, 0x7632) ^ neg;
-    const uint32_t d2 = __byte_perm(lo23, hi23, 0x5410) ^ neg;
-    const uint32_t d3 = __byte_perm(lo23, hi23, 0x7632) ^ neg;
-    reinterpret_cast<uint32_t*>(&o[0])[w] = d0;
-    reinterpret_cast<uint32_t*>(&o[1])[w] = d1;
-    reinterpret_cast<uint32_t*>(&o[2])[w] = d2;
-    reinterpret_cast<uint32_t*>(&o[3])[w] = d3;
+    o0[w] = __byte_perm(lo01, hi01, 0x5410) ^ neg;
+    o1[w] = __byte_perm(lo01, hi01, 0x7632) ^ neg;
+    o2[w] = __byte_perm(lo23, hi23, 0x5410) ^ neg;
+    o3[w] = __byte_perm(lo23, hi23, 0x7632) ^ neg;
   }
-  unsigned char* dst = stage + gg * 512 + kb * 128 + i * 16;
-#pragma unroll
-  for (int d = 0; d < NDIG; ++d) *reinterpret_cast<uint4*>(dst + d * PLANE_STAGE) = o[d];
+  unsigned char* dst = stage + g * 256 + kb * 128 + i * 16;
+  *reinterpret_cast<uint4*>(dst + 0 * PLANE_STAGE) = make_uint4(o0[0], o0[1], o0[2], o0[3]);
+  *reinterpret_cast<uint4*>(dst + 1 * PLANE_STAGE) = make_uint4(o1[0], o1[1], o1[2], o1[3]);
+  *reinterpret_cast<uint4*>(dst + 2 * PLANE_STAGE) = make_uint4(o2[0], o2[1], o2[2], o2[3]);
+  *reinterpret_cast<uint4*>(dst + 3 * PLANE_STAGE) = make_uint4(o3[0], o3[1], o3[2], o3[3]);
 }
 
 // Column maxima of |Qh| over this thread's rows of all tiles, reduced over the warp's 32 lanes
@@ -446,8 +448,8 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_xwide(const MixedXwid
   const uint32_t rank = cluster_ctarank();
   const int angle = blockIdx.x / n_cta, set = p.set0 + blockIdx.y;
   const int N = p.N, R = xp.R, G = xp.G;
-  const int NCH = p.k_slices / KC;      // K-chunks (stages) per row tile
-  const int SPK = R * NCH;              // stages per kick
+  const int KSP = p.k_slices;           // K-slices of the product
+  const int SPK = R * KSP;              // stages per kick: stage st = (K-slice st / R, tile st % R)
   const size_t pair = (size_t)set * p.ang.n_angles + angle;             // outputs
   const size_t lp = (size_t)blockIdx.y * p.ang.n_angles + angle;        // launch scratch
   const int cbase = CW * (int)rank + CP * cq;  // this thread's first column (of all N)
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_xwide(const MixedXwid
       mbar_init(&S.empty[b], 1);
     }
     mbar_init(&S.bar_tab, 1);
-    mbar_init(&S.bar_mma, 1);
+    mbar_init(&S.bar_mma, NCONS);
     mbar_init(&S.bar_x[0], n_cta - 1);
     mbar_init(&S.bar_x[1], n_cta - 1);
     mbar_fence_init();
@@ -562,10 +564,12 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_xwide(const MixedXwid
       const int kidx = last ? s + 1 : (r > 0 ? r : (i == 0 ? 0 : s));
       const float alpha = __ldg(scale_set + kick_no);
       int to = 0;
-      if (warp == 0) {
-        // consumer: each stage's MMAs once its producers have arrived; after the last stage
-        // (every producer is done with the table) the next node's table is fetched
-        for (int st = 0; st < SPK; ++st) {
+      if (warp < NCONS) {
+        // consumer warp w: the MMAs of row tile w's stages (every R-th stage) once their
+        // producers have arrived; the four tiles' MMAs are issued from four warps at once. After
+        // the kick's last stage (every producer is done with the table) the next node's table is
+        // fetched.
+        for (int st = warp; warp < R && st < SPK; st += R) {
           const uint32_t g = gs + (uint32_t)st, b = g % NBUF, u = g / NBUF;
           if (!wait_warp(&S.full[b], u & 1u)) {
             to = 1;
@@ -573,20 +577,14 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_xwide(const MixedXwid
           }
           if (lane == 0) {
             tc_fence_after();
-            const int rt = st / NCH, c = st - rt * NCH;
+            const int ks = st / R;
             const uint32_t a_base = smem_u32(S.A + b * STAGE_BYTES);
+            const uint64_t bk = (uint64_t)((ks * 2 * B_LBO) >> 4);
 #pragma unroll
-            for (int a = 0; a < NDIG; ++a) {
-              const uint64_t ad = smem_desc(a_base + a * PLANE_STAGE, 128, 512);
-              const uint64_t bd = smem_desc(b_base + a * BT, B_LBO, B_SBO);
-              const uint32_t id = idesc_bf16_f32(MT, CW * (NDIG - a));
-#pragma unroll
-              for (int qq = 0; qq < KC; ++qq) {
-                const int ksg = KC * c + qq;
-                mma_bf16(tmem + (uint32_t)(64 * rt), ad + (uint64_t)((qq * 256) >> 4),
-                         bd + (uint64_t)((ksg * 2 * B_LBO) >> 4), id, !(a == 0 && ksg == 0));
-              }
-            }
+            for (int a = 0; a < NDIG; ++a)
+              mma_bf16(tmem + (uint32_t)(64 * warp), smem_desc(a_base + a * PLANE_STAGE, 128, 256),
+                       smem_desc(b_base + a * BT, B_LBO, B_SBO) + bk,
+                       idesc_bf16_f32(MT, CW * (NDIG - a)), !(a == 0 && ks == 0));
             mma_commit(&S.empty[b]);
             if (st == SPK - 1 && !last) {
               mbar_arrive_expect_tx(&S.bar_tab, tab_bytes);
@@ -599,11 +597,13 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_xwide(const MixedXwid
         if (lane == 0) mma_commit(&S.bar_mma);
         __syncwarp();
       } else {
-        // producers: the node's table, then every stage of the kick into the ring
+        // producers (warps 4 .. 15): the node's table, then the kick's stages in order; each
+        // stage's eight two-group tasks go to eight of the twelve warps, rotating with the stage
+        const int pw = warp - NCONS;
         bool ok = wait_warp(&S.bar_tab, ph_tab);
         if (ok) {
           ph_tab ^= 1u;
-          if (warp == 1 && lane == 0) S.tab_waits++;
+          if (pw == 0 && lane == 0) S.tab_waits++;
         }
         for (int st = 0; st < SPK && ok; ++st) {
           const uint32_t g = gs + (uint32_t)st, b = g % NBUF, u = g / NBUF;
@@ -611,11 +611,11 @@ __global__ void __launch_bounds__(NT, 1) k_integrate_mixed_xwide(const MixedXwid
             ok = false;
             break;
           }
-          const int rt = st / NCH, c = st - rt * NCH;
-          unsigned char* stage = S.A + b * STAGE_BYTES;
-          int gg = ((warp - 1 - st) % NPROD + NPROD) % NPROD;
-          for (; gg < GROUPS; gg += NPROD) produce_group(S, stage, rt, c, gg, lane, N);
-          fence_proxy_async_smem();
+          const int gp = (pw + st) % NPROD;  // task of this warp, if < GROUPS / 2
+          if (gp < GROUPS / 2) {
+            produce_pair(S, S.A + b * STAGE_BYTES, st % R, st / R, gp, lane, N);
+            fence_proxy_async_smem();
+          }
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.full[b]);
         }

@@ -35,10 +35,12 @@ LARGE_ANGLES = (10, 40, 70, 100)
 
 def large():
     """The 255-beam square-cell recipe (3000 slices of 0.01 A, sp4) of its first parameter set at
-    LARGE_ANGLES, one process per angle."""
+    LARGE_ANGLES."""
     wl = W.large_n255(1)[0]
     t = time.time()
-    rho, eta, flux, n_rhst = rocking_curve_parallel(wl, "sp4", 1000.0, angles=LARGE_ANGLES)
+    # two processes: the oracle expands U(tau) at every node, about 17 GB per process here
+    rho, eta, flux, n_rhst = rocking_curve_parallel(wl, "sp4", 1000.0, angles=LARGE_ANGLES,
+                                                    processes=2)
     out = os.path.join(HERE, "large_n255_sp4_sampled.npz")
     np.savez_compressed(out, angles=np.array(LARGE_ANGLES), theta0=wl.theta0[list(LARGE_ANGLES)],
                         theta1=wl.theta1[list(LARGE_ANGLES)], rho=rho, eta=eta, n_rhst=n_rhst,
