@@ -169,7 +169,7 @@ def run_large_sample(slices: int = 30):
             "note": "FP64 wide kernel, 120 angles on 120 SMs, measured at this slice count"}
 
 
-def run_large(n_sets: int = 2, slices: int = 0):
+def run_large(n_sets: int = 2, slices: int = 0, n_angles: int = 0):
     """The 255-beam recipe (square 5.4 A cell, 3000 slices of 0.01 A, 120 angles 0.2..6.2 deg)
     on the mixed path for its first n_sets structures in one call: angles/s over the whole call,
     and the error of the first structure's curve against the oracle at the sampled angles of
@@ -180,6 +180,8 @@ def run_large(n_sets: int = 2, slices: int = 0):
     from paper_2306_00271_gb300 import api
     sets = W.large_n255(n_sets)
     wl = sets[0].with_steps(slices) if slices else sets[0]
+    if n_angles:
+        wl = wl.with_angles(wl.theta0[np.linspace(0, len(wl.theta0) - 1, n_angles).astype(int)])
     eng = api.Engine(wl, "mixed", "sp4")
     eng.set_structures(np.stack([s.atoms for s in sets]))
     eng.rocking_curve(wl.theta0[:1], wl.theta1[:1])  # tables and images outside the timing
@@ -200,7 +202,7 @@ def run_large(n_sets: int = 2, slices: int = 0):
                            wl.n_steps, -wl.z_e / wl.n_steps, n_sets)}
     gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
                         "large_n255_sp4_sampled.npz")
-    if not slices and os.path.exists(gold):
+    if not slices and not n_angles and os.path.exists(gold):
         g = np.load(gold)
         e = eta.cpu().numpy()[0][g["angles"]]
         out["curve_error_vs_oracle_sampled"] = curve_error(e, g["eta"])
@@ -545,8 +547,18 @@ def main():
     ap.add_argument("--column-split", default="auto", choices=["auto", "on", "off"],
                     help="mixed path: two CTAs per angle (auto: when the angles fit on half "
                          "the SMs)")
+    ap.add_argument("--large-only", action="store_true",
+                    help="only the 255-beam mixed line (profiling cases with --slices and "
+                         "--large-angles; not the bench line)")
+    ap.add_argument("--large-sets", type=int, default=2)
+    ap.add_argument("--large-angles", type=int, default=0)
     args = ap.parse_args()
     ws, rank, _ = _dist()
+    if args.large_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_large(args.large_sets, args.slices, args.large_angles)))
+        return
     wl = W.trhepd_n61()
     cfg = {"workload": "trhepd_n61: 10 keV e+, hex a=3.84 A, N=61 beams, 16 atoms, "
                        "L=2000 x 0.015 A, 60 angles 0.5..6.4 deg, sp4, RHST threshold 1000",
