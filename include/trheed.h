@@ -133,6 +133,12 @@ typedef struct trh_stats {
   int set_chunks;         /* mixed path: chunks of parameter sets the last call ran in (the
                              sets' digit images are built for one chunk at a time, at most
                              40 GiB of them; 1 when every set fits)                            */
+  int tuned;              /* 1 if the launch shape of the last call (column_split, wide_tile) was
+                             chosen by the autotuner: the candidate shapes timed on a 2-step
+                             probe of the call's own pairs, the fastest kept per (precision, N,
+                             integrator, pair count) for the life of the process; 0 for a fixed
+                             rule (a forced split mode, more pairs than SMs, N <= 32, a mixed
+                             cluster of ceil(N / 32) or ceil(N / 16) CTAs)                      */
 } trh_stats;
 
 /* Create a context for one beam set and method. Validates and copies `p` (the caller may free
@@ -204,8 +210,10 @@ int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* d
  * of a thread-block cluster, 32 each. They exchange the Varah row sums once per step, the column
  * halves of Q and P at every RHST (Section 3.2: both CTAs hold the whole [Q; P] for it) and at
  * the end (CTA 0 assembles rho). This shortens a pair's critical path but takes two SMs per pair:
- * TRH_SPLIT_AUTO (the default) uses it when N > 32 and the call has at most (SM count / 2)
- * pairs, TRH_SPLIT_OFF never, TRH_SPLIT_ON whenever N > 32. Results are identical either way:
+ * TRH_SPLIT_AUTO (the default) lets the autotuner choose when N > 32 and the call has at most
+ * as many pairs as SMs (both forms timed on a 2-step probe of the call's pairs, the faster kept
+ * for that shape; trh_stats.tuned), TRH_SPLIT_OFF never splits, TRH_SPLIT_ON whenever N > 32
+ * (trh_curve_jacobian's forward splits when its pairs fit on half the SMs). Results are identical either way:
  * every column sees the same arithmetic, and the row sums are added in the same fixed order, so
  * the RHST decisions coincide. Batches (trh_batch_*) always run one CTA per pair. A wait for the
  * other CTA that runs out (about 2 s) ends the pair with TRH_ETIMEOUT.

@@ -4,6 +4,7 @@
 // positions of the integrator) and moves data.
 #include "trheed.h"
 #include "internal.h"
+#include "tuner.h"
 
 #include <algorithm>
 #include <chrono>
@@ -850,47 +851,101 @@ static int bad_pairs_error(const trh_ctx* c) {
               S.n_bad, S.first_bad_set, S.first_bad_angle, trh_strerror(S.first_bad_status));
 }
 
-// Autotuner for the wide FP64 kernel's tile edge (64 or 32): times each candidate on a probe
-// (first angle of the first set, 2 steps, outputs later overwritten by the real run) after one
-// warm-up launch, and keeps the fastest per beam count for the life of the process. Padding
-// decides most of it: N = 65 pads to 128 with 64-tiles but to 96 with 32-tiles, while N = 255
-// pads to 256 either way and the larger tile has less overhead.
-static std::mutex g_tune_mu;
-static std::map<int, int> g_wide_tile;  // key 2 N + method
+// Autotuner (tuner.h): launch shapes timed on a probe of the call's own launch and cached per
+// shape for the life of the process.
+}  // extern "C" (the probe helper is a template)
 
+static trh::tune::Cache g_tune;
+
+// Times `launch` on the call's stream: one warm-up launch, then one timed between events.
+template <class F>
+static float probe_ms(trh_ctx* c, cudaStream_t st, F launch) {
+  if (launch() != cudaSuccess) {
+    cudaGetLastError();
+    return -1.0f;
+  }
+  if (cudaEventRecord(c->ev[4], st) != cudaSuccess || launch() != cudaSuccess ||
+      cudaEventRecord(c->ev[5], st) != cudaSuccess || cudaEventSynchronize(c->ev[5]) != cudaSuccess) {
+    cudaGetLastError();
+    return -1.0f;
+  }
+  return elapsed_ms(c->ev[4], c->ev[5]);
+}
+
+// Tile edge of the wide FP64 kernel (64 or 32): each candidate timed on the first angle of the
+// first set for 2 steps (outputs later overwritten by the real run). Padding decides most of it:
+// N = 65 pads to 128 with 64-tiles but to 96 with 32-tiles, while N = 255 pads to 256 either way
+// and the larger tile has less overhead.
 static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* state,
                           cudaStream_t st, int* tile) {
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_wide_tile.find(2 * c->N + ip.method);
-    if (it != g_wide_tile.end()) {
-      *tile = it->second;
-      return TRH_OK;
-    }
-  }
+  const trh::tune::Key key{trh::tune::kWideTile, c->precision, c->N, ip.method, 1};
+  if (g_tune.find(key, tile)) return TRH_OK;
   trh::IntegrateParams pp = ip;
   pp.L = ip.L < 2 ? ip.L : 2;
   pp.ang.n_angles = 1;
   pp.n_sets = 1;
-  float best = 3.0e38f;
-  int best_tile = 64;
-  for (int cand : {64, 32}) {
-    TRH_CUDA(trh::launch_integrate_fp64_wide(pp, state, cand, st, nullptr));
-    TRH_CUDA(cudaEventRecord(c->ev[4], st));
-    TRH_CUDA(trh::launch_integrate_fp64_wide(pp, state, cand, st, nullptr));
-    TRH_CUDA(cudaEventRecord(c->ev[5], st));
-    TRH_CUDA(cudaEventSynchronize(c->ev[5]));
-    const float ms = elapsed_ms(c->ev[4], c->ev[5]);
-    if (ms < best) {
-      best = ms;
-      best_tile = cand;
-    }
-  }
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_wide_tile[2 * c->N + ip.method] = best_tile;
-  *tile = best_tile;
+  const int cand[2] = {64, 32};
+  float ms[2];
+  for (int i = 0; i < 2; ++i)
+    ms[i] = probe_ms(c, st, [&] {
+      return trh::launch_integrate_fp64_wide(pp, state, cand[i], st, nullptr);
+    });
+  *tile = cand[trh::tune::pick(ms, 2, 0.0f)];
+  g_tune.put(key, *tile);
   return TRH_OK;
 }
+
+// One CTA per (set, angle) pair or two sharing its columns (mixed path and FP64 path with
+// N <= 64): a forced mode, or (AUTO) the faster of the two forms on a 2-step probe of this call's
+// pairs (cached per precision, N, integrator and pair count). The two forms give the same bits.
+// With more pairs than SMs the split only adds waves, so no probe runs.
+static int choose_split(trh_ctx* c, const trh::IntegrateParams& ip, size_t pairs,
+                        cudaStream_t st, int* launched, bool* split, bool* tuned) {
+  *split = false;
+  *tuned = false;
+  const bool mixed_small = c->precision == TRH_MIXED && c->N <= trh::kMaxBeamsMixed;
+  const bool fp64_smem = c->precision == TRH_FP64 && c->N <= trh::kMaxBeamsFp64 &&
+                         (c->integrator == TRH_SP4 || c->integrator == TRH_SP6);
+  if ((!mixed_small && !fp64_smem) || c->N <= 32 || c->split_mode == TRH_SPLIT_OFF) return TRH_OK;
+  if (c->split_mode == TRH_SPLIT_ON) {
+    *split = true;
+    return TRH_OK;
+  }
+  int dev = 0, sms = 0;
+  TRH_CUDA(cudaGetDevice(&dev));
+  TRH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (pairs > (size_t)sms) return TRH_OK;
+  const trh::tune::Key key{trh::tune::kColumnSplit, c->precision, c->N, c->integrator,
+                           (long long)pairs};
+  int v = 0;
+  if (!g_tune.find(key, &v)) {
+    float ms[2];
+    if (mixed_small) {
+      const int ns = std::min(mixed_chunk_sets(c), c->n_sets);
+      const int rc = ensure_images(c, 0, ns, st, launched);
+      if (rc != TRH_OK) return rc;
+      trh::MixedParams mp = mixed_params(c, ip);
+      mp.L = c->L < 2 ? c->L : 2;
+      mp.n_sets = ns;
+      mp.ckpt = nullptr;
+      for (int i = 0; i < 2; ++i)
+        ms[i] = probe_ms(c, st, [&] { return trh::launch_integrate_mixed(mp, i == 1, st, nullptr); });
+    } else {
+      trh::IntegrateParams pp = ip;
+      pp.L = ip.L < 2 ? ip.L : 2;
+      pp.ckpt = nullptr;
+      for (int i = 0; i < 2; ++i)
+        ms[i] = probe_ms(c, st, [&] { return trh::launch_integrate_fp64(pp, i == 1, st, nullptr); });
+    }
+    v = trh::tune::pick(ms, 2, 0.02f);
+    g_tune.put(key, v);
+  }
+  *split = v == 1;
+  *tuned = true;
+  return TRH_OK;
+}
+
+extern "C" {
 
 int trh_set_image_budget(trh_ctx* c, size_t bytes) {
   if (!c) return fail(TRH_EINVAL, "ctx is NULL");
@@ -1103,7 +1158,11 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
     rc = tune_wide_tile(c, ip, c->d_wide.p, st, &tile);
     if (rc != TRH_OK) return rc;
   }
-  const bool split = use_split(c, pairs);
+  bool split = false, tuned = wide;
+  if (!wide) {
+    rc = choose_split(c, ip, pairs, st, &launched, &split, &tuned);
+    if (rc != TRH_OK) return rc;
+  }
   int chunks = 1, ctas = split ? 2 : 1;
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
@@ -1142,6 +1201,7 @@ int trh_rocking_curve(trh_ctx* c, int n_angles, const double* theta0, const doub
   S.column_split = split ? 1 : 0;
   S.ctas_per_pair = ctas;
   S.set_chunks = chunks;
+  S.tuned = tuned ? 1 : 0;
   S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
                   .count();
   if (S.n_bad) return bad_pairs_error(c);
@@ -1263,6 +1323,7 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   ip.n_ckpt = n_seg + 1;
   bool split = false;
   c->stats.column_split = 0;
+  c->stats.tuned = 0;
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
     // mixed forward: curve and checkpoints from the double-float state; every segment is then

@@ -55,6 +55,7 @@ def test_bulk_fp64_against_oracle(api, n_beams):
 def test_bulk_mixed_against_oracle(api, n_beams):
     wl, atoms, dw, sp = _case(n_beams)
     eng = api.Engine(wl, "mixed", "sp4")
+    eng.set_column_split("on")  # two CTAs per pair when N > 32: the split form starts from [I; X]
     eng.set_bulk(atoms, dw, sp, PERIOD, STEPS)
     _, eta = eng.rocking_curve(wl.theta0, wl.theta1)
     assert eng.stats()["column_split"] == (1 if n_beams > 32 else 0)

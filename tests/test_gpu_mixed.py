@@ -129,3 +129,30 @@ def test_full_rocking_curve_61_beams(api, mode):
         idx = [0, 15, 37, 59]
         rho_o, eta_o, _, _ = rocking_curve(wl, "sp4", angles=idx)
         _check(rho[idx], eta[idx], rho_o, eta_o)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_autotuned_split_matches_both_forms(api, precision):
+    """TRH_SPLIT_AUTO: the autotuner times both forms on a probe of the call's pairs and keeps the
+    faster (trh_stats.tuned = 1); the curve equals the forced one-CTA and two-CTA curves bitwise,
+    and a second call with the same shape reuses the cached choice."""
+    wl = W.tiny(n_beams=45, seed=17, n_steps=30, theta0=(0.7, 1.6, 2.9, 4.1), depth=6.0)
+    out = {}
+    for mode in ("off", "on", "auto"):
+        eng = api.Engine(wl, precision, "sp4")
+        eng.set_column_split(mode)
+        rho, eta = eng.rocking_curve(wl.theta0, wl.theta1)
+        st = eng.stats()
+        out[mode] = (rho.cpu().numpy(), st)
+        if mode == "auto":
+            assert st["tuned"] == 1
+            rho2, _ = eng.rocking_curve(wl.theta0, wl.theta1)
+            assert eng.stats()["tuned"] == 1
+            assert eng.stats()["column_split"] == st["column_split"]
+            assert np.array_equal(rho2.cpu().numpy(), out[mode][0])
+        else:
+            assert st["tuned"] == 0
+        eng.close()
+    assert out["off"][1]["column_split"] == 0 and out["on"][1]["column_split"] == 1
+    assert np.array_equal(out["off"][0], out["on"][0])
+    assert np.array_equal(out["auto"][0], out["off"][0])
