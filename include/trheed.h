@@ -261,12 +261,16 @@ int trh_set_image_budget(trh_ctx* ctx, size_t bytes);
  * checkpoints: the forward pass stores [Q; P] every `ckpt_every` steps and the reverse sweep
  * recomputes one segment at a time. Device scratch per (set, angle) pair, in bytes:
  *   16 N^2 (2 (L / C + 1) + 2 (s C + 1) + 2 C + 2) + 4 C,   C = ckpt_every, s = kicks per step,
- * about 53 MB at N = 61, L = 2000, C = 64 (sp4).
- * On a TRH_FP64 context everything runs on the binary64 path. On a TRH_MIXED context the forward
- * pass (curve, R and the checkpoints, binary64 values of its double-float state) runs on the
- * mixed path and every segment is recomputed on the binary64 path from its checkpoint, so the
- * reverse map differentiates the trajectory it recomputes; the gradient then carries the mixed
- * path's ~1e-8 relative error. */
+ * about 53 MB at N = 61, L = 2000, C = 64 (sp4); for 64 < N <= 256 (the wide reverse sweep,
+ * state in global memory)
+ *   16 N^2 (2 (L / C + 1) + (s C + 1) + 2 C + 6) + 4 C.
+ * N <= 64: on a TRH_FP64 context everything runs on the binary64 path; on a TRH_MIXED context
+ * the forward pass (curve, R and the checkpoints, binary64 values of its double-float state)
+ * runs on the mixed path and every segment is recomputed on the binary64 path from its
+ * checkpoint, so the reverse map differentiates the trajectory it recomputes; the gradient then
+ * carries the mixed path's ~1e-8 relative error. 64 < N <= 256: the forward pass, the recompute
+ * and the adjoint all run on the binary64 wide kernels for either precision (the beam set's
+ * distinct differences must fit shared memory twice: about 2000 at most). */
 
 /* Declare the fit parameters: the z coordinates of atoms free_atoms[0..n_free-1] (distinct
  * indices into the context's atoms) and n_classes Debye-Waller classes, dw_class[a] in
@@ -284,7 +288,8 @@ int trh_set_fit(trh_ctx* ctx, int n_free, const int* free_atoms, int n_classes,
  *   jac_out        : [n_sets][n_angles][n_free + n_classes] float64: d eta_1 / d z of each free
  *                    atom (1/A), then d eta_1 / d B of each class (1/A^2); host or device.
  *   stream         : cudaStream_t (NULL = legacy default stream); synchronised before return.
- * Errors: as trh_rocking_curve, and TRH_EINVAL before trh_set_fit. */
+ * Errors: as trh_rocking_curve, TRH_EINVAL before trh_set_fit, TRH_EUNSUPPORTED (RK4 or the
+ * conventional integrator; above 64 beams, too many distinct differences). */
 int trh_curve_jacobian(trh_ctx* ctx, int n_angles, const double* theta0, const double* theta1,
                        double* eta_out, double* jac_out, void* stream);
 

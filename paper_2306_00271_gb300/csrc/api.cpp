@@ -1266,16 +1266,95 @@ int trh_set_fit(trh_ctx* c, int n_free, const int* free_atoms, int n_classes,
   return TRH_OK;
 }
 
+// The reverse sweep for 64 < N <= 256: the FP64 wide kernel's forward with checkpoints (on
+// either precision: the mixed cluster kernels write no checkpoints), then per segment from the
+// surface down the wide recompute and the wide adjoint with the contraction folded in, in stream
+// order on `st`. Leaves eta in d_eta and d eta_1 / d(z_a, B_a) in d_jacA.
+static int run_reverse_sweep_wide(trh_ctx* c, int n_angles, const double* theta0,
+                                  const double* theta1, cudaStream_t st, int* launched,
+                                  bool* rebuilt) {
+  int rc = upload_angles(c, n_angles, theta0, theta1, st);
+  if (rc != TRH_OK) return rc;
+  rc = build_tables(c, st, launched, rebuilt, false);
+  if (rc != TRH_OK) return rc;
+  const size_t pairs = (size_t)c->n_sets * n_angles;
+  const size_t NN = (size_t)c->N * c->N;
+  const int C = c->ckpt_every, s = c->scheme.s;
+  const int n_seg = (c->L + C - 1) / C;
+  const int kseg = s * C + 1;
+  const int n_act = (int)c->active.size();
+  TRH_CUDA(c->d_rho.ensure(pairs * c->N));
+  TRH_CUDA(c->d_eta.ensure(pairs * c->N));
+  TRH_CUDA(c->d_status.ensure(2 * pairs));
+  TRH_CUDA(c->d_ckpt.ensure(pairs * (n_seg + 1) * 2 * NN));
+  TRH_CUDA(c->d_segQ[0].ensure(pairs * kseg * NN));
+  TRH_CUDA(c->d_segR[0].ensure(pairs * C * 2 * NN));
+  TRH_CUDA(c->d_rflag[0].ensure(pairs * C));
+  TRH_CUDA(c->d_adjZ.ensure(pairs * 2 * NN));
+  TRH_CUDA(c->d_jacA.ensure(pairs * 2 * n_act));
+  TRH_CUDA(c->d_wide.ensure(pairs * 4 * NN));   // forward state, then the sweep's scratch
+  TRH_CUDA(cudaMemsetAsync(c->d_jacA.p, 0, pairs * 2 * n_act * sizeof(double), st));
+  const double2* bulk_p0 = nullptr;
+  rc = bulk_prepare(c, n_angles, theta0, theta1, c->d_theta.p, c->d_theta.p + n_angles, st,
+                    launched, &bulk_p0);
+  if (rc != TRH_OK) return rc;
+  trh::IntegrateParams ip = integrate_params(c, n_angles, pairs, c->d_rho.p, c->d_eta.p);
+  ip.p0 = bulk_p0;
+  int tile = 0;
+  rc = tune_wide_tile(c, ip, c->d_wide.p, st, &tile);
+  if (rc != TRH_OK) return rc;
+  ip.ckpt = c->d_ckpt.p;
+  ip.ckpt_every = C;
+  ip.n_ckpt = n_seg + 1;
+  c->stats.column_split = 0;
+  c->stats.tuned = 1;
+  c->stats.wide_tile = tile;
+  TRH_CUDA(cudaEventRecord(c->ev[2], st));
+  TRH_CUDA(trh::launch_integrate_fp64_wide(ip, c->d_wide.p, tile, st, launched));
+  TRH_CUDA(cudaEventRecord(c->ev[3], st));
+  trh::GradParams g{};
+  g.ip = ip;
+  g.adjZ = c->d_adjZ.p;
+  g.status = c->d_status.p;
+  g.kseg = kseg;
+  g.F = c->d_F.p;
+  g.gdiff = c->d_g.p;
+  g.atoms = c->d_atoms.p;
+  g.dw = c->d_dw.p;
+  g.species = c->d_species.p;
+  g.sf = c->d_sf.p;
+  g.node_z = c->d_nodes.p;
+  g.active = c->d_active.p;
+  g.n_active = n_act;
+  g.n_atoms = c->n_atoms;
+  g.pref = potential_prefactor(c);
+  g.jac_atoms = c->d_jacA.p;
+  g.segQ = c->d_segQ[0].p;
+  g.segR = c->d_segR[0].p;
+  g.rflag = c->d_rflag[0].p;
+  for (int seg = n_seg - 1; seg >= 0; --seg) {
+    g.seg = seg;
+    TRH_CUDA(trh::launch_grad_wide(g, c->d_wide.p, tile, true, st, launched));
+    TRH_CUDA(trh::launch_grad_wide(g, c->d_wide.p, tile, false, st, launched));
+  }
+  TRH_CUDA(cudaEventRecord(c->ev[4], st));
+  return TRH_OK;
+}
+
 // Forward pass with checkpoints, then the reverse sweep segment by segment: leaves eta in
 // d_eta and d eta_1 / d(z_a, B_a) of the active atoms in d_jacA.
 static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
                              const double* theta1, cudaStream_t st, int* launched,
                              bool* rebuilt) {
   if (c->n_free + c->n_classes < 1) return fail(TRH_EINVAL, "call trh_set_fit first");
-  if (c->N > trh::kMaxBeamsFp64)
-    return fail(TRH_EUNSUPPORTED, "the reverse sweep supports N <= %d", trh::kMaxBeamsFp64);
   if (c->integrator == TRH_RK4 || c->integrator == TRH_CONVENTIONAL)
     return fail(TRH_EUNSUPPORTED, "the reverse sweep supports the splitting integrators");
+  if (c->N > trh::kMaxBeamsFp64 &&
+      trh::wide_grad_smem_bytes(c->M, (int)c->active.size()) > 227 * 1024)
+    return fail(TRH_EUNSUPPORTED, "the wide reverse sweep holds at most about 2000 distinct beam "
+                "differences (this beam set has %d)", c->M);
+  if (c->N > trh::kMaxBeamsFp64)
+    return run_reverse_sweep_wide(c, n_angles, theta0, theta1, st, launched, rebuilt);
   int rc = upload_angles(c, n_angles, theta0, theta1, st);
   if (rc != TRH_OK) return rc;
   rc = build_tables(c, st, launched, rebuilt);
@@ -1324,6 +1403,7 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   bool split = false;
   c->stats.column_split = 0;
   c->stats.tuned = 0;
+  c->stats.wide_tile = 0;
   TRH_CUDA(cudaEventRecord(c->ev[2], st));
   if (c->precision == TRH_MIXED) {
     // mixed forward: curve and checkpoints from the double-float state; every segment is then
@@ -1410,7 +1490,6 @@ static int finish_gradient_call(trh_ctx* c, int n_angles, int launched, bool reb
   S.ms_potential = rebuilt ? elapsed_ms(c->ev[0], c->ev[1]) : 0.0;
   S.ms_integrate = elapsed_ms(c->ev[2], c->ev[3]);
   S.ms_gradient = elapsed_ms(c->ev[3], c->ev[5]);
-  S.wide_tile = 0;
   S.ms_last = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
                   .count();
   if (S.n_bad) return bad_pairs_error(c);

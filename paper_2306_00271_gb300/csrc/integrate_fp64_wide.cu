@@ -96,7 +96,9 @@ struct WideArgs {
 
 // One kick with coefficient hb and (if do_drift) the drift with ha, for the table in shared
 // memory.
-template <int TB>
+// HERM (the kick's adjoint, Qbar <- Qbar - c (U^H + Gamma^2) Pbar, called with Q = Pbar and
+// P = Qbar): U's tile is gathered transposed and conjugated, (U^H)_jk = conj(u_{l(k, j)}).
+template <int TB, bool HERM = false>
 __device__ __forceinline__ void wide_kick(WideSmem& S, const double2* tbl, const int* lmap, double2* Q, double2* P,
                           int N, double hb, double ha, bool do_drift) {
   using T = Tile<TB>;
@@ -116,9 +118,9 @@ __device__ __forceinline__ void wide_kick(WideSmem& S, const double2* tbl, const
           const int gr = ib * TB + r, gk = kb * TB + k, gc = jb * TB + k;
           double ur = 0.0, ui = 0.0;
           if (gr < N && gk < N) {
-            const double2 v = tbl[__ldg(lmap + gr * N + gk)];
+            const double2 v = tbl[__ldg(lmap + (HERM ? gk * N + gr : gr * N + gk))];
             ur = v.x;
-            ui = v.y;
+            ui = HERM ? -v.y : v.y;
           }
           S.Ar[r * TLD + k] = ur;
           S.Ai[r * TLD + k] = ui;
@@ -590,6 +592,18 @@ __device__ __forceinline__ void wide_conventional(WideSmem& S, double2* tbl, con
   __syncthreads();
 }
 
+// [Q; P] into checkpoint slot `slot` of the pair (layout of IntegrateParams::ckpt).
+__device__ __forceinline__ void wide_store_ckpt(const IntegrateParams& p, size_t pair, int slot,
+                                                const double2* Q, const double2* P, int N) {
+  const size_t NN = (size_t)N * N;
+  double2* dst = p.ckpt + (pair * p.n_ckpt + slot) * 2 * NN;
+  for (size_t e = threadIdx.x; e < NN; e += WT) {
+    dst[e] = Q[e];
+    dst[NN + e] = P[e];
+  }
+  __syncthreads();
+}
+
 // Integrates one (set, angle) pair of `p` with its state block Z (Q, P and, for RK4, four more
 // N x N scratch matrices).
 template <int TB>
@@ -640,6 +654,7 @@ __device__ __forceinline__ void wide_pair(WideSmem& S, double2* tbl, const Integ
   const int s = p.sch.s;
   if (S.status == kOk) {
     for (int i = 0; i < p.L && S.status == kOk; ++i) {
+      if (p.ckpt && i % p.ckpt_every == 0) wide_store_ckpt(p, pair, i / p.ckpt_every, Q, P, N);
       if (p.method == kMethodRK4) {
         wide_rk4_step<TB>(S, tbl, p, set, i, Q, P);
       } else {
@@ -670,6 +685,7 @@ __device__ __forceinline__ void wide_pair(WideSmem& S, double2* tbl, const Integ
       __syncthreads();
       wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * p.sch.b[s], 0.0, false);
     }
+    if (p.ckpt) wide_store_ckpt(p, pair, p.n_ckpt - 1, Q, P, N);  // seeds the reverse sweep
   }
   wide_assemble(S, p, pair, Q, P);
   if (tid == 0) p.out.n_rhst[pair] = S.n_rhst;
@@ -731,6 +747,330 @@ __global__ void __launch_bounds__(WT, 1) k_assemble_wide(IntegrateParams p, int 
   wide_assemble(S, p, pair, state + lp * 2 * NN, state + lp * 2 * NN + NN);
 }
 
+
+// ---- reverse sweep for wide beam sets (64 < N <= 256), one CTA per (set, angle) pair ---------
+// The reverse map of adjoint_fp64.cu (its header states it) with the state in global memory and
+// every N x N product on this file's DMMA tiles: per segment of C steps, k_grad_wide_recompute
+// reruns the forward from its checkpoint (the same device code as wide_pair, so the same
+// trajectory bit for bit) storing Q at every kick and (Q before, P after) of every RHST;
+// k_grad_wide_adjoint then runs the reverse map over the segment and contracts
+// Ubar_n = -c_n Pbar Q_n^H with the potential's derivatives at every kick.
+// Scratch per pair: W = 4 N x N (Q, P in the recompute; Qbar, Pbar, T1, T2 in the adjoint).
+
+__device__ __forceinline__ double wide_kick_coef(const Scheme& sch, double h, int L, int n) {
+  const int s = sch.s;
+  if (n == s * L) return h * sch.b[s];
+  const int i = n / s, r = n - i * s;
+  if (r > 0) return h * sch.b[r];
+  return (i == 0) ? h * sch.b[0] : h * (sch.b[s] + sch.b[0]);
+}
+
+__device__ __forceinline__ void wide_copy(double2* dst, const double2* src, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t e = threadIdx.x; e < NN; e += WT) dst[e] = src[e];
+  __syncthreads();
+}
+
+// dst = src^H (conjugate transpose; N x N row-major; dst must not alias src)
+__device__ __forceinline__ void wide_herm(double2* dst, const double2* src, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t e = threadIdx.x; e < NN; e += WT) {
+    const int r = (int)(e / N), c = (int)(e - (size_t)r * N);
+    const double2 v = src[(size_t)c * N + r];
+    dst[e] = make_double2(v.x, -v.y);
+  }
+  __syncthreads();
+}
+
+struct WideGradArgs {
+  GradParams g;
+  double2* W;   // [pairs][4][N][N] scratch
+};
+
+// Dynamic shared memory of the reverse-sweep kernels: WideSmem, the node table tbl[M], the
+// accumulator ubar[M] of the contraction and acc[2 n_active].
+__host__ __device__ inline size_t wide_grad_smem(int M, int n_active) {
+  return kTblOffset + 2 * (size_t)M * sizeof(double2) + 2 * (size_t)n_active * sizeof(double);
+}
+
+template <int TB>
+__global__ void __launch_bounds__(WT, 1) k_grad_wide_recompute(WideGradArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
+  double2* tbl = reinterpret_cast<double2*>(smem_raw + kTblOffset);
+  const GradParams& g = a.g;
+  const IntegrateParams& p = g.ip;
+  const int angle = blockIdx.x, set = blockIdx.y, tid = threadIdx.x, N = p.N;
+  const size_t pair = (size_t)set * p.ang.n_angles + angle;
+  if (g.status[pair] != kOk) return;
+  const size_t NN = (size_t)N * N;
+  const int s = p.sch.s, C = p.ckpt_every;
+  const int i0 = g.seg * C, i1 = min(i0 + C, p.L);
+  if (tid == 0) S.status = kOk;
+  __syncthreads();
+  wide_gamma(S, p, angle);
+  double2* Q = a.W + pair * 4 * NN;
+  double2* P = Q + NN;
+  const double2* ck = p.ckpt + (pair * p.n_ckpt + g.seg) * 2 * NN;
+  wide_copy(Q, ck, N);
+  wide_copy(P, ck + NN, N);
+  double2* segQ = g.segQ + pair * g.kseg * NN;
+  double2* segR = g.segR + pair * C * 2 * NN;
+  for (int i = i0; i < i1 && S.status == kOk; ++i) {
+    for (int r = 0; r < s; ++r) {
+      const int n = s * i + r;
+      wide_copy(segQ + (size_t)(n - s * i0) * NN, Q, N);
+      const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
+      load_table(tbl, p, set, n);
+      __syncthreads();
+      wide_kick<TB>(S, tbl, p.lmap, Q, P, N, p.h * coef, p.h * p.sch.a[r], true);
+    }
+    wide_badness(S, Q, N, p.threshold);
+    const int c = i - i0;
+    const bool flag = S.flag != 0;
+    if (flag) {
+      wide_copy(segR + (size_t)(2 * c) * NN, Q, N);
+      wide_gauss_jordan(S, Q, P, N);
+      if (S.status != kOk) break;
+      for (size_t e = tid; e < NN; e += WT) {
+        const int rr = (int)(e / N), cc = (int)(e - (size_t)rr * N);
+        Q[e] = make_double2(rr == cc ? 1.0 : 0.0, 0.0);
+      }
+      __syncthreads();
+      wide_copy(segR + (size_t)(2 * c + 1) * NN, P, N);
+    }
+    if (tid == 0) g.rflag[pair * C + c] = flag ? 1 : 0;
+    __syncthreads();
+  }
+  if (S.status == kOk && i1 == p.L) wide_copy(segQ + (size_t)(s * (i1 - i0)) * NN, Q, N);
+  if (tid == 0 && S.status != kOk) g.status[pair] = S.status;
+}
+
+// Ubar_n = -c Pbar Q_n^H reduced to the distinct differences (ubar_m = sum over l(j, k) = m of
+// Ubar_jk, Eq. sch2) and contracted with the z- and B-derivatives of the potential model at the
+// node tau (as k_grad_ubar of adjoint_fp64.cu); accumulates into acc[2 n_active]. T1, T2 scratch.
+template <int TB>
+__device__ __forceinline__ void wide_contract(WideSmem& S, double* ubar, double* acc,
+                                              const GradParams& g, int set, const double2* Pb,
+                                              const double2* Qn, double c, double tau,
+                                              double2* T1, double2* T2) {
+  const IntegrateParams& p = g.ip;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = p.N, M = p.M;
+  wide_herm(T2, Qn, N);
+  wide_gmm<TB>(S, Pb, T2, T1, nullptr, N);           // Pbar Q^H
+  double* ur = ubar;
+  double* ui = ubar + M;
+  for (int m = tid; m < M; m += WT) ur[m] = ui[m] = 0.0;
+  __syncthreads();
+  const size_t NN = (size_t)N * N;
+  for (size_t e = tid; e < NN; e += WT) {
+    const int m = __ldg(p.lmap + e);
+    const double2 v = T1[e];
+    atomicAdd(ur + m, v.x);
+    atomicAdd(ui + m, v.y);
+  }
+  __syncthreads();
+  const int T = 4 * g.n_atoms;
+  const double2* Fs = g.F + (size_t)set * T * M;
+  constexpr double k16pi2 = 16.0 * kPiW * kPiW;
+  for (int w = warp; w < 4 * g.n_active; w += WT / 32) {
+    const int ai = w >> 2, i = w & 3;
+    const int a = g.active[ai];
+    const double2* Ft = Fs + (size_t)(4 * a + i) * M;
+    double v = 0.0, vg = 0.0;   // Re sum_m conj(ubar_m) pref F_m, and with |g_m|^2
+    for (int m = lane; m < M; m += 32) {
+      const double2 f = Ft[m];
+      const double fr = g.pref.x * f.x - g.pref.y * f.y, fi = g.pref.x * f.y + g.pref.y * f.x;
+      const double re = ur[m] * fr + ui[m] * fi;
+      const double2 gm = g.gdiff[m];
+      v += re;
+      vg += re * (gm.x * gm.x + gm.y * gm.y);
+    }
+    v = -c * wsum(v);
+    vg = -c * wsum(vg);
+    if (lane == 0) {
+      const double za = g.atoms[((size_t)set * g.n_atoms + a) * 3 + 2];
+      const double B = g.dw[(size_t)set * g.n_atoms + a];
+      const double beta = (g.sf[8 * g.species[a] + 4 + i] + B) / k16pi2;
+      const double d = tau - za;
+      const double G = exp(-d * d / (4.0 * beta));
+      atomicAdd(acc + 2 * ai, v * G * d / (2.0 * beta));
+      atomicAdd(acc + 2 * ai + 1,
+                (v * G * (d * d / (4.0 * beta * beta) - 0.5 / beta) - vg * G) / k16pi2);
+    }
+  }
+  __syncthreads();
+}
+
+// Adjoint seed from the final state (Qf, Pf): Qbar, Pbar of eta_1 = |rho_1|^2 sin(theta0) with
+// rho = B x, A x = e_1, A = Gamma Q - i P, B = Gamma Q + i P; A^{-1} by Gauss-Jordan into T2.
+__device__ __forceinline__ void wide_seed(WideSmem& S, const double2* Qf, const double2* Pf,
+                                          double2* Qb, double2* Pb, double2* T1, double2* T2,
+                                          int N) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t NN = (size_t)N * N;
+  for (size_t e = tid; e < NN; e += WT) {
+    const int j = (int)(e / N), k = (int)(e - (size_t)j * N);
+    const double2 q = Qf[e], pv = Pf[e];
+    T1[e] = make_double2(S.Gr[j] * q.x - S.Gi[j] * q.y + pv.y, S.Gr[j] * q.y + S.Gi[j] * q.x - pv.x);
+    T2[e] = make_double2(j == k ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  wide_gauss_jordan(S, T1, T2, N);                                 // T2 = A^{-1}
+  if (S.status != kOk) return;
+  double* xr = S.cr;
+  double* xi = S.ci;
+  double* ybr = S.cr + NW;
+  double* ybi = S.ci + NW;
+  for (int k = tid; k < N; k += WT) {                              // x = A^{-1} e_1
+    const double2 v = T2[(size_t)k * N];
+    xr[k] = v.x;
+    xi[k] = v.y;
+  }
+  __syncthreads();
+  double rr = 0.0, ri = 0.0;                                       // rho_1 = (B x)_1
+  for (int k = tid; k < N; k += WT) {
+    const double2 q = Qf[k], pv = Pf[k];
+    const double br = S.Gr[0] * q.x - S.Gi[0] * q.y - pv.y;
+    const double bi = S.Gr[0] * q.y + S.Gi[0] * q.x + pv.x;
+    rr += br * xr[k] - bi * xi[k];
+    ri += br * xi[k] + bi * xr[k];
+  }
+  rr = wsum(rr);
+  ri = wsum(ri);
+  if (lane == 0) {
+    S.red0[warp] = rr;
+    S.red1[warp] = ri;
+  }
+  __syncthreads();
+  double rbr = 0.0, rbi = 0.0;
+  for (int w = 0; w < WT / 32; ++w) {
+    rbr += S.red0[w];
+    rbi += S.red1[w];
+  }
+  rbr *= 2.0 * S.sin_t0;                                           // rhobar_1
+  rbi *= 2.0 * S.sin_t0;
+  for (int k = tid; k < N; k += WT) {                              // xbar_k = conj(B_1k) rhobar_1
+    const double2 q = Qf[k], pv = Pf[k];
+    const double br = S.Gr[0] * q.x - S.Gi[0] * q.y - pv.y;
+    const double bi = S.Gr[0] * q.y + S.Gi[0] * q.x + pv.x;
+    ybr[k] = br * rbr + bi * rbi;
+    ybi[k] = br * rbi - bi * rbr;
+  }
+  __syncthreads();
+  for (int j = tid; j < N; j += WT) {                              // bbar = A^{-H} xbar
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < N; ++k) {
+      const double2 v = T2[(size_t)k * N + j];                     // conj(Ainv_kj) xbar_k
+      sr += v.x * ybr[k] + v.y * ybi[k];
+      si += v.x * ybi[k] - v.y * ybr[k];
+    }
+    S.fr[j] = sr;
+    S.fi[j] = si;
+  }
+  __syncthreads();
+  for (size_t e = tid; e < NN; e += WT) {
+    const int j = (int)(e / N), k = (int)(e - (size_t)j * N);
+    const double cxr = xr[k], cxi = -xi[k];                        // conj(x_k)
+    const double abr = -(S.fr[j] * cxr - S.fi[j] * cxi);           // Abar_jk = -bbar_j conj(x_k)
+    const double abi = -(S.fr[j] * cxi + S.fi[j] * cxr);
+    double bbr = 0.0, bbi = 0.0;                                   // Bbar_jk = d_j1 rhobar conj(x_k)
+    if (j == 0) {
+      bbr = rbr * cxr - rbi * cxi;
+      bbi = rbr * cxi + rbi * cxr;
+    }
+    const double sr = abr + bbr, si = abi + bbi;
+    Qb[e] = make_double2(S.Gr[j] * sr + S.Gi[j] * si, S.Gr[j] * si - S.Gi[j] * sr);
+    Pb[e] = make_double2(-(abi - bbi), abr - bbr);                 // i (Abar - Bbar)
+  }
+  __syncthreads();
+}
+
+template <int TB>
+__global__ void __launch_bounds__(WT, 1) k_grad_wide_adjoint(WideGradArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WideSmem& S = *reinterpret_cast<WideSmem*>(smem_raw);
+  const GradParams& g = a.g;
+  const IntegrateParams& p = g.ip;
+  double2* tbl = reinterpret_cast<double2*>(smem_raw + kTblOffset);
+  double* ubar = reinterpret_cast<double*>(tbl + p.M);
+  double* acc = ubar + 2 * p.M;
+  const int angle = blockIdx.x, set = blockIdx.y, tid = threadIdx.x, N = p.N;
+  const size_t pair = (size_t)set * p.ang.n_angles + angle;
+  if (g.status[pair] != kOk) return;
+  const size_t NN = (size_t)N * N;
+  const int s = p.sch.s, C = p.ckpt_every;
+  const int i0 = g.seg * C, i1 = min(i0 + C, p.L);
+  const bool last = (i1 == p.L);
+  if (tid == 0) S.status = kOk;
+  for (int e = tid; e < 2 * g.n_active; e += WT) acc[e] = 0.0;
+  __syncthreads();
+  wide_gamma(S, p, angle);
+  double2* Qb = a.W + pair * 4 * NN;
+  double2* Pb = Qb + NN;
+  double2* T1 = Qb + 2 * NN;
+  double2* T2 = Qb + 3 * NN;
+  double2* az = g.adjZ + pair * 2 * NN;
+  const double2* segQ = g.segQ + pair * g.kseg * NN;
+  const double2* segR = g.segR + pair * C * 2 * NN;
+  if (last) {
+    const double2* fin = p.ckpt + (pair * p.n_ckpt + p.n_ckpt - 1) * 2 * NN;
+    wide_seed(S, fin, fin + NN, Qb, Pb, T1, T2, N);
+    if (S.status == kOk) {                       // the final kick (no drift after it)
+      const int n = s * p.L;
+      const double c = wide_kick_coef(p.sch, p.h, p.L, n);
+      wide_contract<TB>(S, ubar, acc, g, set, Pb, segQ + (size_t)(n - s * i0) * NN, c,
+                        g.node_z[n], T1, T2);
+      load_table(tbl, p, set, n);
+      __syncthreads();
+      wide_kick<TB, true>(S, tbl, p.lmap, Pb, Qb, N, c, 0.0, false);
+    }
+  } else {
+    wide_copy(Qb, az, N);
+    wide_copy(Pb, az + NN, N);
+  }
+  for (int i = i1 - 1; i >= i0 && S.status == kOk; --i) {
+    const int cs = i - i0;
+    if (g.rflag[pair * C + cs]) {
+      // RHST adjoint: project onto Zbar^H Z = 0 (Qbar = -X^H Pbar, X = P after the transform),
+      // then Zbar <- Zbar Q_pre^{-H}
+      const double2* rec = segR + (size_t)(2 * cs) * NN;
+      wide_herm(T1, rec + NN, N);
+      wide_gmm<TB>(S, T1, Pb, Qb, nullptr, N);
+      for (size_t e = tid; e < NN; e += WT) Qb[e] = make_double2(-Qb[e].x, -Qb[e].y);
+      __syncthreads();
+      wide_herm(T1, rec, N);
+      wide_gauss_jordan(S, T1, Qb, N);
+      if (S.status != kOk) break;
+      wide_herm(T1, rec, N);
+      wide_gauss_jordan(S, T1, Pb, N);
+      if (S.status != kOk) break;
+    }
+    for (int r = s - 1; r >= 0; --r) {
+      const int n = s * i + r;
+      const double d = p.h * p.sch.a[r];
+      for (size_t e = tid; e < NN; e += WT) {    // drift adjoint
+        const double2 pv = Pb[e], qv = Qb[e];
+        Pb[e] = make_double2(pv.x + d * qv.x, pv.y + d * qv.y);
+      }
+      __syncthreads();
+      const double c = wide_kick_coef(p.sch, p.h, p.L, n);
+      wide_contract<TB>(S, ubar, acc, g, set, Pb, segQ + (size_t)(n - s * i0) * NN, c,
+                        g.node_z[n], T1, T2);
+      load_table(tbl, p, set, n);
+      __syncthreads();
+      wide_kick<TB, true>(S, tbl, p.lmap, Pb, Qb, N, c, 0.0, false);
+    }
+  }
+  if (S.status == kOk) {
+    wide_copy(az, Qb, N);
+    wide_copy(az + NN, Pb, N);
+  }
+  for (int e = tid; e < 2 * g.n_active; e += WT) g.jac_atoms[pair * 2 * g.n_active + e] += acc[e];
+  __syncthreads();
+  if (tid == 0 && S.status != kOk) g.status[pair] = S.status;
+}
+
 }  // namespace
 
 cudaError_t launch_assemble_wide(const IntegrateParams& p, int set0, double2* state,
@@ -784,6 +1124,33 @@ cudaError_t launch_integrate_fp64_wide_items(const IntegrateParams* jobs, const 
   else
     k_integrate_fp64_wide_items<32><<<n_ctas, WT, smem, st>>>(jobs, items, n_items, counter,
                                                                state, slot_elems);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+size_t wide_grad_smem_bytes(int M, int n_active) { return wide_grad_smem(M, n_active); }
+
+cudaError_t launch_grad_wide(const GradParams& g, double2* W, int tile, bool recompute,
+                             cudaStream_t st, int* n_launched) {
+  const size_t smem = wide_grad_smem(g.ip.M, g.n_active);
+  if (smem > 227 * 1024 || g.ip.N > NW || (tile != 32 && tile != 64) || !g.ip.ckpt)
+    return cudaErrorInvalidValue;
+  const void* fn;
+  if (recompute)
+    fn = tile == 64 ? (const void*)k_grad_wide_recompute<64> : (const void*)k_grad_wide_recompute<32>;
+  else
+    fn = tile == 64 ? (const void*)k_grad_wide_adjoint<64> : (const void*)k_grad_wide_adjoint<32>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  WideGradArgs a{g, W};
+  const dim3 grid(g.ip.ang.n_angles, g.ip.n_sets);
+  if (recompute) {
+    if (tile == 64) k_grad_wide_recompute<64><<<grid, WT, smem, st>>>(a);
+    else k_grad_wide_recompute<32><<<grid, WT, smem, st>>>(a);
+  } else {
+    if (tile == 64) k_grad_wide_adjoint<64><<<grid, WT, smem, st>>>(a);
+    else k_grad_wide_adjoint<32><<<grid, WT, smem, st>>>(a);
+  }
   if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }

@@ -19,8 +19,8 @@
 // buffers; consumer warp r (r < 4) issues the MMAs of row tile r's stages as soon as their
 // producers have arrived on the stage's "full" mbarrier, and the MMA completion
 // (tcgen05.commit) on the stage's "empty" mbarrier hands the buffer back. The four issuing warps
-// run at once: with products this narrow (N <= 64) the time an issuing thread spends per MMA, not
-// the tensor core, sets the pace. Entry (2j+p, 2k+q) of
+// run at once (one issuing warp measured the same: the tile production and the MMAs' operand
+// reads, both through this SM's shared memory, set the pace, not the issue). Entry (2j+p, 2k+q) of
 // the real-ified A is [[Re u, -Im u], [Im u, Re u]][p][q]; the digits of -Im u are those of Im u
 // with the BF16 sign bit flipped. The node's scale (a power of two >= every |Re u|, |Im u|) makes
 // every digit product exact, as for N <= 128.

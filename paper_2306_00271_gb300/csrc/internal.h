@@ -213,6 +213,13 @@ cudaError_t launch_grad_recompute(const GradParams& g, cudaStream_t st, int* n_l
 cudaError_t launch_grad_adjoint(const GradParams& g, cudaStream_t st, int* n_launched);
 cudaError_t launch_grad_ubar(const GradParams& g, cudaStream_t st, int* n_launched);
 cudaError_t launch_rfactor(const RFactorParams& r, cudaStream_t st, int* n_launched);
+// Reverse sweep for 64 < N <= 256 (integrate_fp64_wide.cu): one segment's recompute (recompute =
+// true; state, Q at every kick and the RHST records) or adjoint with the contraction folded in
+// (g.segPb unused). W: [pairs][4][N][N] complex128 scratch; tile: the forward's tile edge (the
+// recompute must follow the same trajectory bit for bit).
+cudaError_t launch_grad_wide(const GradParams& g, double2* W, int tile, bool recompute,
+                             cudaStream_t st, int* n_launched);
+size_t wide_grad_smem_bytes(int M, int n_active);
 
 cudaError_t launch_potential(const PotentialParams& p, cudaStream_t st, int* n_launched);
 cudaError_t launch_umma_images(const MixedImageParams& p, cudaStream_t st, int* n_launched);

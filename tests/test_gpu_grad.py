@@ -169,3 +169,41 @@ def test_mixed_forward_gradient(api):
     assert _rel(g, gold["grad"]) <= TOL, _rel(g, gold["grad"])
     st = eng.stats()
     assert st["ms_integrate"] < 1000.0      # the forward ran on the mixed path
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_wide_jacobian_matches_oracle_differences(api, precision):
+    """70 beams (64 < N <= 256): the wide reverse sweep (state in global memory, products on the
+    FP64 tensor pipe in tiles, the contraction folded into the adjoint kernel) against the
+    oracle's central differences, with a ragged last segment. On a mixed context the forward of a
+    gradient above 64 beams also runs in binary64, so both precisions give this Jacobian."""
+    wl = W.tiny(n_beams=70, n_steps=60, seed=33, depth=6.0, theta0=(0.8, 2.2, 3.5))
+    free, cls = np.array([0, 1, 2, 3]), np.array([0, 1, 1, 0])
+    eng = api.Engine(wl, precision, "sp4")
+    eng.set_fit(free, cls, ckpt_every=16)
+    eta, jac = eng.curve_jacobian(wl.theta0, wl.theta1)
+    fd = G.fd_gradient(wl, free, cls, target=np.ones(len(wl.theta0)))
+    jac = jac.cpu().numpy()[0]
+    assert _rel(jac, fd["jac"]) <= 1e-6, _rel(jac, fd["jac"])
+    assert np.allclose(eta.cpu().numpy()[0][:, 0], fd["eta1"], rtol=1e-10, atol=0)
+    st = eng.stats()
+    assert st["rhst_total"] > 0 and st["ms_gradient"] > 0 and st["wide_tile"] in (32, 64)
+    eng.set_fit(free, cls, ckpt_every=7)
+    jac7 = eng.curve_jacobian(wl.theta0, wl.theta1)[1].cpu().numpy()[0]
+    assert _rel(jac7, jac) <= 1e-12
+
+
+def test_wide_rfactor_gradient(api):
+    """The R-factor and its gradient through trh_rfactor_grad at 91 beams against the oracle's
+    central differences of R."""
+    wl = W.tiny(n_beams=91, n_steps=40, seed=35, depth=5.0, theta0=(0.9, 1.8, 2.6, 3.9))
+    free, cls = np.array([1, 3]), np.array([0, 0, 1, 1])
+    target = np.array([0.2, 0.3, 0.25, 0.25])
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_fit(free, cls, ckpt_every=16)
+    R, gz, gb = eng.rfactor_grad(wl.theta0, wl.theta1, target)
+    fd = G.fd_gradient(wl, free, cls, target=target)
+    got = np.concatenate([np.asarray(gz.cpu()).ravel(), np.asarray(gb.cpu()).ravel()])
+    want = fd["grad"]
+    assert float(np.asarray(R.cpu()).ravel()[0]) == pytest.approx(fd["R"], rel=1e-10)
+    assert _rel(got, want) <= 1e-5, _rel(got, want)
