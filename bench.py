@@ -368,6 +368,43 @@ def run_gradient(local: int, slices: int = 0, warmup: int = 1, path: str = "fp64
             "kernels_launched": st["kernels_launched"], "R": float(R[0])}
 
 
+def run_gradient_large(slices: int = 30, n_angles: int = 16):
+    """The 255-beam recipe's gradient on a stated sample: its first structure, n_angles of its
+    120 angles, the first `slices` slices of 0.01 A (a slab of slices * 0.01 A; the full 3000
+    would take the binary64 sweep tens of minutes), the z of its 8 surface atoms and 4
+    Debye-Waller classes of 2 of them as the 12 parameters, one checkpoint segment. Reports the
+    measured gradient time and its rate in angle-slices/s (not extrapolated)."""
+    import torch
+    from paper_2306_00271_gb300 import api
+    wl = W.large_n255(1)[0]
+    wl = replace(wl, z_e=-0.01 * slices).with_steps(slices)
+    wl = wl.with_angles(wl.theta0[np.linspace(0, len(wl.theta0) - 1, n_angles).astype(int)])
+    free = np.arange(8)
+    cls = np.full(wl.atoms.shape[0], -1)
+    cls[:8] = np.arange(8) // 2
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_fit(free, cls, ckpt_every=slices)
+    target = np.full(n_angles, 1.0 / n_angles)
+    eng.rfactor_grad(wl.theta0, wl.theta1, target)   # tables, tuner probe
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    R, gz, gb = eng.rfactor_grad(wl.theta0, wl.theta1, target)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = eng.stats()
+    eng.close()
+    return {"metric": "R-factor gradient, 255 beams (wide binary64 reverse sweep), 12 parameters",
+            "value": 1000.0 / ms, "unit": "gradients/s", "ms_per_gradient": ms,
+            "ms_forward": st["ms_integrate"], "ms_reverse": st["ms_gradient"],
+            "angle_slices_per_s": n_angles * slices / (ms / 1e3), "angles": n_angles,
+            "slices": slices, "sample": f"{n_angles} of 120 angles, first {slices} of 3000 "
+                                        "slices of 0.01 A, 1 of 64 structures",
+            "wide_tile": st["wide_tile"], "R": float(R[0])}
+
+
 def run_batches(slices: int = 0):
     """A small batched line: 8 perturbed structures (4 with 31 and 4 with 61 beams) x 60 angles
     on the mixed path at 2000 slices, one persistent launch replayed from its CUDA graph, timed
@@ -659,6 +696,8 @@ def main():
                                               eta_121_fp64=eta_ref)
         out["large_n255"] = run_large(2, args.slices)
         out["large_n255_fp64_sample"] = run_large_sample()
+        if not args.no_grad:
+            out["large_n255_gradient_sample"] = run_gradient_large()
         out["rheed_row_latency"] = rheed_row_latency()
     out["paper_context"] = PAPER_CONTEXT
     if ws == 1 and not args.no_cpu:

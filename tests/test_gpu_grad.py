@@ -207,3 +207,15 @@ def test_wide_rfactor_gradient(api):
     want = fd["grad"]
     assert float(np.asarray(R.cpu()).ravel()[0]) == pytest.approx(fd["R"], rel=1e-10)
     assert _rel(got, want) <= 1e-5, _rel(got, want)
+
+
+def test_wide_jacobian_150_beams(api):
+    """150 beams (three 64-column blocks with a ragged last one): the wide reverse sweep's
+    Jacobian against the oracle's central differences on a thin slab."""
+    wl = W.tiny(n_beams=150, n_steps=16, seed=37, depth=2.5, theta0=(1.1, 2.4))
+    free, cls = np.array([0]), np.array([0, 0, -1, -1])
+    eng = api.Engine(wl, "fp64", "sp4")
+    eng.set_fit(free, cls, ckpt_every=6)
+    _, jac = eng.curve_jacobian(wl.theta0, wl.theta1)
+    fd = G.fd_gradient(wl, free, cls, target=np.ones(len(wl.theta0)))
+    assert _rel(jac.cpu().numpy()[0], fd["jac"]) <= 1e-6
