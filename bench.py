@@ -214,10 +214,37 @@ def run_large(n_sets: int = 2, slices: int = 0, n_angles: int = 0):
 # + dram__bytes_write of a small case, divided by its node count; the traffic of these kernels is
 # proportional to the node count). Summaries: profiles/k_integrate_mixed_split_trhepd_n61_L400.md,
 # profiles/k_integrate_mixed_trhepd_n61_L400.md, profiles/k_integrate_fp64_split_trhepd_n61_L60.md
-# and profiles/k_integrate_fp64_trhepd_n61_L60.md.
-# Set to None when the kernel changes.
-TRAFFIC_PER_NODE = {"mixed_split": 324.232704e6 / 2401, "mixed": 325.20192e6 / 2401,
-                    "fp64_split": 1.504512e6 / 361, "fp64": 1.624832e6 / 361}
+# and profiles/k_integrate_fp64_trhepd_n61_L60.md. Each figure holds for the kernel sources it was
+# measured on: the hash of those files at capture time is stored beside it, and a figure whose
+# sources have changed since is reported as null (kernel_source_hash).
+KERNEL_SOURCES = {
+    "mixed": ("integrate_mixed.cu", "umma.cuh", "mixed_digits.cuh", "dense_fp64.cuh", "internal.h"),
+    "fp64": ("integrate_fp64.cu", "fp64_core.cuh", "internal.h"),
+}
+TRAFFIC_PER_NODE = {  # kernel: (bytes per node, sources, hash of the sources at capture)
+    "mixed_split": (324.232704e6 / 2401, "mixed", None),
+    "mixed": (325.20192e6 / 2401, "mixed", None),
+    "fp64_split": (1.504512e6 / 361, "fp64", None),
+    "fp64": (1.624832e6 / 361, "fp64", None),
+}
+
+
+def kernel_source_hash(group: str) -> str:
+    """sha256 (16 hex digits) of the CUDA sources a kernel family is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2306_00271_gb300",
+                        "csrc")
+    for name in KERNEL_SOURCES[group]:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_node(kernel: str):
+    """The captured DRAM bytes per node of `kernel`, or None when its sources changed since."""
+    per_node, group, captured = TRAFFIC_PER_NODE[kernel]
+    return per_node if captured is not None and captured == kernel_source_hash(group) else None
 
 
 # The paper's own timings (Table tab:times): another machine and another workload (Si(111)-7x7,
@@ -256,8 +283,7 @@ def run_ours(args):
     engines = {}
     for path in args.paths:
         engines[path] = api.Engine(wl, path, "sp4")
-        if path == "mixed":
-            engines[path].set_column_split(args.column_split)
+        engines[path].set_column_split(args.column_split)
     atoms_d = torch.tensor(wl.atoms, dtype=torch.float64, device=dev)
     dw_d = torch.tensor(wl.dw, dtype=torch.float64, device=dev)
     t0_d = torch.tensor(wl.theta0, dtype=torch.float64, device=dev)
@@ -582,8 +608,8 @@ def main():
     ap.add_argument("--config2-sets", type=int, default=512,
                     help="parameter sets of the batching recipe (512 = its stated size)")
     ap.add_argument("--column-split", default="auto", choices=["auto", "on", "off"],
-                    help="mixed path: two CTAs per angle (auto: when the angles fit on half "
-                         "the SMs)")
+                    help="two CTAs per angle (auto: the autotuner times both forms on probes "
+                         "of the call and keeps the faster)")
     ap.add_argument("--large-only", action="store_true",
                     help="only the 255-beam mixed line (profiling cases with --slices and "
                          "--large-angles; not the bench line)")
@@ -649,7 +675,7 @@ def main():
     if paths[0] == "mixed":
         peak = peaks.get("bf16_tflops", 1900.0)
         kern = "mixed_split" if head["column_split"] else "mixed"
-        tpn = TRAFFIC_PER_NODE[kern]
+        tpn = traffic_per_node(kern)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": None if tpn is None else tpn * (6 * L + 1),
@@ -658,7 +684,7 @@ def main():
     else:
         bf = peaks.get("bf16_tflops", 1900.0)
         peak = bf * 1.25 / 2250.0
-        tpn = TRAFFIC_PER_NODE["fp64_split" if head["column_split"] else "fp64"]
+        tpn = traffic_per_node("fp64_split" if head["column_split"] else "fp64")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": None if tpn is None else tpn * (6 * L + 1),

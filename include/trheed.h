@@ -134,9 +134,9 @@ typedef struct trh_stats {
                              sets' digit images are built for one chunk at a time, at most
                              40 GiB of them; 1 when every set fits)                            */
   int tuned;              /* 1 if the launch shape of the last call (column_split, wide_tile) was
-                             chosen by the autotuner: the candidate shapes timed on a 2-step
-                             probe of the call's own pairs, the fastest kept per (precision, N,
-                             integrator, pair count) for the life of the process; 0 for a fixed
+                             chosen by the autotuner: the candidate shapes timed on short
+                             probes of the call's own pairs, the fastest kept per (precision, N,
+                             integrator, pair count, L) for the life of the process; 0 for a fixed
                              rule (a forced split mode, more pairs than SMs, N <= 32, a mixed
                              cluster of ceil(N / 32) or ceil(N / 16) CTAs)                      */
 } trh_stats;
@@ -211,8 +211,8 @@ int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* d
  * halves of Q and P at every RHST (Section 3.2: both CTAs hold the whole [Q; P] for it) and at
  * the end (CTA 0 assembles rho). This shortens a pair's critical path but takes two SMs per pair:
  * TRH_SPLIT_AUTO (the default) lets the autotuner choose when N > 32 and the call has at most
- * as many pairs as SMs (both forms timed on a 2-step probe of the call's pairs, the faster kept
- * for that shape; trh_stats.tuned), TRH_SPLIT_OFF never splits, TRH_SPLIT_ON whenever N > 32
+ * as many pairs as SMs (both forms timed on probes of the call's pairs at 2 and 12 steps, their
+ * times at the call's L extrapolated, the faster kept for that shape; trh_stats.tuned), TRH_SPLIT_OFF never splits, TRH_SPLIT_ON whenever N > 32
  * (trh_curve_jacobian's forward splits when its pairs fit on half the SMs). Results are identical either way:
  * every column sees the same arithmetic, and the row sums are added in the same fixed order, so
  * the RHST decisions coincide. Batches (trh_batch_*) always run one CTA per pair. A wait for the

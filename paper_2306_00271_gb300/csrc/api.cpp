@@ -878,7 +878,7 @@ static float probe_ms(trh_ctx* c, cudaStream_t st, F launch) {
 // and the larger tile has less overhead.
 static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* state,
                           cudaStream_t st, int* tile) {
-  const trh::tune::Key key{trh::tune::kWideTile, c->precision, c->N, ip.method, 1};
+  const trh::tune::Key key{trh::tune::kWideTile, c->precision, c->N, ip.method, 1, 2};
   if (g_tune.find(key, tile)) return TRH_OK;
   trh::IntegrateParams pp = ip;
   pp.L = ip.L < 2 ? ip.L : 2;
@@ -896,9 +896,12 @@ static int tune_wide_tile(trh_ctx* c, const trh::IntegrateParams& ip, double2* s
 }
 
 // One CTA per (set, angle) pair or two sharing its columns (mixed path and FP64 path with
-// N <= 64): a forced mode, or (AUTO) the faster of the two forms on a 2-step probe of this call's
-// pairs (cached per precision, N, integrator and pair count). The two forms give the same bits.
-// With more pairs than SMs the split only adds waves, so no probe runs.
+// N <= 64): a forced mode, or (AUTO) the faster of the two forms for this call: each form timed on
+// probes of this call's pairs at 2 and 12 steps and its time at the call's L steps extrapolated
+// (tune::extrapolate; a 2-step probe alone is dominated by the launch's set-up, where the one-CTA
+// form is cheaper, while the split shortens every step), cached per precision, N, integrator, pair
+// count and L. The two forms give the same bits. With more pairs than SMs the split only adds
+// waves, so no probe runs.
 static int choose_split(trh_ctx* c, const trh::IntegrateParams& ip, size_t pairs,
                         cudaStream_t st, int* launched, bool* split, bool* tuned) {
   *split = false;
@@ -916,26 +919,39 @@ static int choose_split(trh_ctx* c, const trh::IntegrateParams& ip, size_t pairs
   TRH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (pairs > (size_t)sms) return TRH_OK;
   const trh::tune::Key key{trh::tune::kColumnSplit, c->precision, c->N, c->integrator,
-                           (long long)pairs};
+                           (long long)pairs, (long long)c->L};
   int v = 0;
   if (!g_tune.find(key, &v)) {
+    const int L1 = c->L < 2 ? c->L : 2, L2 = c->L < 12 ? c->L : 12;
     float ms[2];
     if (mixed_small) {
       const int ns = std::min(mixed_chunk_sets(c), c->n_sets);
       const int rc = ensure_images(c, 0, ns, st, launched);
       if (rc != TRH_OK) return rc;
       trh::MixedParams mp = mixed_params(c, ip);
-      mp.L = c->L < 2 ? c->L : 2;
       mp.n_sets = ns;
       mp.ckpt = nullptr;
-      for (int i = 0; i < 2; ++i)
-        ms[i] = probe_ms(c, st, [&] { return trh::launch_integrate_mixed(mp, i == 1, st, nullptr); });
+      for (int i = 0; i < 2; ++i) {
+        mp.L = L1;
+        const float t1 = probe_ms(c, st, [&] { return trh::launch_integrate_mixed(mp, i == 1, st, nullptr); });
+        mp.L = L2;
+        const float t2 = L2 > L1 ? probe_ms(c, st, [&] {
+          return trh::launch_integrate_mixed(mp, i == 1, st, nullptr);
+        }) : t1;
+        ms[i] = trh::tune::extrapolate(t1, L1, t2, L2, c->L);
+      }
     } else {
       trh::IntegrateParams pp = ip;
-      pp.L = ip.L < 2 ? ip.L : 2;
       pp.ckpt = nullptr;
-      for (int i = 0; i < 2; ++i)
-        ms[i] = probe_ms(c, st, [&] { return trh::launch_integrate_fp64(pp, i == 1, st, nullptr); });
+      for (int i = 0; i < 2; ++i) {
+        pp.L = L1;
+        const float t1 = probe_ms(c, st, [&] { return trh::launch_integrate_fp64(pp, i == 1, st, nullptr); });
+        pp.L = L2;
+        const float t2 = L2 > L1 ? probe_ms(c, st, [&] {
+          return trh::launch_integrate_fp64(pp, i == 1, st, nullptr);
+        }) : t1;
+        ms[i] = trh::tune::extrapolate(t1, L1, t2, L2, c->L);
+      }
     }
     v = trh::tune::pick(ms, 2, 0.02f);
     g_tune.put(key, v);

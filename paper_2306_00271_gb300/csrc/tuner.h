@@ -32,8 +32,15 @@ inline int pick(const float* ms, int n, float rel_margin) {
   return best < 0 ? 0 : best;
 }
 
-// (kind, precision, N, method, pairs per launch): the shape a probe's result holds for.
-using Key = std::tuple<int, int, int, int, long long>;
+// (kind, precision, N, method, pairs per launch, steps): the shape a probe's result holds for.
+using Key = std::tuple<int, int, int, int, long long, long long>;
+
+// Time of a launch of L steps from probes of L1 < L2 steps (launch overhead plus a per-step cost,
+// so that a short probe does not favour the shape with the cheaper set-up).
+inline float extrapolate(float t1, int L1, float t2, int L2, int L) {
+  if (!(t1 > 0.0f) || !(t2 > 0.0f) || L2 <= L1) return t1;
+  return t1 + (t2 - t1) * (float)(L - L1) / (float)(L2 - L1);
+}
 
 class Cache {
  public:

@@ -156,3 +156,13 @@ def test_autotuned_split_matches_both_forms(api, precision):
     assert out["off"][1]["column_split"] == 0 and out["on"][1]["column_split"] == 1
     assert np.array_equal(out["off"][0], out["on"][0])
     assert np.array_equal(out["auto"][0], out["off"][0])
+
+
+def test_autotuner_picks_the_split_for_a_long_curve(api):
+    """60 angles of 61 beams at 400 slices: the two-CTA form is about 1.7x faster per step there,
+    and the tuner, extrapolating its 2- and 12-step probes to the call's 400 steps, picks it."""
+    wl = W.trhepd_n61().with_steps(400)
+    eng = api.Engine(wl, "mixed", "sp4")
+    eng.rocking_curve(wl.theta0, wl.theta1)
+    st = eng.stats()
+    assert st["tuned"] == 1 and st["column_split"] == 1

@@ -1,6 +1,7 @@
 """The autotuner's selection rule and cache (paper_2306_00271_gb300/csrc/tuner.h), compiled with the
 host C++ compiler and run on the CPU: the earliest (cheapest) candidate wins unless a later one
-is faster by more than the margin, failed probes never win, and choices are cached per shape key."""
+is faster by more than the margin, failed probes never win, choices are cached per shape key, and
+a call's time is extrapolated from probes of two step counts."""
 import os
 import shutil
 import subprocess
@@ -28,18 +29,23 @@ int main() {
   { const float m[3] = {1.0f, 0.5f, 0.49f}; std::printf("%d\n", pick(m, 3, 0.05f)); } // 1
   Cache c;
   int v = -1;
-  const Key a{kColumnSplit, 1, 61, 0, 60}, b{kColumnSplit, 1, 61, 0, 120}, t{kWideTile, 0, 61, 0, 60};
+  const Key a{kColumnSplit, 1, 61, 0, 60, 2000}, b{kColumnSplit, 1, 61, 0, 120, 2000},
+      t{kWideTile, 0, 61, 0, 60, 2000}, a400{kColumnSplit, 1, 61, 0, 60, 400};
   std::printf("%d\n", (int)c.find(a, &v));                                        // 0
   c.put(a, 1);
   c.put(t, 32);
   { const int f = c.find(a, &v); std::printf("%d %d\n", f, v); }                // 1 1
   std::printf("%d\n", (int)c.find(b, &v));                                        // 0: other pair count
+  std::printf("%d\n", (int)c.find(a400, &v));                                     // 0: other step count
   { const int f = c.find(t, &v); std::printf("%d %d\n", f, v); }                // 1 32
   std::vector<std::thread> th;
   for (int i = 0; i < 8; ++i)
-    th.emplace_back([&c, i] { for (int k = 0; k < 1000; ++k) c.put(Key{kWideTile, i, k, 0, 1}, k); });
+    th.emplace_back([&c, i] { for (int k = 0; k < 1000; ++k) c.put(Key{kWideTile, i, k, 0, 1, 1}, k); });
   for (auto& x : th) x.join();
   std::printf("%zu\n", c.size());                                                 // 8002
+  // a probe of 2 and 12 steps, the call 2000 steps: overhead 1.0 ms, 0.1 ms a step
+  std::printf("%.1f\n", extrapolate(1.2f, 2, 2.2f, 12, 2000));                    // 201.0
+  std::printf("%.1f\n", extrapolate(1.2f, 2, -1.0f, 12, 2000));                   // 1.2: failed probe
   return 0;
 }
 """
@@ -56,4 +62,5 @@ def test_selection_rule_and_cache(tmp_path):
                     str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     assert out[:7] == ["0", "1", "1", "0", "2", "0", "1"]
-    assert out[7:12] == ["0", "1 1", "0", "1 32", "8002"]
+    assert out[7:13] == ["0", "1 1", "0", "0", "1 32", "8002"]
+    assert out[13:15] == ["201.0", "1.2"]
