@@ -212,9 +212,8 @@ def run_large(n_sets: int = 2, slices: int = 0, n_angles: int = 0):
 
 # DRAM bytes per kick node of the integration kernels, from one ncu capture each (dram__bytes_read
 # + dram__bytes_write of a small case, divided by its node count; the traffic of these kernels is
-# proportional to the node count). Summaries: profiles/k_integrate_mixed_split_trhepd_n61_L400.md,
-# profiles/k_integrate_mixed_trhepd_n61_L400.md, profiles/k_integrate_fp64_split_trhepd_n61_L60.md
-# and profiles/k_integrate_fp64_trhepd_n61_L60.md. Each figure holds for the kernel sources it was
+# proportional to the node count). Summary and commands: profiles/dram_integration_trhepd_n61.md.
+# Each figure holds for the kernel sources it was
 # measured on: the hash of those files at capture time is stored beside it, and a figure whose
 # sources have changed since is reported as null (kernel_source_hash).
 KERNEL_SOURCES = {
@@ -222,10 +221,10 @@ KERNEL_SOURCES = {
     "fp64": ("integrate_fp64.cu", "fp64_core.cuh", "internal.h"),
 }
 TRAFFIC_PER_NODE = {  # kernel: (bytes per node, sources, hash of the sources at capture)
-    "mixed_split": (324.232704e6 / 2401, "mixed", None),
-    "mixed": (325.20192e6 / 2401, "mixed", None),
-    "fp64_split": (1.504512e6 / 361, "fp64", None),
-    "fp64": (1.624832e6 / 361, "fp64", None),
+    "mixed_split": ((318.562304e6 + 4.07936e6) / 2401, "mixed", "a98f9ca143e94dbb"),
+    "mixed": ((320.856832e6 + 3.96544e6) / 2401, "mixed", "a98f9ca143e94dbb"),
+    "fp64_split": (2.05952e6 / 361, "fp64", "07906019533b4fb9"),
+    "fp64": (2.1952e6 / 361, "fp64", "07906019533b4fb9"),
 }
 
 
