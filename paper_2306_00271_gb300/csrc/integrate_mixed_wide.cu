@@ -34,7 +34,7 @@
 // every CTA of the cluster (distributed shared memory), added in a fixed order so that all CTAs
 // take the same RHST decision. RHST: every CTA writes its columns of Q and P (hi, lo) to a
 // per-pair buffer in global memory (L2-resident), inverts the full Q in FP32 by Gauss-Jordan
-// elimination in registers (the same computation in every CTA; any invertible T is a valid RHST,
+// elimination in shared memory (the same computation in every CTA; any invertible T is a valid RHST,
 // Section 3.2), and forms Z T for its own columns in double-float from the gathered rows. At the
 // end every CTA writes its columns of Q and P in binary64 to `fstate`, and a separate kernel
 // (launch_assemble_wide) assembles rho and eta in binary64.
@@ -64,9 +64,11 @@ constexpr int NBUF = 4;              // stage buffers
 constexpr int PLANE_SLICE = (MT / 8) * 2 * 128;     // one digit plane of one K-slice: 4 KB
 constexpr int SLICE_BYTES = NDIG * PLANE_SLICE;     // 16 KB
 constexpr int STAGE_BYTES = KC * SLICE_BYTES;       // 32 KB
-constexpr int TSW = NW + 1;          // row stride (float2) of T = Q^{-1} in the A region
+constexpr int TSC = NW + 4;          // column stride (float2) of T = Q^{-1} in the A region:
+                                     // = 4 (mod 16), so a warp's 8 columns x 4 row groups fall
+                                     // on distinct bank pairs
 constexpr int A_BYTES =
-    (NBUF * STAGE_BYTES > NW * TSW * 8) ? NBUF * STAGE_BYTES : NW * TSW * 8;
+    (NBUF * STAGE_BYTES > NW * TSC * 8) ? NBUF * STAGE_BYTES : NW * TSC * 8;
 constexpr int B_LBO = 144;           // padded K-block stride: conflict-free digit stores
 constexpr int B_SBO = 2 * KSMAX * B_LBO;
 constexpr int BT = (CW / 8) * B_SBO; // one digit plane of this CTA's 32 columns
@@ -104,21 +106,6 @@ struct __align__(1024) WSmem {
   int piv[NW], ipiv[NW];
 };
 static_assert(sizeof(WSmem) + 1024 <= 232448, "shared memory above the 227 KB a CTA may use");
-
-// tv[i] for a run-time i in [0, NR) by a tree of selects (keeps tv in registers)
-template <int NR>
-__device__ __forceinline__ float2 pick_sel(const float2 (&tv)[NR], int i) {
-  float2 cur[NR];
-#pragma unroll
-  for (int n = 0; n < NR; ++n) cur[n] = tv[n];
-#pragma unroll
-  for (int w = 1; w < NR; w <<= 1) {
-    const bool bit = (i & w) != 0;
-#pragma unroll
-    for (int n = 0; n + w < NR; n += 2 * w) cur[n] = bit ? cur[n + w] : cur[n];
-  }
-  return cur[0];
-}
 
 // Digit images of the real-ified U(tau), one CTA per node: the node's scale (smallest power of
 // two >= every |Re u_g|, |Im u_g| as FP32) and the four BF16 digit planes in the stage layout.
@@ -339,24 +326,26 @@ __device__ __forceinline__ uint32_t wdigits_b(WSmem& S, const float (&qh)[R][CP]
   return ovf;
 }
 
-// Gauss-Jordan step c of wgj_invert, executed by the warp that holds column c: the column is
-// staged for step c and its pivot chosen among the rows not yet used (bit i of `used`: row
-// rg + 4 i; largest modulus, lowest row on ties) over this thread's rows, then over the column's
-// four owner lanes.
-__device__ __forceinline__ void wgj_publish(WSmem& S, const float2 (&tv)[32], uint32_t used, int c,
-                                            int n, int col, int rg) {
+// Gauss-Jordan step c of wgj_invert, executed by the warp that holds column c: the column (in
+// T, column-major) is staged for step c and its pivot chosen among the rows not yet used (bit i
+// of `used`: row rg + 4 i; largest modulus, lowest row on ties) over this thread's rows, then over
+// the column's four owner lanes.
+__device__ __forceinline__ void wgj_publish(WSmem& S, const float2* T, uint32_t used, int c, int n,
+                                            int col, int rg) {
   const int par = c & 1;
   float best = -1.0f;
   int bi = 0x7fffffff;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = rg + 4 * i;
-    const bool ok = r < n && !((used >> i) & 1u);
-    const float m2 = ok ? tv[i].x * tv[i].x + tv[i].y * tv[i].y : -1.0f;
-    if (col == c && r < n) S.gstage[par][r] = tv[i];
-    if (m2 > best) {
-      best = m2;
-      bi = r;
+  if (col == c) {
+    for (int i = 0; i < 32; ++i) {
+      const int r = rg + 4 * i;
+      if (r >= n) break;
+      const float2 v = T[c * TSC + r];
+      S.gstage[par][r] = v;
+      const float m2 = ((used >> i) & 1u) ? -1.0f : v.x * v.x + v.y * v.y;
+      if (m2 > best) {
+        best = m2;
+        bi = r;
+      }
     }
   }
 #pragma unroll
@@ -377,27 +366,27 @@ __device__ __forceinline__ void wgj_publish(WSmem& S, const float2 (&tv)[32], ui
 
 // Inverse of the n x n complex FP32 matrix Q (n <= 128; read by column from the gather buffer,
 // zq[c 2n + 2r .. +1] = Q[r][c]) by Gauss-Jordan elimination in the exchange form (implicit
-// row pivoting: step k trades column k for the pivot row p_k, no row moves). Thread t owns
-// column t / 4 and rows t % 4 + 4 i (i < 32) in registers; the four owners of a column share a
-// warp and pass the pivot row's entry by a shuffle; the owners of column k + 1 publish it and
-// its pivot at the end of step k, in buffers alternating by parity: one block barrier a step.
-// On return T (row stride TSW) holds B with Q^{-1}[k][j] = B[piv[k]][ipiv[j]].
+// row pivoting: step k trades column k for the pivot row p_k, no row moves), in place in T
+// (shared memory, column-major, column stride TSC). Thread t updates column t / 4, rows t % 4 +
+// 4 i; the owner of the pivot row's entry passes it to the column's other three lanes by a
+// shuffle before anyone overwrites it; the owners of column k + 1 publish it and its pivot at the
+// end of step k, in buffers alternating by parity: one block barrier a step. (Held in shared
+// memory rather than registers: 32 complex entries a thread in registers spilled.)
+// On return T holds B column by column, Q^{-1}[k][j] = B[piv[k]][ipiv[j]] = T[ipiv[j] TSC + piv[k]].
 __device__ __forceinline__ void wgj_invert(WSmem& S, const float* zq, float2* T, int n) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int col = tid >> 2, rg = tid & 3;
   const int base = lane & ~3;               // lane of (col, rg = 0)
   const int warp = tid >> 5;                // holds columns 8 warp .. 8 warp + 7
-  float2 tv[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = rg + 4 * i;
-    tv[i] = (r < n && col < n)
-                ? *reinterpret_cast<const float2*>(zq + (size_t)col * 2 * n + 2 * r)
-                : make_float2(0.f, 0.f);
+  for (int e = tid; e < n * n; e += NT) {
+    const int c = e / n, r = e - c * n;
+    T[c * TSC + r] = *reinterpret_cast<const float2*>(zq + (size_t)c * 2 * n + 2 * r);
   }
-  uint32_t used = 0;
-  if (warp == 0) wgj_publish(S, tv, used, 0, n, col, rg);
   __syncthreads();
+  uint32_t used = 0;
+  if (warp == 0) wgj_publish(S, T, used, 0, n, col, rg);
+  __syncthreads();
+  float2* Tc = T + col * TSC;
   for (int k = 0; k < n; ++k) {
     const int par = k & 1;
     const int p = S.gpr[par];
@@ -408,30 +397,27 @@ __device__ __forceinline__ void wgj_invert(WSmem& S, const float* zq, float2* T,
     // any invertible T is a valid RHST (Section 3.2): an approximate reciprocal serves
     const float id = (a2 < 1e37f) ? __fdividef(1.0f, a2) : __frcp_rn(a2);
     const float2 inv = make_float2(a.x * id, -a.y * id);
-    const float2 vp = pick_sel<32>(tv, p >> 2);
+    const bool owner = (p & 3) == rg;
+    const float2 vp = (owner && col < n) ? Tc[p] : make_float2(0.f, 0.f);
     const float2 tp = make_float2(__shfl_sync(0xffffffffu, vp.x, base + (p & 3)),
                                   __shfl_sync(0xffffffffu, vp.y, base + (p & 3)));
     const bool ck = (col == k);
     const float2 fr = ck ? inv
                          : make_float2(tp.x * inv.x - tp.y * inv.y, tp.x * inv.y + tp.y * inv.x);
-    const int ip = ((p & 3) == rg) ? (p >> 2) : -1;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const int r = rg + 4 * i;
-      const float2 f = stg[r < n ? r : 0];
-      float2 t = ck ? make_float2(0.f, 0.f) : tv[i];
-      t.x -= f.x * fr.x - f.y * fr.y;
-      t.y -= f.x * fr.y + f.y * fr.x;
-      if (r < n && col < n) tv[i] = (i == ip) ? fr : t;
+    if (col < n) {
+      for (int i = 0; i < 32; ++i) {
+        const int r = rg + 4 * i;
+        if (r >= n) break;
+        const float2 f = stg[r];
+        float2 t = ck ? make_float2(0.f, 0.f) : Tc[r];
+        t.x -= f.x * fr.x - f.y * fr.y;
+        t.y -= f.x * fr.y + f.y * fr.x;
+        Tc[r] = (r == p) ? fr : t;
+      }
     }
-    if (ip >= 0) used |= 1u << ip;
-    if (k + 1 < n && warp == ((k + 1) >> 3)) wgj_publish(S, tv, used, k + 1, n, col, rg);
+    if (owner) used |= 1u << (p >> 2);
+    if (k + 1 < n && warp == ((k + 1) >> 3)) wgj_publish(S, T, used, k + 1, n, col, rg);
     __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = rg + 4 * i;
-    if (r < n && col < n) T[r * TSW + col] = tv[i];
   }
   if (tid < n) S.ipiv[S.piv[tid]] = tid;
   __syncthreads();
@@ -483,10 +469,10 @@ __device__ __forceinline__ void wapply(WSmem& S, const float* zg, const float2* 
     __syncthreads();
     const int kend = min(ZS, n - kc);
     for (int kk = 0; kk < kend; ++kk) {
-      const float2* Brow = T + S.piv[kc + kk] * TSW;
+      const int prow = S.piv[kc + kk];
       float2 t[CP];
 #pragma unroll
-      for (int i = 0; i < CP; ++i) t[i] = Brow[bc[i]];
+      for (int i = 0; i < CP; ++i) t[i] = T[bc[i] * TSC + prow];
 #pragma unroll
       for (int rt = 0; rt < R; ++rt) {
         const int m = MT * rt + 32 * qd + lane;
