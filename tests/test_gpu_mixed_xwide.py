@@ -143,3 +143,28 @@ def test_large_recipe_full_depth_sampled_angles(api):
     rho, eta = rho.cpu().numpy()[0], eta.cpu().numpy()[0]
     assert np.all(np.isfinite(rho)) and eng.stats()["n_bad"] == 0
     _check(rho[g["angles"]], eta[g["angles"]], g["rho"], g["eta"])
+
+
+def test_batch_with_a_wide_job_equals_standalone(api):
+    """A batch holding a 140-beam mixed job (16-column CTAs in a cluster of 9) beside a 37-beam
+    mixed job and an FP64 job: the eager run and the graph replay equal the standalone curves
+    bitwise."""
+    w140 = W.tiny(n_beams=140, seed=21, n_steps=20, theta0=(1.2, 2.8), depth=5.0)
+    w37 = W.tiny(n_beams=37, seed=22, n_steps=30, theta0=(0.9, 2.1, 3.3), depth=6.0)
+    w19 = W.tiny(n_beams=19, seed=23, n_steps=30, theta0=(1.5,), depth=6.0)
+    e140 = api.Engine(w140, "mixed", "sp4")
+    e140.set_structures(np.stack([w140.atoms, w140.atoms + np.array([0.0, 0.0, -0.1])]))
+    e37 = api.Engine(w37, "mixed", "sp4")
+    e19 = api.Engine(w19, "fp64", "sp4")
+    batch = api.Batch()
+    jobs = ((e140, w140), (e37, w37), (e19, w19))
+    outs = [batch.add(e, w.theta0, w.theta1) for e, w in jobs]
+    for run in range(2):
+        batch.run()
+        st = batch.stats()
+        assert st["graph_replay"] == run and st["n_bad"] == 0
+        for (rho_b, eta_b), (e, w) in zip(outs, jobs):
+            rho_s, eta_s = e.rocking_curve(w.theta0, w.theta1)
+            np.testing.assert_array_equal(rho_b.cpu().numpy(), rho_s.cpu().numpy())
+            np.testing.assert_array_equal(eta_b.cpu().numpy(), eta_s.cpu().numpy())
+    batch.close()
