@@ -679,7 +679,12 @@ def main():
                 "frac": achieved / peak,
                 "traffic": None if tpn is None else tpn * (6 * L + 1),
                 "peak_source": "MEASURED_PEAKS.json bf16 burst (of measured)",
-                "note": "achieved counts complex FP32-equivalent algorithmic flops"}
+                "note": "achieved counts complex FP32-equivalent algorithmic flops",
+                # each algorithmic product costs ten BF16 digit products (four digits per
+                # operand, orders 0..3), so the tensor pipe's own ceiling for this arithmetic
+                # is a tenth of the BF16 peak
+                "digit_product_ceiling": peak / 10.0,
+                "frac_of_digit_product_ceiling": achieved / (peak / 10.0)}
     else:
         bf = peaks.get("bf16_tflops", 1900.0)
         peak = bf * 1.25 / 2250.0
