@@ -358,7 +358,8 @@ def run_ours(args):
 
 def run_gradient(local: int, slices: int = 0, warmup: int = 1, path: str = "fp64"):
     """One R-factor gradient at the differentiation workload (N = 61, 2000 slices, 60 angles,
-    12 free z + 6 Debye-Waller classes, checkpoints every 64 steps), FP64 reverse sweep. The
+    12 free z + 6 Debye-Waller classes, checkpoints every 64 steps): binary64 recompute and
+    adjoint, the contraction in binary64 (FP64 context) or as BF16 digit products (mixed). The
     target curve is this library's own FP64 curve at the hidden true structure."""
     import torch
     from paper_2306_00271_gb300 import api
@@ -386,8 +387,9 @@ def run_gradient(local: int, slices: int = 0, warmup: int = 1, path: str = "fp64
     st = eng.stats()
     eng.close()
     return {"metric": f"R-factor gradients/s (N=61, L={wl.n_steps}, 60 angles, 18 parameters, "
-                      f"{'mixed' if path == 'mixed' else 'FP64'} forward, FP64 reverse sweep, "
-                      "checkpoints every 64 steps)",
+                      + ("mixed forward, reverse sweep binary64 with the contraction on BF16 "
+                         "digits, " if path == "mixed" else "FP64 forward, FP64 reverse sweep, ")
+                      + "checkpoints every 64 steps)",
             "value": 1000.0 / ms, "unit": "gradients/s", "ms_per_gradient": ms,
             "ms_forward": st["ms_integrate"], "ms_reverse": st["ms_gradient"],
             "kernels_launched": st["kernels_launched"], "R": float(R[0])}

@@ -1,0 +1,280 @@
+// The contraction of the reverse sweep on the tensor cores, for mixed-precision contexts with
+// N <= 64 (the binary64 form is k_grad_ubar in adjoint_fp64.cu; the reverse map and the
+// potential derivatives are stated there).
+//
+// Per kick n of a segment and angle, Ubar_n = -c_n Pbar_n Q_n^H is reduced to the distinct
+// differences and contracted with the derivatives of the potential model. Of the reverse sweep's
+// three N x N x N products per kick (the recomputed kick, the kick adjoint, this one) this is the
+// one whose result is only summed: each ubar_m collects N^2 / M products and enters the gradient
+// through a further sum over kicks, so FP32-level products (relative error ~1e-7, unbiased) leave
+// the gradient's 1e-5 target untouched while the binary64 pipe is freed for the recompute and the
+// adjoint, which carry the trajectory.
+//
+// The product as in integrate_mixed.cu: real-ified A[2j+p][2k+q] = [[Re, -Im], [Im, Re]] of
+// Pbar_jk (M = 128 rows, K = 2N) against B[2k+q][l] = part q of conj(Q_lk) (the first column of
+// the real-ified Q^H), so that D[2j+p][l] is part p of (Pbar Q^H)_jl; both operands cut into four
+// signed 8-bit digits with power-of-two scales (rows of A, columns of B), the ten digit products
+// of orders <= 3 accumulated exactly in four TMEM accumulators and combined in FP32.
+#include "internal.h"
+#include "mixed_digits.cuh"
+#include "umma.cuh"
+
+namespace trh {
+
+namespace {
+
+using namespace umma;
+using namespace mixed;
+
+constexpr int UT = 256;                     // threads
+constexpr int MT = 128;                     // rows of the tile (2N <= 128)
+constexpr int KT = 128;                     // K = 2N <= 128
+constexpr int PW = 64;                      // width of a B digit plane (columns l < N <= 64)
+constexpr int A_LBO = 128;                  // K-blocks of 8 elements, 128 B apart
+constexpr int A_SBO = (KT / 8) * A_LBO;     // 8-row groups, 2 KB apart
+constexpr int A_TERM = (MT / 8) * A_SBO;    // one digit plane of A: 32 KB
+constexpr int B_LBO = 144;                  // padded K-block stride
+constexpr int B_SBO = (KT / 8) * B_LBO;     // 8-column groups
+constexpr int B_TERM = (PW / 8) * B_SBO;    // one digit plane of B
+constexpr uint32_t TMEM_COLS = 256;         // 4 orders x PW columns
+constexpr double kPiU = 3.14159265358979323846;
+
+struct __align__(1024) USmem {
+  unsigned char A[NDIG * A_TERM];
+  unsigned char B[NDIG * B_TERM];
+  float alpha[MT / 2];          // scale of the real-ified rows 2j, 2j+1 of A (row j of Pbar)
+  float gam[PW];                // scale of column l of B (row l of Q)
+  double acc[2 * 64];           // per active atom: d/dz, d/dB
+  uint64_t bar_mma;
+  uint32_t tmem_base;
+  int to;
+};
+static_assert(sizeof(USmem) <= 232448, "shared memory above the 227 KB a CTA may use");
+
+// Largest |Re|, |Im| over row r of an N x N complex matrix, one warp per row.
+__device__ __forceinline__ float row_max(const double2* X, int r, int N, int lane) {
+  float mx = 0.0f;
+  for (int k = lane; k < N; k += 32) {
+    const double2 v = X[(size_t)r * N + k];
+    mx = fmaxf(mx, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  return pow2_ceil(mx);
+}
+
+// Eight consecutive K elements (16 B) of one digit plane: word w of the chunk holds elements
+// (2w, 2w + 1).
+__device__ __forceinline__ void store_chunk(unsigned char* dst, const float (&x)[8], float inv,
+                                            int plane_stride) {
+  uint16_t d[8][NDIG];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) digits4(x[e], inv, d[e]);
+#pragma unroll
+  for (int t = 0; t < NDIG; ++t)
+    *reinterpret_cast<uint4*>(dst + t * plane_stride) =
+        make_uint4(d[0][t] | ((uint32_t)d[1][t] << 16), d[2][t] | ((uint32_t)d[3][t] << 16),
+                   d[4][t] | ((uint32_t)d[5][t] << 16), d[6][t] | ((uint32_t)d[7][t] << 16));
+}
+
+__global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  USmem& S = *reinterpret_cast<USmem*>(smem_raw);
+  double* ur = reinterpret_cast<double*>(smem_raw + sizeof(USmem));
+  const IntegrateParams& p = g.ip;
+  const int local = blockIdx.x, angle = blockIdx.y, set = blockIdx.z;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = p.N, M = p.M;
+  double* ui = ur + M;
+  const size_t pair = (size_t)set * p.ang.n_angles + angle;
+  const int s = p.sch.s, C = p.ckpt_every;
+  const int i0 = g.seg * C, i1 = min(i0 + C, p.L);
+  const int count = s * (i1 - i0) + (i1 == p.L ? 1 : 0);
+  if (local >= count || g.status[pair] != kOk) return;
+  const int n = s * i0 + local;
+  const size_t NN = (size_t)N * N;
+  const double2* Pb = g.segPb + (pair * g.kseg + local) * NN;
+  const double2* Qn = g.segQ + (pair * g.kseg + local) * NN;
+
+  if (tid == 0) {
+    mbar_init(&S.bar_mma, 1);
+    mbar_fence_init();
+    S.to = 0;
+  }
+  if (warp == 0) tmem_alloc(&S.tmem_base, TMEM_COLS);
+  for (int m = tid; m < M; m += UT) ur[m] = ui[m] = 0.0;
+  for (int e = tid; e < 2 * g.n_active; e += UT) S.acc[e] = 0.0;
+  // scales: rows of Pbar (rows of A) and rows of Q (columns of B)
+  for (int r = warp; r < N; r += UT / 32) {
+    const float a = row_max(Pb, r, N, lane);
+    const float b = row_max(Qn, r, N, lane);
+    if (lane == 0) {
+      S.alpha[r] = a;
+      S.gam[r] = b;
+    }
+  }
+  for (int r = N + tid; r < PW; r += UT) {
+    S.alpha[r] = 1.0f;
+    S.gam[r] = 1.0f;
+  }
+  __syncthreads();
+  // digits of A: task (row m, K-block kb) = elements 8 kb .. 8 kb + 7 of row m, i.e. Pbar_jk for
+  // k = 4 kb .. 4 kb + 3 (both parts q); zero outside 2N x 2N. Eight consecutive threads take the
+  // eight rows of one core matrix, whose 16-byte rows are contiguous: conflict-free stores.
+  for (int task = tid; task < MT * (KT / 8); task += UT) {
+    const int m = ((task >> 7) << 3) | (task & 7), kb = (task >> 3) & (KT / 8 - 1);
+    const int j = m >> 1, pp = m & 1;
+    float x[8];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int k = 4 * kb + w;
+      double re = 0.0, im = 0.0;
+      if (j < N && k < N) {
+        const double2 v = Pb[(size_t)j * N + k];
+        re = v.x;
+        im = v.y;
+      }
+      // [[Re, -Im], [Im, Re]][pp][q]
+      x[2 * w] = (float)(pp ? im : re);
+      x[2 * w + 1] = (float)(pp ? re : -im);
+    }
+    const float inv = pow2_inv(S.alpha[j < N ? j : 0]);
+    store_chunk(S.A + (m >> 3) * A_SBO + kb * A_LBO + (m & 7) * 16, x, inv, A_TERM);
+  }
+  // digits of B: task (column l, K-block kb) = B[8 kb .. 8 kb + 7][l], part q of conj(Q_lk) for
+  // k = 4 kb .. 4 kb + 3; digit t in plane position 3 - t
+  for (int task = tid; task < PW * (KT / 8); task += UT) {
+    const int l = ((task >> 7) << 3) | (task & 7), kb = (task >> 3) & (KT / 8 - 1);
+    float x[8];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int k = 4 * kb + w;
+      double re = 0.0, im = 0.0;
+      if (l < N && k < N) {
+        const double2 v = Qn[(size_t)l * N + k];
+        re = v.x;
+        im = -v.y;
+      }
+      x[2 * w] = (float)re;
+      x[2 * w + 1] = (float)im;
+    }
+    const float inv = pow2_inv(S.gam[l]);
+    store_chunk(S.B + (NDIG - 1) * B_TERM + (l >> 3) * B_SBO + kb * B_LBO + (l & 7) * 16, x, inv,
+                -B_TERM);
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+  const int n_mma = (N + 15) / 16 * 16;
+  const int KS = (2 * N + 15) / 16;
+  if (tid == 0) {
+    const uint32_t a_base = smem_u32(S.A), b_base = smem_u32(S.B);
+    // digit a of A against the planes b = 3 - a .. 0 of B (contiguous from plane position a):
+    // the accumulator of order a + b at TMEM column PW (3 - a - b)
+    for (int a = 0; a < NDIG; ++a) {
+      const uint64_t at = smem_desc(a_base + a * A_TERM, A_LBO, A_SBO);
+      const uint64_t bt = smem_desc(b_base + a * B_TERM, B_LBO, B_SBO);
+      const uint32_t id = idesc_bf16_f32(MT, PW * (NDIG - 1 - a) + n_mma);
+      for (int ks = 0; ks < KS; ++ks)
+        mma_bf16(tmem, at + (uint64_t)((ks * 2 * A_LBO) >> 4),
+                 bt + (uint64_t)((ks * 2 * B_LBO) >> 4), id, !(a == 0 && ks == 0));
+    }
+    mma_commit(&S.bar_mma);
+  }
+  if (!mbar_wait(&S.bar_mma, 0, kWaitCycles)) S.to = 1;
+  tc_fence_after();
+  __syncthreads();
+  const bool ok = S.to == 0;
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (real-ified row m) and columns 32 (w / 4) ..
+  {
+    constexpr float kQ = 0.00390625f;  // 2^-8
+    const int m = 32 * (warp & 3) + lane, j = m >> 1, pp = m & 1;
+    const uint32_t t_lane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    const float ra = (j < N) ? S.alpha[j] * (1.0f / 16384.0f) : 0.0f;
+    for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32 && c0 < N && ok; c0 += 8) {
+      float d3[8], d2[8], d1[8], d0[8];
+      tmem_ld8x4(t_lane + c0, d3, t_lane + PW + c0, d2, t_lane + 2 * PW + c0, d1,
+                 t_lane + 3 * PW + c0, d0);
+      if (j >= N) continue;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int l = c0 + e;
+        if (l >= N) break;
+        float a = __fadd_rn(d2[e], __fmul_rn(d3[e], kQ));
+        a = __fadd_rn(d0[e], __fmul_rn(__fadd_rn(d1[e], __fmul_rn(a, kQ)), kQ));
+        const double w = (double)__fmul_rn(__fmul_rn(a, S.gam[l]), ra);
+        const int mi = __ldg(p.lmap + j * N + l);
+        atomicAdd(pp ? ui + mi : ur + mi, w);
+      }
+    }
+  }
+  __syncthreads();
+  if (ok) {
+    const double c = (n == s * p.L) ? p.h * p.sch.b[s]
+                     : (n % s > 0) ? p.h * p.sch.b[n % s]
+                     : (n == 0 ? p.h * p.sch.b[0] : p.h * (p.sch.b[s] + p.sch.b[0]));
+    const double tau = g.node_z[n];
+    const int T = 4 * g.n_atoms;
+    const double2* Fs = g.F + (size_t)set * T * M;
+    constexpr double k16pi2 = 16.0 * kPiU * kPiU;
+    for (int w = warp; w < 4 * g.n_active; w += UT / 32) {
+      const int ai = w >> 2, i = w & 3;
+      const int a = g.active[ai];
+      const double2* Ft = Fs + (size_t)(4 * a + i) * M;
+      double v = 0.0, vg = 0.0;   // Re sum_m conj(ubar_m) pref F_m, and with |g_m|^2
+      for (int mm = lane; mm < M; mm += 32) {
+        const double2 f = Ft[mm];
+        const double fr = g.pref.x * f.x - g.pref.y * f.y, fi = g.pref.x * f.y + g.pref.y * f.x;
+        const double re = ur[mm] * fr + ui[mm] * fi;
+        const double2 gm = g.gdiff[mm];
+        v += re;
+        vg += re * (gm.x * gm.x + gm.y * gm.y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        vg += __shfl_xor_sync(0xffffffffu, vg, o);
+      }
+      v *= -c;
+      vg *= -c;
+      if (lane == 0) {
+        const double za = g.atoms[((size_t)set * g.n_atoms + a) * 3 + 2];
+        const double B = g.dw[(size_t)set * g.n_atoms + a];
+        const double beta = (g.sf[8 * g.species[a] + 4 + i] + B) / k16pi2;
+        const double d = tau - za;
+        const double G = exp(-d * d / (4.0 * beta));
+        atomicAdd(&S.acc[2 * ai], v * G * d / (2.0 * beta));
+        atomicAdd(&S.acc[2 * ai + 1],
+                  (v * G * (d * d / (4.0 * beta * beta) - 0.5 / beta) - vg * G) / k16pi2);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < 2 * g.n_active; e += UT)
+      atomicAdd(g.jac_atoms + pair * 2 * g.n_active + e, S.acc[e]);
+  } else if (tid == 0) {
+    g.status[pair] = kTimeout;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace
+
+// A difference table too long for the shared-memory ubar beside the digit images (M > 1536; the
+// beam sets of up to 64 beams used here have a few hundred) takes the binary64 contraction.
+cudaError_t launch_grad_ubar_mixed(const GradParams& g, cudaStream_t st, int* n_launched) {
+  if (g.n_active > 64 || g.ip.N > kMaxBeamsMixed) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(USmem) + 2 * (size_t)g.ip.M * sizeof(double);
+  if (smem > 232448) return launch_grad_ubar(g, st, n_launched);
+  cudaError_t e = cudaFuncSetAttribute(k_grad_ubar_mixed,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_grad_ubar_mixed<<<dim3(g.kseg, g.ip.ang.n_angles, g.ip.n_sets), UT, smem, st>>>(g);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace trh

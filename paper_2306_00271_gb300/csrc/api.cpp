@@ -77,6 +77,8 @@ bool is_device_ptr(const void* ptr) {
 
 namespace trh {
 void set_last_error(const char* msg) { g_last_error = msg; }
+// adjoint_mixed.cu: the contraction of the reverse sweep on the BF16 digit path (mixed contexts)
+cudaError_t launch_grad_ubar_mixed(const GradParams& g, cudaStream_t st, int* n_launched);
 }  // namespace trh
 
 struct trh_ctx {
@@ -1458,6 +1460,10 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   // and segment g+1's contraction runs (stream 2). Buffers of parity b are reused two segments
   // later, after the contraction and adjoint that read them.
   cudaStream_t rs = c->gs[0], as = c->gs[1], us = c->gs[2];
+  // a mixed context takes the contraction on the tensor cores as four-digit products (relative
+  // error ~1e-7 in each Ubar entry, summed into the gradient); the recompute and the adjoint, which
+  // carry the trajectory, stay binary64
+  const bool ubar_digits = c->precision == TRH_MIXED && n_act <= 64;
   TRH_CUDA(cudaEventRecord(c->gev[0][0], st));
   for (int k = 0; k < 3; ++k) TRH_CUDA(cudaStreamWaitEvent(c->gs[k], c->gev[0][0], 0));
   for (int seg = n_seg - 1; seg >= 0; --seg) {
@@ -1478,7 +1484,10 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
     TRH_CUDA(trh::launch_grad_adjoint(g, as, launched));
     TRH_CUDA(cudaEventRecord(c->gev[2][b], as));
     TRH_CUDA(cudaStreamWaitEvent(us, c->gev[2][b], 0));
-    TRH_CUDA(trh::launch_grad_ubar(g, us, launched));
+    if (ubar_digits)
+      TRH_CUDA(trh::launch_grad_ubar_mixed(g, us, launched));
+    else
+      TRH_CUDA(trh::launch_grad_ubar(g, us, launched));
     TRH_CUDA(cudaEventRecord(c->gev[3][b], us));
   }
   // join: the last contraction ran after every adjoint and recompute it depends on

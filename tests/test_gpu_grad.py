@@ -171,6 +171,30 @@ def test_mixed_forward_gradient(api):
     assert st["ms_integrate"] < 1000.0      # the forward ran on the mixed path
 
 
+def test_mixed_jacobian_digit_contraction(api):
+    """A mixed context of <= 64 beams forms each kick's Ubar on the tensor cores from four-digit
+    operands (the recompute and the adjoint stay binary64): its Jacobian agrees with the oracle's
+    central differences within the bar and with a binary64 context's Jacobian to ~1e-7, the
+    FP32-level rounding of the digit products summed over kicks. Ragged N (37: a 74 x 74 product
+    in a 128 x 128 tile) and a ragged last segment; the checkpoint interval changes nothing but
+    the order of the contraction's atomic additions."""
+    wl = _small()
+    free, cls = np.array([0, 1, 2, 3]), np.array([0, 1, 1, 0])
+    eng = api.Engine(wl, "mixed", "sp4")
+    eng.set_fit(free, cls, ckpt_every=32)
+    eta, jac = eng.curve_jacobian(wl.theta0, wl.theta1)
+    jac = jac.cpu().numpy()[0]
+    fd = G.fd_gradient(wl, free, cls, target=np.ones(len(wl.theta0)))
+    assert _rel(jac, fd["jac"]) <= TOL, _rel(jac, fd["jac"])
+    ref = api.Engine(wl, "fp64", "sp4")
+    ref.set_fit(free, cls, ckpt_every=32)
+    jac64 = ref.curve_jacobian(wl.theta0, wl.theta1)[1].cpu().numpy()[0]
+    assert 0.0 < _rel(jac, jac64) <= 1e-6, _rel(jac, jac64)
+    eng.set_fit(free, cls, ckpt_every=7)
+    jac7 = eng.curve_jacobian(wl.theta0, wl.theta1)[1].cpu().numpy()[0]
+    assert _rel(jac7, jac) <= 1e-6
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_wide_jacobian_matches_oracle_differences(api, precision):
     """70 beams (64 < N <= 256): the wide reverse sweep (state in global memory, products on the
