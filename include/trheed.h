@@ -139,6 +139,9 @@ typedef struct trh_stats {
                              integrator, pair count, L) for the life of the process; 0 for a fixed
                              rule (a forced split mode, more pairs than SMs, N <= 32, a mixed
                              cluster of ceil(N / 32) or ceil(N / 16) CTAs)                      */
+  int sweep_split;        /* 1 if the reverse sweep of the last trh_curve_jacobian /
+                             trh_rfactor_grad call ran its recompute and adjoint kernels as
+                             two-CTA clusters (column split, N <= 64), else 0                  */
 } trh_stats;
 
 /* Create a context for one beam set and method. Validates and copies `p` (the caller may free
@@ -213,7 +216,8 @@ int trh_set_bulk(trh_ctx* ctx, int n_atoms, const double* atoms, const double* d
  * TRH_SPLIT_AUTO (the default) lets the autotuner choose when N > 32 and the call has at most
  * as many pairs as SMs (both forms timed on probes of the call's pairs at 2 and 12 steps, their
  * times at the call's L extrapolated, the faster kept for that shape; trh_stats.tuned), TRH_SPLIT_OFF never splits, TRH_SPLIT_ON whenever N > 32
- * (trh_curve_jacobian's forward splits when its pairs fit on half the SMs). Results are identical either way:
+ * (trh_curve_jacobian's forward splits when its pairs fit on half the SMs, and so do its reverse
+ * sweep's recompute and adjoint kernels: trh_stats.sweep_split). Results are identical either way:
  * every column sees the same arithmetic, and the row sums are added in the same fixed order, so
  * the RHST decisions coincide. Batches (trh_batch_*) always run one CTA per pair. A wait for the
  * other CTA that runs out (about 2 s) ends the pair with TRH_ETIMEOUT.
@@ -259,10 +263,11 @@ int trh_set_image_budget(trh_ctx* ctx, size_t bytes);
  * with t~ the target curve normalised the same way. The RHST matrices are constants of the
  * reverse map (rho is invariant under Z -> Z T, Section 3.2). Memory is bounded by
  * checkpoints: the forward pass stores [Q; P] every `ckpt_every` steps and the reverse sweep
- * recomputes one segment at a time. Device scratch per (set, angle) pair, in bytes:
- *   16 N^2 (2 (L / C + 1) + 2 (s C + 1) + 2 C + 2) + 4 C,   C = ckpt_every, s = kicks per step,
- * about 53 MB at N = 61, L = 2000, C = 64 (sp4); for 64 < N <= 256 (the wide reverse sweep,
- * state in global memory)
+ * recomputes one segment at a time, up to two segments ahead of the adjoint (three segment
+ * slots). Device scratch per (set, angle) pair, in bytes:
+ *   16 N^2 (2 (L / C + 1) + 3 (2 (s C + 1) + 2 C) + 2) + 12 C,   C = ckpt_every,
+ * s = kicks per step, about 164 MB at N = 61, L = 2000, C = 64 (sp4, s = 6); for 64 < N <= 256
+ * (the wide reverse sweep, state in global memory)
  *   16 N^2 (2 (L / C + 1) + (s C + 1) + 2 C + 6) + 4 C.
  * N <= 64: on a TRH_FP64 context everything runs on the binary64 path; on a TRH_MIXED context
  * the forward pass (curve, R and the checkpoints, binary64 values of its double-float state)

@@ -46,6 +46,7 @@ class TrhStats(C.Structure):
         ("ms_gradient", C.c_double), ("wide_tile", C.c_int), ("graph_replay", C.c_int),
         ("bulk_periods", C.c_int), ("ms_bulk", C.c_double), ("column_split", C.c_int),
         ("ctas_per_pair", C.c_int), ("set_chunks", C.c_int), ("tuned", C.c_int),
+        ("sweep_split", C.c_int),
     ]
 
     def as_dict(self):

@@ -48,13 +48,32 @@ __device__ __forceinline__ void segment_bounds(const GradParams& g, int& i0, int
   i1 = min(i0 + g.ip.ckpt_every, g.ip.L);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_grad_recompute(GradParams g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+// Columns c0 .. c0 + nc - 1 of an N x N complex matrix from shared planes to global memory
+// (row-major, stride N): a CTA of a column split stores the half it owns.
+__device__ __forceinline__ void store_cols(double2* dst, const double* Sr, const double* Si, int N,
+                                           int c0, int nc) {
+  nc = min(nc, N - c0);
+  if (nc <= 0) return;
+  for (int e = threadIdx.x; e < N * nc; e += NT) {
+    const int j = e / nc, k = c0 + (e - j * nc);
+    dst[j * N + k] = make_double2(Sr[j * LD + k], Si[j * LD + k]);
+  }
+}
+
+// The forward over one segment from its checkpoint, storing Q at every kick and (Q before, P
+// after) of every RHST. SPLIT: the two CTAs of a cluster own columns 32 r .. 32 r + 31 of [Q; P]
+// and exchange as the forward kernel's column split does (Varah row sums every step, the column
+// halves before an RHST, a confirmation after it); every stored value is bitwise the one-CTA one.
+template <bool SPLIT>
+__device__ __forceinline__ void recompute_pair(Smem& S, const GradParams& g, int angle, int set) {
+  constexpr int NS = SPLIT ? 2 : 4;
   const IntegrateParams& p = g.ip;
-  const int angle = blockIdx.x, set = blockIdx.y, tid = threadIdx.x, N = p.N;
+  const int tid = threadIdx.x, N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   if (g.status[pair] != kOk) return;
+  const uint32_t rank = SPLIT ? umma::cluster_ctarank() : 0u, peer = rank ^ 1u;
+  const int col0 = SPLIT ? 32 * (int)rank : 0, ncol = SPLIT ? 32 : NP;
+  uint32_t xk = 0;
   const size_t NN = nn_of(g);
   const int s = p.sch.s, C = p.ckpt_every;
   int i0, i1;
@@ -68,27 +87,68 @@ __global__ void __launch_bounds__(NT, 1) k_grad_recompute(GradParams g) {
   __syncthreads();
   double2* segQ = g.segQ + pair * g.kseg * NN;
   double2* segR = g.segR + pair * C * 2 * NN;
+  bool timed_out = false;
   for (int i = i0; i < i1; ++i) {
     for (int r = 0; r < s; ++r) {
       const int n = s * i + r;
-      store_mat(segQ + (size_t)(n - s * i0) * NN, S.Qr, S.Qi, N);
+      store_cols(segQ + (size_t)(n - s * i0) * NN, S.Qr, S.Qi, N, col0, ncol);
       const double coef = (r > 0) ? p.sch.b[r] : (i == 0 ? p.sch.b[0] : p.sch.b[s] + p.sch.b[0]);
-      kick_drift(S, p, set, coef, p.sch.a[r], true, n + 1);
+      kick_drift<NS>(S, p, set, coef, p.sch.a[r], true, n + 1, col0);
     }
-    badness(S, p);
+    if (!badness<SPLIT>(S, p, i & 1, rank, peer, &xk)) {
+      timed_out = true;
+      break;
+    }
     const int c = i - i0;
     if (S.flag) {
-      store_mat(segR + (size_t)(2 * c) * NN, S.Qr, S.Qi, N);
+      store_cols(segR + (size_t)(2 * c) * NN, S.Qr, S.Qi, N, col0, ncol);
+      if constexpr (SPLIT) {
+        send_columns(S, N, rank, peer);
+        if (!cta_exchange(S, peer, xk)) {
+          timed_out = true;
+          break;
+        }
+      }
       __syncthreads();
       rhst(S, p);
       if (S.status != kOk) break;
-      store_mat(segR + (size_t)(2 * c + 1) * NN, S.Pr, S.Pi, N);
+      store_cols(segR + (size_t)(2 * c + 1) * NN, S.Pr, S.Pi, N, col0, ncol);
+      if constexpr (SPLIT) {
+        if (!cta_exchange(S, peer, xk)) {  // both have read their planes
+          timed_out = true;
+          break;
+        }
+      }
     }
-    if (tid == 0) g.rflag[pair * C + c] = S.flag ? 1 : 0;
+    if (tid == 0 && rank == 0) g.rflag[pair * C + c] = S.flag ? 1 : 0;
   }
-  if (S.status == kOk && i1 == p.L) store_mat(segQ + (size_t)(s * (i1 - i0)) * NN, S.Qr, S.Qi, N);
+  if (timed_out && tid == 0) S.status = kTimeout;
+  __syncthreads();
+  if (S.status == kOk && i1 == p.L)
+    store_cols(segQ + (size_t)(s * (i1 - i0)) * NN, S.Qr, S.Qi, N, col0, ncol);
   __syncthreads();
   if (tid == 0 && S.status != kOk) g.status[pair] = S.status;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_grad_recompute(GradParams g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  recompute_pair<false>(S, g, blockIdx.x, blockIdx.y);
+}
+
+// Column split: a cluster of two CTAs (blockIdx.x = 2 angle + rank) per (set, angle) pair.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 1)
+    k_grad_recompute_split(GradParams g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  if (threadIdx.x == 0) {
+    umma::mbar_init(&S.bar_x[0], 1);
+    umma::mbar_init(&S.bar_x[1], 1);
+    umma::mbar_fence_init();
+  }
+  umma::cluster_sync();  // both CTAs' mbarriers are initialised before any remote arrival
+  recompute_pair<true>(S, g, blockIdx.x >> 1, blockIdx.y);
+  umma::cluster_sync();  // no CTA exits while the other may still write to its shared memory
 }
 
 // Adjoint seed from the final state [Q; P] in the Q/P planes; leaves [Qbar; Pbar] there.
@@ -161,16 +221,18 @@ __device__ __forceinline__ void adjoint_seed(Smem& S, int N) {
   __syncthreads();
 }
 
-// Qbar <- Qbar - c (U^H + Gamma^2) Pbar with U(tau_n) in the U planes.
-__device__ __forceinline__ void kick_adjoint(Smem& S, int N, double c) {
+// Qbar <- Qbar - c (U^H + Gamma^2) Pbar with U(tau_n) in the U planes; columns col0 ..
+// col0 + 16 NS - 1 only (the kick adjoint acts column by column).
+template <int NS = 4>
+__device__ __forceinline__ void kick_adjoint(Smem& S, int N, double c, int col0 = 0) {
   double wr[4][4], wi[4][4];
-  cgemm<true, true, false, false>(S.Ur, S.Ui, S.Pr, S.Pi, N, wr, wi);
-  if (tile_active(N)) {
+  cgemm<true, true, false, false, NS>(S.Ur, S.Ui, S.Pr, S.Pi, N, wr, wi, col0);
+  if (tile_active<NS>(N, col0)) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int row = frag_row(q), col = frag_col(s, q);
+        const int row = frag_row<NS>(q), col = frag_col<NS>(s, q, col0);
         if (row < N && col < N) {
           const int o = row * LD + col;
           const double g2 = S.gam2[row];
@@ -208,13 +270,23 @@ __device__ __forceinline__ void rhst_adjoint(Smem& S, int N, const double2* qpre
   gauss_jordan_right<3>(S, Z, N);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_grad_adjoint(GradParams g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+// The reverse map over one segment, storing Pbar entering every kick's adjoint. SPLIT: the two
+// CTAs of a cluster own columns 32 r .. 32 r + 31 of [Qbar; Pbar]; kicks and drifts act column by
+// column, an RHST adjoint exchanges the halves first (both then run the same elimination) and
+// confirms after it. One exchange after the initial load or seed keeps a CTA's halves from
+// reaching the other before it has finished writing its whole planes.
+template <bool SPLIT>
+__device__ __forceinline__ void adjoint_pair(Smem& S, const GradParams& g, int angle, int set) {
+  constexpr int NS = SPLIT ? 2 : 4;
   const IntegrateParams& p = g.ip;
-  const int angle = blockIdx.x, set = blockIdx.y, tid = threadIdx.x, N = p.N;
+  const int tid = threadIdx.x, N = p.N;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   if (g.status[pair] != kOk) return;
+  const uint32_t rank = SPLIT ? umma::cluster_ctarank() : 0u, peer = rank ^ 1u;
+  const int col0 = SPLIT ? 32 * (int)rank : 0, ncol = SPLIT ? 32 : NP;
+  const int c0 = col0, nc = min(ncol, N - col0);
+  uint32_t xk = 0;
+  bool timed_out = false;
   const size_t NN = nn_of(g);
   const int s = p.sch.s, C = p.ckpt_every;
   int i0, i1;
@@ -234,43 +306,79 @@ __global__ void __launch_bounds__(NT, 1) k_grad_adjoint(GradParams g) {
     load_mat(S.Pr, S.Pi, az + NN, N);
     __syncthreads();
   }
+  if constexpr (SPLIT) timed_out = !cta_exchange(S, peer, xk);
   double2* segPb = g.segPb + pair * g.kseg * NN;
   const double2* segR = g.segR + pair * C * 2 * NN;
-  if (S.status == kOk && last) {                 // the final kick (no drift after it)
+  if (!timed_out && S.status == kOk && last) {   // the final kick (no drift after it)
     const int n = s * p.L;
-    store_mat(segPb + (size_t)(n - s * i0) * NN, S.Pr, S.Pi, N);
+    store_cols(segPb + (size_t)(n - s * i0) * NN, S.Pr, S.Pi, N, col0, ncol);
     load_u(S, p, set, n);
     __syncthreads();
-    kick_adjoint(S, N, kick_coef(p.sch, p.h, p.L, n));
+    kick_adjoint<NS>(S, N, kick_coef(p.sch, p.h, p.L, n), col0);
   }
-  for (int i = i1 - 1; i >= i0 && S.status == kOk; --i) {
+  for (int i = i1 - 1; i >= i0 && !timed_out && S.status == kOk; --i) {
     if (g.rflag[pair * C + (i - i0)]) {
       const double2* rec = segR + (size_t)(2 * (i - i0)) * NN;
+      if constexpr (SPLIT) {
+        send_columns(S, N, rank, peer);
+        if (!cta_exchange(S, peer, xk)) {
+          timed_out = true;
+          break;
+        }
+      }
       rhst_adjoint(S, N, rec, rec + NN);
       if (S.status != kOk) break;
+      if constexpr (SPLIT) {
+        if (!cta_exchange(S, peer, xk)) {  // both have read their planes
+          timed_out = true;
+          break;
+        }
+      }
     }
     for (int r = s - 1; r >= 0; --r) {
       const int n = s * i + r;
       const double d = p.h * p.sch.a[r];
       double2* dst = segPb + (size_t)(n - s * i0) * NN;
-      for (int e = tid; e < N * N; e += NT) {    // drift adjoint, and Pbar for this kick
-        const int j = e / N, k = e - j * N, o = j * LD + k;
+      for (int e = tid; e < N * nc; e += NT) {   // drift adjoint, and Pbar for this kick
+        const int j = e / nc, k = c0 + (e - j * nc), o = j * LD + k;
         const double pr = S.Pr[o] + d * S.Qr[o], pi = S.Pi[o] + d * S.Qi[o];
         S.Pr[o] = pr;
         S.Pi[o] = pi;
-        dst[e] = make_double2(pr, pi);
+        dst[j * N + k] = make_double2(pr, pi);
       }
       load_u(S, p, set, n);
       __syncthreads();
-      kick_adjoint(S, N, kick_coef(p.sch, p.h, p.L, n));
+      kick_adjoint<NS>(S, N, kick_coef(p.sch, p.h, p.L, n), col0);
     }
   }
+  if (timed_out && tid == 0) S.status = kTimeout;
+  __syncthreads();
   if (S.status == kOk) {
-    store_mat(az, S.Qr, S.Qi, N);
-    store_mat(az + NN, S.Pr, S.Pi, N);
+    store_cols(az, S.Qr, S.Qi, N, col0, ncol);
+    store_cols(az + NN, S.Pr, S.Pi, N, col0, ncol);
   }
   __syncthreads();
   if (tid == 0 && S.status != kOk) g.status[pair] = S.status;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_grad_adjoint(GradParams g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  adjoint_pair<false>(S, g, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT, 1)
+    k_grad_adjoint_split(GradParams g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  if (threadIdx.x == 0) {
+    umma::mbar_init(&S.bar_x[0], 1);
+    umma::mbar_init(&S.bar_x[1], 1);
+    umma::mbar_fence_init();
+  }
+  umma::cluster_sync();
+  adjoint_pair<true>(S, g, blockIdx.x >> 1, blockIdx.y);
+  umma::cluster_sync();
 }
 
 struct UbarSmem {
@@ -437,6 +545,26 @@ cudaError_t launch_grad_recompute(const GradParams& g, cudaStream_t st, int* n_l
   cudaError_t e = set_smem((const void*)k_grad_recompute, sizeof(Smem));
   if (e != cudaSuccess) return e;
   k_grad_recompute<<<dim3(g.ip.ang.n_angles, g.ip.n_sets), NT, sizeof(Smem), st>>>(g);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+// Column split of the recompute and the adjoint (N > 32): two-CTA clusters, every stored value
+// bitwise the one-CTA kernel's.
+cudaError_t launch_grad_recompute_split(const GradParams& g, cudaStream_t st, int* n_launched) {
+  if (g.ip.N <= 32) return cudaErrorInvalidValue;  // the second CTA would own no column
+  cudaError_t e = set_smem((const void*)k_grad_recompute_split, sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  k_grad_recompute_split<<<dim3(2 * g.ip.ang.n_angles, g.ip.n_sets), NT, sizeof(Smem), st>>>(g);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_adjoint_split(const GradParams& g, cudaStream_t st, int* n_launched) {
+  if (g.ip.N <= 32) return cudaErrorInvalidValue;
+  cudaError_t e = set_smem((const void*)k_grad_adjoint_split, sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  k_grad_adjoint_split<<<dim3(2 * g.ip.ang.n_angles, g.ip.n_sets), NT, sizeof(Smem), st>>>(g);
   if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }

@@ -79,7 +79,14 @@ namespace trh {
 void set_last_error(const char* msg) { g_last_error = msg; }
 // adjoint_mixed.cu: the contraction of the reverse sweep on the BF16 digit path (mixed contexts)
 cudaError_t launch_grad_ubar_mixed(const GradParams& g, cudaStream_t st, int* n_launched);
+// adjoint_fp64.cu: the recompute and the adjoint as two-CTA clusters (column split, N > 32)
+cudaError_t launch_grad_recompute_split(const GradParams& g, cudaStream_t st, int* n_launched);
+cudaError_t launch_grad_adjoint_split(const GradParams& g, cudaStream_t st, int* n_launched);
 }  // namespace trh
+
+// Segment slots of the reverse sweep (N <= 64): the recompute may run up to two segments ahead
+// of the adjoint, which keeps SMs busy while the adjoint's clusters finish.
+constexpr int kSweepSlots = 3;
 
 struct trh_ctx {
   // problem (host copies)
@@ -150,12 +157,13 @@ struct trh_ctx {
   // derivatives the reverse sweep accumulates (union of both)
   int n_free = 0, n_classes = 0, ckpt_every = 64;
   std::vector<int> free_atoms, dw_class, active, free_active, class_of_active;
-  DevBuf<int> d_active, d_free_active, d_class_active, d_rflag[2];
-  DevBuf<double2> d_ckpt, d_segQ[2], d_segPb[2], d_segR[2], d_adjZ;
+  DevBuf<int> d_active, d_free_active, d_class_active, d_rflag[kSweepSlots];
+  DevBuf<double2> d_ckpt, d_segQ[kSweepSlots], d_segPb[kSweepSlots], d_segR[kSweepSlots], d_adjZ;
   // reverse-sweep pipeline: recompute / adjoint / contraction on their own streams, buffers
   // double-buffered by segment parity
-  cudaStream_t gs[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t gev[4][2] = {};   // forward done / recompute / adjoint / contraction, by slot
+  // reverse sweep: one recompute stream per segment slot, then the adjoint and the contraction
+  cudaStream_t gs[kSweepSlots + 2] = {};
+  cudaEvent_t gev[4][kSweepSlots] = {};   // forward done / recompute / adjoint / contraction, by slot
   DevBuf<double> d_jacA, d_target, d_jac, d_R, d_gz, d_gb;
 };
 
@@ -1387,7 +1395,7 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   TRH_CUDA(c->d_eta.ensure(pairs * c->N));
   TRH_CUDA(c->d_status.ensure(2 * pairs));
   TRH_CUDA(c->d_ckpt.ensure(pairs * (n_seg + 1) * 2 * NN));
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kSweepSlots; ++b) {
     TRH_CUDA(c->d_segQ[b].ensure(pairs * kseg * NN));
     TRH_CUDA(c->d_segPb[b].ensure(pairs * kseg * NN));
     TRH_CUDA(c->d_segR[b].ensure(pairs * C * 2 * NN));
@@ -1397,15 +1405,18 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   TRH_CUDA(c->d_jacA.ensure(pairs * 2 * n_act));
   TRH_CUDA(cudaMemsetAsync(c->d_jacA.p, 0, pairs * 2 * n_act * sizeof(double), st));
   if (!c->gs[0]) {
-    // recompute and adjoint form the critical path of the pipeline; the contraction, whose many
-    // short CTAs fill the remaining SMs, gets the lowest priority so that it does not delay them
+    // the adjoint chain is the critical path: highest priority; the recompute, which runs ahead
+    // of it into free slots, next (its CTAs take the SMs the adjoint leaves); the contraction,
+    // whose many short CTAs fill the remaining SMs, lowest, so that it delays neither
     int least = 0, greatest = 0;
     TRH_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    for (int k = 0; k < 3; ++k)
+    const int next = greatest < least ? greatest + 1 : greatest;
+    for (int k = 0; k < kSweepSlots + 2; ++k)
       TRH_CUDA(cudaStreamCreateWithPriority(&c->gs[k], cudaStreamNonBlocking,
-                                            k < 2 ? greatest : least));
+                                            k < kSweepSlots ? next
+                                                            : (k == kSweepSlots ? greatest : least)));
     for (int k = 0; k < 4; ++k)
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < kSweepSlots; ++b)
         TRH_CUDA(cudaEventCreateWithFlags(&c->gev[k][b], cudaEventDisableTiming));
   }
 
@@ -1456,32 +1467,51 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   g.n_atoms = c->n_atoms;
   g.pref = potential_prefactor(c);
   g.jac_atoms = c->d_jacA.p;
-  // Pipeline: while segment g's adjoint runs (stream 1), segment g-1 is recomputed (stream 0)
-  // and segment g+1's contraction runs (stream 2). Buffers of parity b are reused two segments
-  // later, after the contraction and adjoint that read them.
-  cudaStream_t rs = c->gs[0], as = c->gs[1], us = c->gs[2];
+  // Pipeline: while segment g's adjoint runs, segments g-1 and g-2 are recomputed (one stream per
+  // slot) and segment g+1's contraction runs. The buffers of slot g % kSweepSlots are reused
+  // kSweepSlots segments later, after the contraction and adjoint that read them.
+  cudaStream_t as = c->gs[kSweepSlots], us = c->gs[kSweepSlots + 1];
+  // two-CTA clusters for the recompute and the adjoint when one wave of them fits on the device
+  // (the rule of the forward's split; bitwise the one-CTA results)
+  bool sweep_split = false;
+  if (c->N > 32 && c->split_mode != TRH_SPLIT_OFF) {
+    int dev = 0, sms = 0;
+    TRH_CUDA(cudaGetDevice(&dev));
+    TRH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    sweep_split = c->split_mode == TRH_SPLIT_ON || 2 * pairs <= (size_t)sms;
+  }
+  c->stats.sweep_split = sweep_split ? 1 : 0;
   // a mixed context takes the contraction on the tensor cores as four-digit products (relative
   // error ~1e-7 in each Ubar entry, summed into the gradient); the recompute and the adjoint, which
   // carry the trajectory, stay binary64
   const bool ubar_digits = c->precision == TRH_MIXED && n_act <= 64;
   TRH_CUDA(cudaEventRecord(c->gev[0][0], st));
-  for (int k = 0; k < 3; ++k) TRH_CUDA(cudaStreamWaitEvent(c->gs[k], c->gev[0][0], 0));
+  for (int k = 0; k < kSweepSlots + 2; ++k)
+    TRH_CUDA(cudaStreamWaitEvent(c->gs[k], c->gev[0][0], 0));
   for (int seg = n_seg - 1; seg >= 0; --seg) {
-    const int b = seg & 1;
+    const int b = seg % kSweepSlots;
+    cudaStream_t rs = c->gs[b];   // recomputes of different slots may run concurrently
     g.seg = seg;
     g.segQ = c->d_segQ[b].p;
     g.segPb = c->d_segPb[b].p;
     g.segR = c->d_segR[b].p;
     g.rflag = c->d_rflag[b].p;
-    if (seg + 2 < n_seg) {   // slot b was last used by segment seg + 2
+    const bool reused = seg + kSweepSlots < n_seg;   // slot b was last used by seg + kSweepSlots
+    if (reused) {
       TRH_CUDA(cudaStreamWaitEvent(rs, c->gev[2][b], 0));
       TRH_CUDA(cudaStreamWaitEvent(rs, c->gev[3][b], 0));
     }
-    TRH_CUDA(trh::launch_grad_recompute(g, rs, launched));
+    if (sweep_split)
+      TRH_CUDA(trh::launch_grad_recompute_split(g, rs, launched));
+    else
+      TRH_CUDA(trh::launch_grad_recompute(g, rs, launched));
     TRH_CUDA(cudaEventRecord(c->gev[1][b], rs));
     TRH_CUDA(cudaStreamWaitEvent(as, c->gev[1][b], 0));
-    if (seg + 2 < n_seg) TRH_CUDA(cudaStreamWaitEvent(as, c->gev[3][b], 0));
-    TRH_CUDA(trh::launch_grad_adjoint(g, as, launched));
+    if (reused) TRH_CUDA(cudaStreamWaitEvent(as, c->gev[3][b], 0));
+    if (sweep_split)
+      TRH_CUDA(trh::launch_grad_adjoint_split(g, as, launched));
+    else
+      TRH_CUDA(trh::launch_grad_adjoint(g, as, launched));
     TRH_CUDA(cudaEventRecord(c->gev[2][b], as));
     TRH_CUDA(cudaStreamWaitEvent(us, c->gev[2][b], 0));
     if (ubar_digits)
@@ -1490,9 +1520,9 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
       TRH_CUDA(trh::launch_grad_ubar(g, us, launched));
     TRH_CUDA(cudaEventRecord(c->gev[3][b], us));
   }
-  // join: the last contraction ran after every adjoint and recompute it depends on
-  TRH_CUDA(cudaStreamWaitEvent(st, c->gev[3][0], 0));
-  TRH_CUDA(cudaStreamWaitEvent(st, c->gev[3][n_seg > 1 ? 1 : 0], 0));
+  // join: the last contraction of each slot ran after every adjoint and recompute it depends on
+  for (int b = 0; b < kSweepSlots && b < n_seg; ++b)
+    TRH_CUDA(cudaStreamWaitEvent(st, c->gev[3][b], 0));
   TRH_CUDA(cudaEventRecord(c->ev[4], st));
   return TRH_OK;
 }
@@ -1664,16 +1694,16 @@ void trh_destroy(trh_ctx* c) {
   c->d_free_active.release();
   c->d_class_active.release();
   c->d_ckpt.release();
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kSweepSlots; ++b) {
     c->d_rflag[b].release();
     c->d_segQ[b].release();
     c->d_segPb[b].release();
     c->d_segR[b].release();
   }
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < kSweepSlots + 2; ++k)
     if (c->gs[k]) cudaStreamDestroy(c->gs[k]);
   for (int k = 0; k < 4; ++k)
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kSweepSlots; ++b)
       if (c->gev[k][b]) cudaEventDestroy(c->gev[k][b]);
   c->d_adjZ.release();
   c->d_jacA.release();

@@ -48,11 +48,12 @@ def test_jacobian_matches_oracle_differences(api):
     st = eng.stats()
     assert st["rhst_total"] > 10 * len(wl.theta0) and st["ms_gradient"] > 0
     assert st["column_split"] == 1   # 4 angles: the forward ran with two CTAs per angle
-    # the one-CTA forward: the same trajectory bit for bit, so the same curve and the same
-    # Jacobian (to the order of the contraction's atomic additions)
+    assert st["sweep_split"] == 1    # and so did the reverse sweep's recompute and adjoint
+    # the one-CTA forward and sweep: the same trajectory and the same adjoint bit for bit, so the
+    # same curve and the same Jacobian (to the order of the contraction's atomic additions)
     eng.set_column_split("off")
     eta1, jac1 = eng.curve_jacobian(wl.theta0, wl.theta1)
-    assert eng.stats()["column_split"] == 0
+    assert eng.stats()["column_split"] == 0 and eng.stats()["sweep_split"] == 0
     assert np.array_equal(eta1.cpu().numpy(), eta.cpu().numpy())
     assert _rel(jac1.cpu().numpy()[0], jac) <= 1e-12
 
