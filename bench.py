@@ -616,12 +616,20 @@ def main():
                          "--large-angles; not the bench line)")
     ap.add_argument("--large-sets", type=int, default=2)
     ap.add_argument("--large-angles", type=int, default=0)
+    ap.add_argument("--grad-only", default=None, choices=["mixed", "fp64"],
+                    help="only the 18-parameter gradient line on a context of this precision "
+                         "(one warm-up gradient, one timed; profiling runs, not the bench line)")
     args = ap.parse_args()
     ws, rank, _ = _dist()
     if args.large_only:
         import torch
         torch.cuda.set_device(0)
         print(json.dumps(run_large(args.large_sets, args.slices, args.large_angles)))
+        return
+    if args.grad_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_gradient(0, args.slices, path=args.grad_only)))
         return
     wl = W.trhepd_n61()
     cfg = {"workload": "trhepd_n61: 10 keV e+, hex a=3.84 A, N=61 beams, 16 atoms, "
