@@ -196,6 +196,23 @@ def test_mixed_jacobian_digit_contraction(api):
     assert _rel(jac7, jac) <= 1e-6
 
 
+@pytest.mark.parametrize("n_beams, n_steps, depth", [(11, 60, 4.0), (64, 40, 3.0)])
+def test_mixed_jacobian_edge_sizes(api, n_beams, n_steps, depth):
+    """The digit contraction at its shape limits: 11 beams (a 22 x 22 product, two K-steps, one
+    CTA per angle in the sweep) and 64 beams (2N = 128 fills the tile's rows, the leading digit's
+    MMA is 256 columns wide): the mixed context's Jacobian against the binary64 context's."""
+    wl = W.tiny(n_beams=n_beams, n_steps=n_steps, seed=41, depth=depth, theta0=(0.9, 2.4))
+    free, cls = np.array([0, 2]), np.array([0, 0, 1, 1])
+    out = {}
+    for prec in ("mixed", "fp64"):
+        eng = api.Engine(wl, prec, "sp4")
+        eng.set_fit(free, cls, ckpt_every=16)
+        out[prec] = eng.curve_jacobian(wl.theta0, wl.theta1)[1].cpu().numpy()[0]
+        assert eng.stats()["sweep_split"] == (1 if n_beams > 32 else 0)
+    assert np.all(np.isfinite(out["mixed"])) and np.max(np.abs(out["fp64"])) > 0
+    assert _rel(out["mixed"], out["fp64"]) <= 1e-6, _rel(out["mixed"], out["fp64"])
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_wide_jacobian_matches_oracle_differences(api, precision):
     """70 beams (64 < N <= 256): the wide reverse sweep (state in global memory, products on the
