@@ -51,16 +51,43 @@ struct __align__(1024) USmem {
 };
 static_assert(sizeof(USmem) <= 232448, "shared memory above the 227 KB a CTA may use");
 
-// Largest |Re|, |Im| over row r of an N x N complex matrix, one warp per row.
-__device__ __forceinline__ float row_max(const double2* X, int r, int N, int lane) {
-  float mx = 0.0f;
-  for (int k = lane; k < N; k += 32) {
-    const double2 v = X[(size_t)r * N + k];
-    mx = fmaxf(mx, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
-  }
+// Power-of-two scales of the rows of two N x N complex matrices X and Y (N <= 64): the smallest
+// power of two >= the largest |Re|, |Im| of the row. Warp w takes rows w + 8 u; the loads of four
+// rows of both matrices are issued before any is used (one latency per four rows, not per row).
+__device__ __forceinline__ void row_scales(const double2* X, const double2* Y, int N, int warp,
+                                           int lane, float* sx, float* sy) {
+  constexpr int NW = UT / 32;
+  for (int r0 = warp; r0 < N; r0 += 4 * NW) {
+    double2 vx[4][2], vy[4][2];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  return pow2_ceil(mx);
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + u * NW, k = lane + 32 * h;
+        const bool in = r < N && k < N;
+        vx[u][h] = in ? X[(size_t)r * N + k] : make_double2(0.0, 0.0);
+        vy[u][h] = in ? Y[(size_t)r * N + k] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float mx = 0.0f, my = 0.0f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        mx = fmaxf(mx, fmaxf(fabsf((float)vx[u][h].x), fabsf((float)vx[u][h].y)));
+        my = fmaxf(my, fmaxf(fabsf((float)vy[u][h].x), fabsf((float)vy[u][h].y)));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+      }
+      const int r = r0 + u * NW;
+      if (lane == 0 && r < N) {
+        sx[r] = pow2_ceil(mx);
+        sy[r] = pow2_ceil(my);
+      }
+    }
+  }
 }
 
 // Eight consecutive K elements (16 B) of one digit plane: word w of the chunk holds elements
@@ -104,14 +131,7 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
   for (int m = tid; m < M; m += UT) ur[m] = ui[m] = 0.0;
   for (int e = tid; e < 2 * g.n_active; e += UT) S.acc[e] = 0.0;
   // scales: rows of Pbar (rows of A) and rows of Q (columns of B)
-  for (int r = warp; r < N; r += UT / 32) {
-    const float a = row_max(Pb, r, N, lane);
-    const float b = row_max(Qn, r, N, lane);
-    if (lane == 0) {
-      S.alpha[r] = a;
-      S.gam[r] = b;
-    }
-  }
+  row_scales(Pb, Qn, N, warp, lane, S.alpha, S.gam);
   for (int r = N + tid; r < PW; r += UT) {
     S.alpha[r] = 1.0f;
     S.gam[r] = 1.0f;
@@ -120,6 +140,7 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
   // digits of A: task (row m, K-block kb) = elements 8 kb .. 8 kb + 7 of row m, i.e. Pbar_jk for
   // k = 4 kb .. 4 kb + 3 (both parts q); zero outside 2N x 2N. Eight consecutive threads take the
   // eight rows of one core matrix, whose 16-byte rows are contiguous: conflict-free stores.
+#pragma unroll 4
   for (int task = tid; task < MT * (KT / 8); task += UT) {
     const int m = ((task >> 7) << 3) | (task & 7), kb = (task >> 3) & (KT / 8 - 1);
     const int j = m >> 1, pp = m & 1;
@@ -142,6 +163,7 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
   }
   // digits of B: task (column l, K-block kb) = B[8 kb .. 8 kb + 7][l], part q of conj(Q_lk) for
   // k = 4 kb .. 4 kb + 3; digit t in plane position 3 - t
+#pragma unroll 4
   for (int task = tid; task < PW * (KT / 8); task += UT) {
     const int l = ((task >> 7) << 3) | (task & 7), kb = (task >> 3) & (KT / 8 - 1);
     float x[8];
@@ -186,30 +208,61 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
   tc_fence_after();
   __syncthreads();
   const bool ok = S.to == 0;
+  // Reduction to the distinct differences. Each warp sums into its own copy of (ubar_r, ubar_i),
+  // held in the A planes (free once the MMAs have completed), and the copies are then added in
+  // warp order: no atomics, and the same sums on every run. Within one warp instruction the 32
+  // lanes update distinct entries (rows j of one column l have distinct differences g_j - g_l);
+  // __syncwarp orders a lane's update before another lane's in the next column. Tables of more
+  // than kPrivM differences fall back to shared-memory atomics on ubar itself.
+  constexpr int kPrivM = (int)(sizeof(S.A) / (2 * (UT / 32) * sizeof(double)));
+  const bool priv = M <= kPrivM;
+  double* part = reinterpret_cast<double*>(S.A) + (size_t)warp * 2 * M;
+  if (priv && ok) {
+    for (int e = tid; e < 2 * (UT / 32) * M; e += UT) reinterpret_cast<double*>(S.A)[e] = 0.0;
+    __syncthreads();
+  }
   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (real-ified row m) and columns 32 (w / 4) ..
   {
     constexpr float kQ = 0.00390625f;  // 2^-8
     const int m = 32 * (warp & 3) + lane, j = m >> 1, pp = m & 1;
     const uint32_t t_lane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const float ra = (j < N) ? S.alpha[j] * (1.0f / 16384.0f) : 0.0f;
+    double* dst = priv ? part + (pp ? M : 0) : (pp ? ui : ur);
     for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32 && c0 < N && ok; c0 += 8) {
       float d3[8], d2[8], d1[8], d0[8];
       tmem_ld8x4(t_lane + c0, d3, t_lane + PW + c0, d2, t_lane + 2 * PW + c0, d1,
                  t_lane + 3 * PW + c0, d0);
-      if (j >= N) continue;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int l = c0 + e;
-        if (l >= N) break;
-        float a = __fadd_rn(d2[e], __fmul_rn(d3[e], kQ));
-        a = __fadd_rn(d0[e], __fmul_rn(__fadd_rn(d1[e], __fmul_rn(a, kQ)), kQ));
-        const double w = (double)__fmul_rn(__fmul_rn(a, S.gam[l]), ra);
-        const int mi = __ldg(p.lmap + j * N + l);
-        atomicAdd(pp ? ui + mi : ur + mi, w);
+        if (j < N && l < N) {
+          float a = __fadd_rn(d2[e], __fmul_rn(d3[e], kQ));
+          a = __fadd_rn(d0[e], __fmul_rn(__fadd_rn(d1[e], __fmul_rn(a, kQ)), kQ));
+          const double w = (double)__fmul_rn(__fmul_rn(a, S.gam[l]), ra);
+          const int mi = __ldg(p.lmap + j * N + l);
+          if (priv)
+            dst[mi] += w;
+          else
+            atomicAdd(dst + mi, w);
+        }
+        __syncwarp();
       }
     }
   }
   __syncthreads();
+  if (priv && ok) {
+    for (int e = tid; e < M; e += UT) {
+      double sr = 0.0, si = 0.0;
+#pragma unroll
+      for (int w = 0; w < UT / 32; ++w) {
+        sr += reinterpret_cast<const double*>(S.A)[(size_t)w * 2 * M + e];
+        si += reinterpret_cast<const double*>(S.A)[(size_t)w * 2 * M + M + e];
+      }
+      ur[e] = sr;
+      ui[e] = si;
+    }
+    __syncthreads();
+  }
   if (ok) {
     const double c = (n == s * p.L) ? p.h * p.sch.b[s]
                      : (n % s > 0) ? p.h * p.sch.b[n % s]
@@ -223,6 +276,7 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
       const int a = g.active[ai];
       const double2* Ft = Fs + (size_t)(4 * a + i) * M;
       double v = 0.0, vg = 0.0;   // Re sum_m conj(ubar_m) pref F_m, and with |g_m|^2
+#pragma unroll 4
       for (int mm = lane; mm < M; mm += 32) {
         const double2 f = Ft[mm];
         const double fr = g.pref.x * f.x - g.pref.y * f.y, fi = g.pref.x * f.y + g.pref.y * f.x;
