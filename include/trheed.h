@@ -272,8 +272,10 @@ int trh_set_image_budget(trh_ctx* ctx, size_t bytes);
  * N <= 64: on a TRH_FP64 context everything runs on the binary64 path; on a TRH_MIXED context
  * the forward pass (curve, R and the checkpoints, binary64 values of its double-float state)
  * runs on the mixed path and every segment is recomputed on the binary64 path from its
- * checkpoint, so the reverse map differentiates the trajectory it recomputes; the gradient then
- * carries the mixed path's ~1e-8 relative error. 64 < N <= 256: the forward pass, the recompute
+ * checkpoint, so the reverse map differentiates the trajectory it recomputes; the adjoint is
+ * binary64 too, and only the contraction Ubar = -c Pbar Q^H (summed into the gradient, not
+ * carried) runs on the tensor cores as four-digit BF16 products, each entry to FP32 precision.
+ * The gradient then carries a relative error of ~1e-7 (the 1e-5 bar of the tests with margin). 64 < N <= 256: the forward pass, the recompute
  * and the adjoint all run on the binary64 wide kernels for either precision (the beam set's
  * distinct differences must fit shared memory twice: about 2000 at most). */
 
