@@ -264,7 +264,7 @@ int trh_set_image_budget(trh_ctx* ctx, size_t bytes);
  * reverse map (rho is invariant under Z -> Z T, Section 3.2). Memory is bounded by
  * checkpoints: the forward pass stores [Q; P] every `ckpt_every` steps and the reverse sweep
  * recomputes one segment at a time, up to two segments ahead of the adjoint (three segment
- * slots). Device scratch per (set, angle) pair, in bytes:
+ * slots, or one per segment when there are fewer). Device scratch per (set, angle) pair, in bytes:
  *   16 N^2 (2 (L / C + 1) + 3 (2 (s C + 1) + 2 C) + 2) + 12 C,   C = ckpt_every,
  * s = kicks per step, about 164 MB at N = 61, L = 2000, C = 64 (sp4, s = 6); for 64 < N <= 256
  * (the wide reverse sweep, state in global memory)

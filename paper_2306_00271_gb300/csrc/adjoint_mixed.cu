@@ -15,6 +15,19 @@
 // the real-ified Q^H), so that D[2j+p][l] is part p of (Pbar Q^H)_jl; both operands cut into four
 // signed 8-bit digits with power-of-two scales (rows of A, columns of B), the ten digit products
 // of orders <= 3 accumulated exactly in four TMEM accumulators and combined in FP32.
+//
+// No binary64 arithmetic per kick: binary64 instructions run on this GPU at a small fraction of
+// the FP32 rate, and in a first form of this kernel the per-element conversions of Pbar and Q to
+// FP32, the double sums and the per-(kick, Gaussian) exponentials kept the FP64 pipe 79 % busy
+// while the tensor pipe stayed idle. So the scales and digits come from the binary64 bit patterns
+// by integer arithmetic (a 31-bit fixed-point value per entry, cut into balanced base-256 digits),
+// the reduction and the contraction run in FP32, and the parts that depend only on the structure
+// and the node (pref F with and without |g|^2; the Gaussian factors at each node) are tabulated
+// once per gradient by k_ubar_tables. Each kick's contribution is then FP32-accurate (~1e-7
+// relative) and the contributions are summed over kicks in binary64.
+#include <algorithm>
+#include <climits>
+
 #include "internal.h"
 #include "mixed_digits.cuh"
 #include "umma.cuh"
@@ -44,18 +57,30 @@ struct __align__(1024) USmem {
   unsigned char B[NDIG * B_TERM];
   float alpha[MT / 2];          // scale of the real-ified rows 2j, 2j+1 of A (row j of Pbar)
   float gam[PW];                // scale of column l of B (row l of Q)
-  double acc[2 * 64];           // per active atom: d/dz, d/dB
+  float acc[2 * 64];            // per active atom: d/dz, d/dB of this kick (times -1/c)
+  int ea[PW], eg[PW];           // scale exponents of the rows of Pbar and of Q
   uint64_t bar_mma;
   uint32_t tmem_base;
   int to;
 };
 static_assert(sizeof(USmem) <= 232448, "shared memory above the 227 KB a CTA may use");
 
-// Power-of-two scales of the rows of two N x N complex matrices X and Y (N <= 64): the smallest
-// power of two >= the largest |Re|, |Im| of the row. Warp w takes rows w + 8 u; the loads of four
-// rows of both matrices are issued before any is used (one latency per four rows, not per row).
-__device__ __forceinline__ void row_scales(const double2* X, const double2* Y, int N, int warp,
-                                           int lane, float* sx, float* sy) {
+// Exponent of the smallest power of two >= |x| from the binary64 bit pattern; INT_MIN for 0
+// (subnormals, far below every scale here, count as 2^-1022).
+__device__ __forceinline__ int ceil_exp(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  if (b == 0) return INT_MIN;
+  const int ex = (int)(b >> 52);
+  if (ex == 0) return -1022;
+  return ex - 1023 + ((b & 0xFFFFFFFFFFFFFull) != 0 ? 1 : 0);
+}
+
+// Row scale exponents of two N x N complex matrices X and Y (N <= 64): the exponent of the
+// smallest power of two >= the largest |Re|, |Im| of the row (0 for a zero row), clamped to the
+// FP32 normal range. Warp w takes rows w + 8 u; the loads of four rows of both matrices are
+// issued before any is used.
+__device__ __forceinline__ void row_exps(const double2* X, const double2* Y, int N, int warp,
+                                         int lane, int* ex, int* ey) {
   constexpr int NW = UT / 32;
   for (int r0 = warp; r0 < N; r0 += 4 * NW) {
     double2 vx[4][2], vy[4][2];
@@ -70,33 +95,62 @@ __device__ __forceinline__ void row_scales(const double2* X, const double2* Y, i
       }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      float mx = 0.0f, my = 0.0f;
+      int mx = INT_MIN, my = INT_MIN;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        mx = fmaxf(mx, fmaxf(fabsf((float)vx[u][h].x), fabsf((float)vx[u][h].y)));
-        my = fmaxf(my, fmaxf(fabsf((float)vy[u][h].x), fabsf((float)vy[u][h].y)));
+        mx = max(mx, max(ceil_exp(vx[u][h].x), ceil_exp(vx[u][h].y)));
+        my = max(my, max(ceil_exp(vy[u][h].x), ceil_exp(vy[u][h].y)));
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
-      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      my = __reduce_max_sync(0xffffffffu, my);
       const int r = r0 + u * NW;
       if (lane == 0 && r < N) {
-        sx[r] = pow2_ceil(mx);
-        sy[r] = pow2_ceil(my);
+        ex[r] = mx == INT_MIN ? 0 : min(max(mx, -126), 127);
+        ey[r] = my == INT_MIN ? 0 : min(max(my, -126), 127);
       }
     }
   }
 }
 
-// Eight consecutive K elements (16 B) of one digit plane: word w of the chunk holds elements
-// (2w, 2w + 1).
-__device__ __forceinline__ void store_chunk(unsigned char* dst, const float (&x)[8], float inv,
+__device__ __forceinline__ float pow2f(int e) {  // 2^e, -126 <= e <= 127
+  return __int_as_float((e + 127) << 23);
+}
+
+// V = x 2^(31 - E) rounded to an integer (|x| <= 2^E, so |V| <= 2^31), from the bit pattern.
+__device__ __forceinline__ long long fixed31(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));  // x = mant 2^(ex-1075)
+  const int k = 1044 + E - ex;   // right shift: x 2^(31-E) = mant 2^-k, k >= 21
+  const long long v = (k >= 60) ? 0 : (((mant >> (k - 1)) + 1) >> 1);
+  return (b >> 63) ? -v : v;
+}
+
+// BF16 bit pattern of an integer |d| <= 256 (exact), by the 1.5 * 2^23 float trick.
+__device__ __forceinline__ uint16_t bf16_of_int(int d) {
+  const float f = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
+  return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
+// Balanced base-256 digits of V = d0 2^24 + d1 2^16 + d2 2^8 + d3 (|d_i| <= 128), as BF16.
+__device__ __forceinline__ void digits_fixed(long long V, uint16_t (&b)[NDIG]) {
+#pragma unroll
+  for (int i = NDIG - 1; i >= 1; --i) {
+    const int r = (int)((V + 128) & 255) - 128;
+    b[i] = bf16_of_int(r);
+    V = (V - r) >> 8;
+  }
+  b[0] = bf16_of_int((int)V);
+}
+
+// Eight consecutive K elements (16 B) of one digit plane from their fixed-point values: word w of
+// the chunk holds elements (2w, 2w + 1).
+__device__ __forceinline__ void store_chunk(unsigned char* dst, const long long (&v)[8],
                                             int plane_stride) {
   uint16_t d[8][NDIG];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) digits4(x[e], inv, d[e]);
+  for (int e = 0; e < 8; ++e) digits_fixed(v[e], d[e]);
 #pragma unroll
   for (int t = 0; t < NDIG; ++t)
     *reinterpret_cast<uint4*>(dst + t * plane_stride) =
@@ -104,14 +158,53 @@ __device__ __forceinline__ void store_chunk(unsigned char* dst, const float (&x)
                    d[4][t] | ((uint32_t)d[5][t] << 16), d[6][t] | ((uint32_t)d[7][t] << 16));
 }
 
-__global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
+// Tables for the contraction, once per gradient call (binary64 arithmetic, rounded to FP32):
+//   pf[set][4 ai + i][m] = (pref F_{a,i,m}, |g_m|^2 pref F_{a,i,m}) as (re, im, re, im),
+//   gc[set][node][4 ai + i] = (G d / (2 beta), G (d^2 / (4 beta^2) - 1 / (2 beta)) / (16 pi^2),
+//                              G / (16 pi^2), 0),  G = exp(-d^2 / (4 beta)), d = tau_node - z_a,
+// for the active atoms a = active[ai] and their four Gaussians i (the factors of
+// d eta_1 / d z_a and d eta_1 / d B_a in adjoint_fp64.cu).
+__global__ void __launch_bounds__(256) k_ubar_tables(GradParams g, float4* pf, float4* gc) {
+  const IntegrateParams& p = g.ip;
+  const int M = p.M, NA = 4 * g.n_active, T = 4 * g.n_atoms;
+  const size_t n_pf = (size_t)p.n_sets * NA * M, n_gc = (size_t)p.n_sets * p.n_nodes * NA;
+  constexpr double k16pi2 = 16.0 * kPiU * kPiU;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_pf + n_gc;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < n_pf) {
+      const int m = (int)(e % M), t = (int)((e / M) % NA), set = (int)(e / ((size_t)M * NA));
+      const int a = g.active[t >> 2], i = t & 3;
+      const double2 f = g.F[((size_t)set * T + 4 * a + i) * M + m];
+      const double fr = g.pref.x * f.x - g.pref.y * f.y, fi = g.pref.x * f.y + g.pref.y * f.x;
+      const double2 gm = g.gdiff[m];
+      const double g2 = gm.x * gm.x + gm.y * gm.y;
+      pf[e] = make_float4((float)fr, (float)fi, (float)(g2 * fr), (float)(g2 * fi));
+    } else {
+      const size_t q = e - n_pf;
+      const int t = (int)(q % NA), node = (int)((q / NA) % p.n_nodes);
+      const int set = (int)(q / ((size_t)NA * p.n_nodes));
+      const int a = g.active[t >> 2], i = t & 3;
+      const double za = g.atoms[((size_t)set * g.n_atoms + a) * 3 + 2];
+      const double B = g.dw[(size_t)set * g.n_atoms + a];
+      const double beta = (g.sf[8 * g.species[a] + 4 + i] + B) / k16pi2;
+      const double d = g.node_z[node] - za;
+      const double G = exp(-d * d / (4.0 * beta));
+      gc[q] = make_float4((float)(G * d / (2.0 * beta)),
+                          (float)(G * (d * d / (4.0 * beta * beta) - 0.5 / beta) / k16pi2),
+                          (float)(G / k16pi2), 0.0f);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g, const float4* pf,
+                                                           const float4* gc) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   USmem& S = *reinterpret_cast<USmem*>(smem_raw);
-  double* ur = reinterpret_cast<double*>(smem_raw + sizeof(USmem));
+  float* ur = reinterpret_cast<float*>(smem_raw + sizeof(USmem));
   const IntegrateParams& p = g.ip;
   const int local = blockIdx.x, angle = blockIdx.y, set = blockIdx.z;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = p.N, M = p.M;
-  double* ui = ur + M;
+  float* ui = ur + M;
   const size_t pair = (size_t)set * p.ang.n_angles + angle;
   const int s = p.sch.s, C = p.ckpt_every;
   const int i0 = g.seg * C, i1 = min(i0 + C, p.L);
@@ -121,6 +214,8 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
   const size_t NN = (size_t)N * N;
   const double2* Pb = g.segPb + (pair * g.kseg + local) * NN;
   const double2* Qn = g.segQ + (pair * g.kseg + local) * NN;
+  int* ea = S.ea;
+  int* eg = S.eg;
 
   if (tid == 0) {
     mbar_init(&S.bar_mma, 1);
@@ -128,59 +223,60 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
     S.to = 0;
   }
   if (warp == 0) tmem_alloc(&S.tmem_base, TMEM_COLS);
-  for (int m = tid; m < M; m += UT) ur[m] = ui[m] = 0.0;
-  for (int e = tid; e < 2 * g.n_active; e += UT) S.acc[e] = 0.0;
+  for (int m = tid; m < M; m += UT) ur[m] = ui[m] = 0.0f;
+  for (int e = tid; e < 2 * g.n_active; e += UT) S.acc[e] = 0.0f;
   // scales: rows of Pbar (rows of A) and rows of Q (columns of B)
-  row_scales(Pb, Qn, N, warp, lane, S.alpha, S.gam);
-  for (int r = N + tid; r < PW; r += UT) {
-    S.alpha[r] = 1.0f;
-    S.gam[r] = 1.0f;
-  }
+  row_exps(Pb, Qn, N, warp, lane, ea, eg);
+  for (int r = N + tid; r < PW; r += UT) ea[r] = eg[r] = 0;
   __syncthreads();
+  for (int r = tid; r < PW; r += UT) {
+    S.alpha[r] = pow2f(ea[r]);
+    S.gam[r] = pow2f(eg[r]);
+  }
   // digits of A: task (row m, K-block kb) = elements 8 kb .. 8 kb + 7 of row m, i.e. Pbar_jk for
   // k = 4 kb .. 4 kb + 3 (both parts q); zero outside 2N x 2N. Eight consecutive threads take the
   // eight rows of one core matrix, whose 16-byte rows are contiguous: conflict-free stores.
-#pragma unroll 4
+#pragma unroll 2
   for (int task = tid; task < MT * (KT / 8); task += UT) {
     const int m = ((task >> 7) << 3) | (task & 7), kb = (task >> 3) & (KT / 8 - 1);
     const int j = m >> 1, pp = m & 1;
-    float x[8];
+    const int E = ea[j < N ? j : 0];
+    long long v[8];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int k = 4 * kb + w;
-      double re = 0.0, im = 0.0;
+      long long re = 0, im = 0;
       if (j < N && k < N) {
-        const double2 v = Pb[(size_t)j * N + k];
-        re = v.x;
-        im = v.y;
+        const double2 x = Pb[(size_t)j * N + k];
+        re = fixed31(x.x, E);
+        im = fixed31(x.y, E);
       }
       // [[Re, -Im], [Im, Re]][pp][q]
-      x[2 * w] = (float)(pp ? im : re);
-      x[2 * w + 1] = (float)(pp ? re : -im);
+      v[2 * w] = pp ? im : re;
+      v[2 * w + 1] = pp ? re : -im;
     }
-    const float inv = pow2_inv(S.alpha[j < N ? j : 0]);
-    store_chunk(S.A + (m >> 3) * A_SBO + kb * A_LBO + (m & 7) * 16, x, inv, A_TERM);
+    store_chunk(S.A + (m >> 3) * A_SBO + kb * A_LBO + (m & 7) * 16, v, A_TERM);
   }
   // digits of B: task (column l, K-block kb) = B[8 kb .. 8 kb + 7][l], part q of conj(Q_lk) for
   // k = 4 kb .. 4 kb + 3; digit t in plane position 3 - t
-#pragma unroll 4
+#pragma unroll 2
   for (int task = tid; task < PW * (KT / 8); task += UT) {
     const int l = ((task >> 7) << 3) | (task & 7), kb = (task >> 3) & (KT / 8 - 1);
-    float x[8];
+    const int E = eg[l];
+    long long v[8];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int k = 4 * kb + w;
-      double re = 0.0, im = 0.0;
+      long long re = 0, im = 0;
       if (l < N && k < N) {
-        const double2 v = Qn[(size_t)l * N + k];
-        re = v.x;
-        im = -v.y;
+        const double2 x = Qn[(size_t)l * N + k];
+        re = fixed31(x.x, E);
+        im = -fixed31(x.y, E);
       }
-      x[2 * w] = (float)re;
-      x[2 * w + 1] = (float)im;
+      v[2 * w] = re;
+      v[2 * w + 1] = im;
     }
-    const float inv = pow2_inv(S.gam[l]);
-    store_chunk(S.B + (NDIG - 1) * B_TERM + (l >> 3) * B_SBO + kb * B_LBO + (l & 7) * 16, x, inv,
+    store_chunk(S.B + (NDIG - 1) * B_TERM + (l >> 3) * B_SBO + kb * B_LBO + (l & 7) * 16, v,
                 -B_TERM);
   }
   fence_proxy_async_smem();
@@ -214,11 +310,11 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
   // lanes update distinct entries (rows j of one column l have distinct differences g_j - g_l);
   // __syncwarp orders a lane's update before another lane's in the next column. Tables of more
   // than kPrivM differences fall back to shared-memory atomics on ubar itself.
-  constexpr int kPrivM = (int)(sizeof(S.A) / (2 * (UT / 32) * sizeof(double)));
+  constexpr int kPrivM = (int)(sizeof(S.A) / (2 * (UT / 32) * sizeof(float)));
   const bool priv = M <= kPrivM;
-  double* part = reinterpret_cast<double*>(S.A) + (size_t)warp * 2 * M;
+  float* part = reinterpret_cast<float*>(S.A) + (size_t)warp * 2 * M;
   if (priv && ok) {
-    for (int e = tid; e < 2 * (UT / 32) * M; e += UT) reinterpret_cast<double*>(S.A)[e] = 0.0;
+    for (int e = tid; e < 2 * (UT / 32) * M; e += UT) reinterpret_cast<float*>(S.A)[e] = 0.0f;
     __syncthreads();
   }
   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (real-ified row m) and columns 32 (w / 4) ..
@@ -227,7 +323,7 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
     const int m = 32 * (warp & 3) + lane, j = m >> 1, pp = m & 1;
     const uint32_t t_lane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const float ra = (j < N) ? S.alpha[j] * (1.0f / 16384.0f) : 0.0f;
-    double* dst = priv ? part + (pp ? M : 0) : (pp ? ui : ur);
+    float* dst = priv ? part + (pp ? M : 0) : (pp ? ui : ur);
     for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32 && c0 < N && ok; c0 += 8) {
       float d3[8], d2[8], d1[8], d0[8];
       tmem_ld8x4(t_lane + c0, d3, t_lane + PW + c0, d2, t_lane + 2 * PW + c0, d1,
@@ -238,7 +334,7 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
         if (j < N && l < N) {
           float a = __fadd_rn(d2[e], __fmul_rn(d3[e], kQ));
           a = __fadd_rn(d0[e], __fmul_rn(__fadd_rn(d1[e], __fmul_rn(a, kQ)), kQ));
-          const double w = (double)__fmul_rn(__fmul_rn(a, S.gam[l]), ra);
+          const float w = __fmul_rn(__fmul_rn(a, S.gam[l]), ra);
           const int mi = __ldg(p.lmap + j * N + l);
           if (priv)
             dst[mi] += w;
@@ -252,11 +348,11 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
   __syncthreads();
   if (priv && ok) {
     for (int e = tid; e < M; e += UT) {
-      double sr = 0.0, si = 0.0;
+      float sr = 0.0f, si = 0.0f;
 #pragma unroll
       for (int w = 0; w < UT / 32; ++w) {
-        sr += reinterpret_cast<const double*>(S.A)[(size_t)w * 2 * M + e];
-        si += reinterpret_cast<const double*>(S.A)[(size_t)w * 2 * M + M + e];
+        sr += reinterpret_cast<const float*>(S.A)[(size_t)w * 2 * M + e];
+        si += reinterpret_cast<const float*>(S.A)[(size_t)w * 2 * M + M + e];
       }
       ur[e] = sr;
       ui[e] = si;
@@ -264,48 +360,38 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
     __syncthreads();
   }
   if (ok) {
-    const double c = (n == s * p.L) ? p.h * p.sch.b[s]
-                     : (n % s > 0) ? p.h * p.sch.b[n % s]
-                     : (n == 0 ? p.h * p.sch.b[0] : p.h * (p.sch.b[s] + p.sch.b[0]));
-    const double tau = g.node_z[n];
-    const int T = 4 * g.n_atoms;
-    const double2* Fs = g.F + (size_t)set * T * M;
-    constexpr double k16pi2 = 16.0 * kPiU * kPiU;
-    for (int w = warp; w < 4 * g.n_active; w += UT / 32) {
-      const int ai = w >> 2, i = w & 3;
-      const int a = g.active[ai];
-      const double2* Ft = Fs + (size_t)(4 * a + i) * M;
-      double v = 0.0, vg = 0.0;   // Re sum_m conj(ubar_m) pref F_m, and with |g_m|^2
+    // per (active atom, Gaussian): v = Re sum_m conj(ubar_m) pref F_m and vg the same with
+    // |g_m|^2, then the node's Gaussian factors; -c_n is applied once at the end
+    const int NA = 4 * g.n_active;
+    const float4* pfs = pf + (size_t)set * NA * M;
+    const float4* gcn = gc + ((size_t)set * p.n_nodes + n) * NA;
+    for (int t = warp; t < NA; t += UT / 32) {
+      const float4* pt = pfs + (size_t)t * M;
+      float v = 0.0f, vg = 0.0f;
 #pragma unroll 4
       for (int mm = lane; mm < M; mm += 32) {
-        const double2 f = Ft[mm];
-        const double fr = g.pref.x * f.x - g.pref.y * f.y, fi = g.pref.x * f.y + g.pref.y * f.x;
-        const double re = ur[mm] * fr + ui[mm] * fi;
-        const double2 gm = g.gdiff[mm];
-        v += re;
-        vg += re * (gm.x * gm.x + gm.y * gm.y);
+        const float4 q = __ldg(pt + mm);
+        const float a = ur[mm], b = ui[mm];
+        v = fmaf(a, q.x, fmaf(b, q.y, v));
+        vg = fmaf(a, q.z, fmaf(b, q.w, vg));
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         v += __shfl_xor_sync(0xffffffffu, v, o);
         vg += __shfl_xor_sync(0xffffffffu, vg, o);
       }
-      v *= -c;
-      vg *= -c;
       if (lane == 0) {
-        const double za = g.atoms[((size_t)set * g.n_atoms + a) * 3 + 2];
-        const double B = g.dw[(size_t)set * g.n_atoms + a];
-        const double beta = (g.sf[8 * g.species[a] + 4 + i] + B) / k16pi2;
-        const double d = tau - za;
-        const double G = exp(-d * d / (4.0 * beta));
-        atomicAdd(&S.acc[2 * ai], v * G * d / (2.0 * beta));
-        atomicAdd(&S.acc[2 * ai + 1],
-                  (v * G * (d * d / (4.0 * beta * beta) - 0.5 / beta) - vg * G) / k16pi2);
+        const float4 gf = __ldg(gcn + t);
+        atomicAdd(&S.acc[2 * (t >> 2)], v * gf.x);
+        atomicAdd(&S.acc[2 * (t >> 2) + 1], fmaf(v, gf.y, -vg * gf.z));
       }
     }
     __syncthreads();
+    const double c = (n == s * p.L) ? p.h * p.sch.b[s]
+                     : (n % s > 0) ? p.h * p.sch.b[n % s]
+                     : (n == 0 ? p.h * p.sch.b[0] : p.h * (p.sch.b[s] + p.sch.b[0]));
     for (int e = tid; e < 2 * g.n_active; e += UT)
-      atomicAdd(g.jac_atoms + pair * 2 * g.n_active + e, S.acc[e]);
+      atomicAdd(g.jac_atoms + pair * 2 * g.n_active + e, -c * (double)S.acc[e]);
   } else if (tid == 0) {
     g.status[pair] = kTimeout;
   }
@@ -317,16 +403,37 @@ __global__ void __launch_bounds__(UT, 1) k_grad_ubar_mixed(GradParams g) {
 
 }  // namespace
 
-// A difference table too long for the shared-memory ubar beside the digit images (M > 1536; the
+// A difference table too long for the shared-memory ubar beside the digit images (M > 3200; the
 // beam sets of up to 64 beams used here have a few hundred) takes the binary64 contraction.
-cudaError_t launch_grad_ubar_mixed(const GradParams& g, cudaStream_t st, int* n_launched) {
+// pf and gc are the tables of k_ubar_tables (launch_ubar_tables, on the same stream or before).
+cudaError_t launch_grad_ubar_mixed(const GradParams& g, const float4* pf, const float4* gc,
+                                   cudaStream_t st, int* n_launched) {
   if (g.n_active > 64 || g.ip.N > kMaxBeamsMixed) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(USmem) + 2 * (size_t)g.ip.M * sizeof(double);
+  const size_t smem = sizeof(USmem) + 2 * (size_t)g.ip.M * sizeof(float);
   if (smem > 232448) return launch_grad_ubar(g, st, n_launched);
   cudaError_t e = cudaFuncSetAttribute(k_grad_ubar_mixed,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_grad_ubar_mixed<<<dim3(g.kseg, g.ip.ang.n_angles, g.ip.n_sets), UT, smem, st>>>(g);
+  k_grad_ubar_mixed<<<dim3(g.kseg, g.ip.ang.n_angles, g.ip.n_sets), UT, smem, st>>>(g, pf, gc);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+// Sizes (elements) of the two tables for `g`: pf n_sets x 4 n_active x M, gc n_sets x n_nodes x
+// 4 n_active.
+size_t ubar_pf_count(const GradParams& g) {
+  return (size_t)g.ip.n_sets * 4 * g.n_active * g.ip.M;
+}
+size_t ubar_gc_count(const GradParams& g) {
+  return (size_t)g.ip.n_sets * g.ip.n_nodes * 4 * g.n_active;
+}
+
+cudaError_t launch_ubar_tables(const GradParams& g, float4* pf, float4* gc, cudaStream_t st,
+                               int* n_launched) {
+  const size_t total = ubar_pf_count(g) + ubar_gc_count(g);
+  if (total == 0) return cudaSuccess;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  k_ubar_tables<<<blocks, 256, 0, st>>>(g, pf, gc);
   if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }

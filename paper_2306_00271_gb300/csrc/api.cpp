@@ -77,8 +77,14 @@ bool is_device_ptr(const void* ptr) {
 
 namespace trh {
 void set_last_error(const char* msg) { g_last_error = msg; }
-// adjoint_mixed.cu: the contraction of the reverse sweep on the BF16 digit path (mixed contexts)
-cudaError_t launch_grad_ubar_mixed(const GradParams& g, cudaStream_t st, int* n_launched);
+// adjoint_mixed.cu: the contraction of the reverse sweep on the BF16 digit path (mixed contexts),
+// with its structure- and node-dependent factors tabulated once per call
+cudaError_t launch_grad_ubar_mixed(const GradParams& g, const float4* pf, const float4* gc,
+                                   cudaStream_t st, int* n_launched);
+size_t ubar_pf_count(const GradParams& g);
+size_t ubar_gc_count(const GradParams& g);
+cudaError_t launch_ubar_tables(const GradParams& g, float4* pf, float4* gc, cudaStream_t st,
+                               int* n_launched);
 // adjoint_fp64.cu: the recompute and the adjoint as two-CTA clusters (column split, N > 32)
 cudaError_t launch_grad_recompute_split(const GradParams& g, cudaStream_t st, int* n_launched);
 cudaError_t launch_grad_adjoint_split(const GradParams& g, cudaStream_t st, int* n_launched);
@@ -159,6 +165,7 @@ struct trh_ctx {
   std::vector<int> free_atoms, dw_class, active, free_active, class_of_active;
   DevBuf<int> d_active, d_free_active, d_class_active, d_rflag[kSweepSlots];
   DevBuf<double2> d_ckpt, d_segQ[kSweepSlots], d_segPb[kSweepSlots], d_segR[kSweepSlots], d_adjZ;
+  DevBuf<float4> d_ubar_pf, d_ubar_gc;   // tables of the digit contraction (mixed contexts)
   // reverse-sweep pipeline: recompute / adjoint / contraction on their own streams, buffers
   // double-buffered by segment parity
   // reverse sweep: one recompute stream per segment slot, then the adjoint and the contraction
@@ -1395,7 +1402,7 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   TRH_CUDA(c->d_eta.ensure(pairs * c->N));
   TRH_CUDA(c->d_status.ensure(2 * pairs));
   TRH_CUDA(c->d_ckpt.ensure(pairs * (n_seg + 1) * 2 * NN));
-  for (int b = 0; b < kSweepSlots; ++b) {
+  for (int b = 0; b < kSweepSlots && b < n_seg; ++b) {   // the slots this sweep uses
     TRH_CUDA(c->d_segQ[b].ensure(pairs * kseg * NN));
     TRH_CUDA(c->d_segPb[b].ensure(pairs * kseg * NN));
     TRH_CUDA(c->d_segR[b].ensure(pairs * C * 2 * NN));
@@ -1485,6 +1492,11 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
   // error ~1e-7 in each Ubar entry, summed into the gradient); the recompute and the adjoint, which
   // carry the trajectory, stay binary64
   const bool ubar_digits = c->precision == TRH_MIXED && n_act <= 64;
+  if (ubar_digits) {
+    TRH_CUDA(c->d_ubar_pf.ensure(trh::ubar_pf_count(g)));
+    TRH_CUDA(c->d_ubar_gc.ensure(trh::ubar_gc_count(g)));
+    TRH_CUDA(trh::launch_ubar_tables(g, c->d_ubar_pf.p, c->d_ubar_gc.p, st, launched));
+  }
   TRH_CUDA(cudaEventRecord(c->gev[0][0], st));
   for (int k = 0; k < kSweepSlots + 2; ++k)
     TRH_CUDA(cudaStreamWaitEvent(c->gs[k], c->gev[0][0], 0));
@@ -1515,7 +1527,7 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
     TRH_CUDA(cudaEventRecord(c->gev[2][b], as));
     TRH_CUDA(cudaStreamWaitEvent(us, c->gev[2][b], 0));
     if (ubar_digits)
-      TRH_CUDA(trh::launch_grad_ubar_mixed(g, us, launched));
+      TRH_CUDA(trh::launch_grad_ubar_mixed(g, c->d_ubar_pf.p, c->d_ubar_gc.p, us, launched));
     else
       TRH_CUDA(trh::launch_grad_ubar(g, us, launched));
     TRH_CUDA(cudaEventRecord(c->gev[3][b], us));
@@ -1706,6 +1718,8 @@ void trh_destroy(trh_ctx* c) {
     for (int b = 0; b < kSweepSlots; ++b)
       if (c->gev[k][b]) cudaEventDestroy(c->gev[k][b]);
   c->d_adjZ.release();
+  c->d_ubar_pf.release();
+  c->d_ubar_gc.release();
   c->d_jacA.release();
   c->d_target.release();
   c->d_jac.release();
