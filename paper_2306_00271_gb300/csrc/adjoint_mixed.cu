@@ -17,8 +17,8 @@
 // of orders <= 3 accumulated exactly in four TMEM accumulators and combined in FP32.
 //
 // No binary64 arithmetic per kick: binary64 instructions run on this GPU at a small fraction of
-// the FP32 rate, and in a first form of this kernel the per-element conversions of Pbar and Q to
-// FP32, the double sums and the per-(kick, Gaussian) exponentials kept the FP64 pipe 79 % busy
+// the FP32 rate; a form of this kernel that converted Pbar and Q to FP32 element by element,
+// summed in double and evaluated the Gaussians per (kick, atom) kept the FP64 pipe 79 % busy
 // while the tensor pipe stayed idle. So the scales and digits come from the binary64 bit patterns
 // by integer arithmetic (a 31-bit fixed-point value per entry, cut into balanced base-256 digits),
 // the reduction and the contraction run in FP32, and the parts that depend only on the structure
