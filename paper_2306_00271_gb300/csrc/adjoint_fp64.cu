@@ -33,6 +33,8 @@
 //   d eta_1 / d B_a = sum_n sum_t [Re(...) G_t (d^2/(4 beta^2) - 1/(2 beta))
 //                                  - Re(sum_m conj(ubar_m) |g_m|^2 pref F[t][m]) G_t] / (16 pi^2)
 // with beta_t = (b_i + B_a) / (16 pi^2) and t = (a, i) over the four Gaussians of atom a.
+#include <algorithm>
+
 #include "fp64_core.cuh"
 
 namespace trh {
@@ -389,7 +391,48 @@ struct UbarSmem {
 
 // One CTA per (kick of the segment, angle, set): Ubar = -c Pbar Q^H, reduced to ubar_m and
 // contracted with the potential derivatives; accumulates into jac_atoms.
-__global__ void __launch_bounds__(NT, 1) k_grad_ubar(GradParams g) {
+// The contraction's factors that depend only on the structure and the node, once per gradient
+// (binary64; the same values k_grad_ubar forms per kick without them):
+//   pf[((set NA + t) M + m) 2 + {0, 1}] = pref F_{a,i,m}, |g_m|^2 pref F_{a,i,m}
+//   gc[((set n_nodes + node) NA + t) 2 + {0, 1}] = (G d / (2 beta), G (d^2 / (4 beta^2) -
+//       1 / (2 beta)) / (16 pi^2)), (G / (16 pi^2), 0)
+// for t = 4 ai + i over the active atoms a = active[ai] and their Gaussians i, NA = 4 n_active.
+__global__ void __launch_bounds__(256) k_ubar_tables_fp64(GradParams g, double2* pf, double2* gc) {
+  const IntegrateParams& p = g.ip;
+  const int M = p.M, NA = 4 * g.n_active, T = 4 * g.n_atoms;
+  const size_t n_pf = (size_t)p.n_sets * NA * M, n_gc = (size_t)p.n_sets * p.n_nodes * NA;
+  constexpr double k16pi2 = 16.0 * kPi * kPi;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_pf + n_gc;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < n_pf) {
+      const int m = (int)(e % M), t = (int)((e / M) % NA), set = (int)(e / ((size_t)M * NA));
+      const int a = g.active[t >> 2], i = t & 3;
+      const double2 f = g.F[((size_t)set * T + 4 * a + i) * M + m];
+      const double fr = g.pref.x * f.x - g.pref.y * f.y, fi = g.pref.x * f.y + g.pref.y * f.x;
+      const double2 gm = g.gdiff[m];
+      const double g2 = gm.x * gm.x + gm.y * gm.y;
+      pf[2 * e] = make_double2(fr, fi);
+      pf[2 * e + 1] = make_double2(g2 * fr, g2 * fi);
+    } else {
+      const size_t q = e - n_pf;
+      const int t = (int)(q % NA), node = (int)((q / NA) % p.n_nodes);
+      const int set = (int)(q / ((size_t)NA * p.n_nodes));
+      const int a = g.active[t >> 2], i = t & 3;
+      const double za = g.atoms[((size_t)set * g.n_atoms + a) * 3 + 2];
+      const double B = g.dw[(size_t)set * g.n_atoms + a];
+      const double beta = (g.sf[8 * g.species[a] + 4 + i] + B) / k16pi2;
+      const double d = g.node_z[node] - za;
+      const double G = exp(-d * d / (4.0 * beta));
+      gc[2 * q] = make_double2(G * d / (2.0 * beta),
+                               G * (d * d / (4.0 * beta * beta) - 0.5 / beta) / k16pi2);
+      gc[2 * q + 1] = make_double2(G / k16pi2, 0.0);
+    }
+  }
+}
+
+// pf, gc: the tables of k_ubar_tables_fp64, or nullptr to form those factors here per kick.
+__global__ void __launch_bounds__(NT, 1) k_grad_ubar(GradParams g, const double2* pf,
+                                                     const double2* gc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   UbarSmem& S = *reinterpret_cast<UbarSmem*>(smem_raw);
   double* ur = reinterpret_cast<double*>(smem_raw + sizeof(UbarSmem));
@@ -434,7 +477,29 @@ __global__ void __launch_bounds__(NT, 1) k_grad_ubar(GradParams g) {
   const int T = 4 * g.n_atoms;
   const double2* Fs = g.F + (size_t)set * T * M;
   constexpr double k16pi2 = 16.0 * kPi * kPi;
-  for (int w = warp; w < 4 * g.n_active; w += NT / 32) {
+  if (pf) {
+    const int NA = 4 * g.n_active;
+    const double2* pfs = pf + (size_t)set * NA * M * 2;
+    const double2* gcn = gc + ((size_t)set * p.n_nodes + n) * NA * 2;
+    for (int t = warp; t < NA; t += NT / 32) {
+      const double2* pt = pfs + (size_t)t * M * 2;
+      double v = 0.0, vg = 0.0;
+#pragma unroll 4
+      for (int m = lane; m < M; m += 32) {
+        const double2 f = pt[2 * m], fg = pt[2 * m + 1];
+        v += ur[m] * f.x + ui[m] * f.y;
+        vg += ur[m] * fg.x + ui[m] * fg.y;
+      }
+      v = -c * warp_sum(v);
+      vg = -c * warp_sum(vg);
+      if (lane == 0) {
+        const double2 g0 = gcn[2 * t], g1 = gcn[2 * t + 1];
+        atomicAdd(&S.acc[2 * (t >> 2)], v * g0.x);
+        atomicAdd(&S.acc[2 * (t >> 2) + 1], v * g0.y - vg * g1.x);
+      }
+    }
+  }
+  for (int w = warp; w < 4 * g.n_active && !pf; w += NT / 32) {
     const int ai = w >> 2, i = w & 3;
     const int a = g.active[ai];
     const double2* Ft = Fs + (size_t)(4 * a + i) * M;
@@ -577,13 +642,37 @@ cudaError_t launch_grad_adjoint(const GradParams& g, cudaStream_t st, int* n_lau
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_ubar(const GradParams& g, cudaStream_t st, int* n_launched) {
+// pf, gc: tables of launch_ubar_tables_fp64 (same stream or before), or nullptr.
+cudaError_t launch_grad_ubar_tab(const GradParams& g, const double2* pf, const double2* gc,
+                                 cudaStream_t st, int* n_launched) {
   if (g.n_active > 64) return cudaErrorInvalidValue;
   const size_t smem = sizeof(UbarSmem) + 2 * (size_t)g.ip.M * sizeof(double);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = set_smem((const void*)k_grad_ubar, smem);
   if (e != cudaSuccess) return e;
-  k_grad_ubar<<<dim3(g.kseg, g.ip.ang.n_angles, g.ip.n_sets), NT, smem, st>>>(g);
+  k_grad_ubar<<<dim3(g.kseg, g.ip.ang.n_angles, g.ip.n_sets), NT, smem, st>>>(g, pf, gc);
+  if (n_launched) *n_launched += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_ubar(const GradParams& g, cudaStream_t st, int* n_launched) {
+  return launch_grad_ubar_tab(g, nullptr, nullptr, st, n_launched);
+}
+
+// Elements (double2) of the two tables: pf 2 n_sets 4 n_active M, gc 2 n_sets n_nodes 4 n_active.
+size_t ubar_tables_fp64_count(const GradParams& g, size_t* n_gc) {
+  const size_t na = 4 * (size_t)g.n_active;
+  *n_gc = 2 * (size_t)g.ip.n_sets * g.ip.n_nodes * na;
+  return 2 * (size_t)g.ip.n_sets * na * g.ip.M;
+}
+
+cudaError_t launch_ubar_tables_fp64(const GradParams& g, double2* pf, double2* gc,
+                                    cudaStream_t st, int* n_launched) {
+  size_t n_gc = 0;
+  const size_t total = (ubar_tables_fp64_count(g, &n_gc) + n_gc) / 2;
+  if (total == 0) return cudaSuccess;
+  const size_t blocks = std::min<size_t>((total + 255) / 256, 152 * 8);
+  k_ubar_tables_fp64<<<(unsigned)blocks, 256, 0, st>>>(g, pf, gc);
   if (n_launched) *n_launched += 1;
   return cudaGetLastError();
 }

@@ -85,6 +85,13 @@ size_t ubar_pf_count(const GradParams& g);
 size_t ubar_gc_count(const GradParams& g);
 cudaError_t launch_ubar_tables(const GradParams& g, float4* pf, float4* gc, cudaStream_t st,
                                int* n_launched);
+// adjoint_fp64.cu: the binary64 contraction with its structure- and node-dependent factors
+// tabulated once per call
+cudaError_t launch_grad_ubar_tab(const GradParams& g, const double2* pf, const double2* gc,
+                                 cudaStream_t st, int* n_launched);
+size_t ubar_tables_fp64_count(const GradParams& g, size_t* n_gc);
+cudaError_t launch_ubar_tables_fp64(const GradParams& g, double2* pf, double2* gc,
+                                    cudaStream_t st, int* n_launched);
 // adjoint_fp64.cu: the recompute and the adjoint as two-CTA clusters (column split, N > 32)
 cudaError_t launch_grad_recompute_split(const GradParams& g, cudaStream_t st, int* n_launched);
 cudaError_t launch_grad_adjoint_split(const GradParams& g, cudaStream_t st, int* n_launched);
@@ -166,6 +173,7 @@ struct trh_ctx {
   DevBuf<int> d_active, d_free_active, d_class_active, d_rflag[kSweepSlots];
   DevBuf<double2> d_ckpt, d_segQ[kSweepSlots], d_segPb[kSweepSlots], d_segR[kSweepSlots], d_adjZ;
   DevBuf<float4> d_ubar_pf, d_ubar_gc;   // tables of the digit contraction (mixed contexts)
+  DevBuf<double2> d_ubar_pf64, d_ubar_gc64;   // tables of the binary64 contraction
   // reverse-sweep pipeline: recompute / adjoint / contraction on their own streams, buffers
   // double-buffered by segment parity
   // reverse sweep: one recompute stream per segment slot, then the adjoint and the contraction
@@ -1496,6 +1504,12 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
     TRH_CUDA(c->d_ubar_pf.ensure(trh::ubar_pf_count(g)));
     TRH_CUDA(c->d_ubar_gc.ensure(trh::ubar_gc_count(g)));
     TRH_CUDA(trh::launch_ubar_tables(g, c->d_ubar_pf.p, c->d_ubar_gc.p, st, launched));
+  } else {
+    size_t n_gc = 0;
+    const size_t n_pf = trh::ubar_tables_fp64_count(g, &n_gc);
+    TRH_CUDA(c->d_ubar_pf64.ensure(n_pf));
+    TRH_CUDA(c->d_ubar_gc64.ensure(n_gc));
+    TRH_CUDA(trh::launch_ubar_tables_fp64(g, c->d_ubar_pf64.p, c->d_ubar_gc64.p, st, launched));
   }
   TRH_CUDA(cudaEventRecord(c->gev[0][0], st));
   for (int k = 0; k < kSweepSlots + 2; ++k)
@@ -1529,7 +1543,7 @@ static int run_reverse_sweep(trh_ctx* c, int n_angles, const double* theta0,
     if (ubar_digits)
       TRH_CUDA(trh::launch_grad_ubar_mixed(g, c->d_ubar_pf.p, c->d_ubar_gc.p, us, launched));
     else
-      TRH_CUDA(trh::launch_grad_ubar(g, us, launched));
+      TRH_CUDA(trh::launch_grad_ubar_tab(g, c->d_ubar_pf64.p, c->d_ubar_gc64.p, us, launched));
     TRH_CUDA(cudaEventRecord(c->gev[3][b], us));
   }
   // join: the last contraction of each slot ran after every adjoint and recompute it depends on
@@ -1720,6 +1734,8 @@ void trh_destroy(trh_ctx* c) {
   c->d_adjZ.release();
   c->d_ubar_pf.release();
   c->d_ubar_gc.release();
+  c->d_ubar_pf64.release();
+  c->d_ubar_gc64.release();
   c->d_jacA.release();
   c->d_target.release();
   c->d_jac.release();
