@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <climits>
 
+#include "fixed_digits.cuh"
 #include "internal.h"
 #include "mixed_digits.cuh"
 #include "umma.cuh"
@@ -38,6 +39,7 @@ namespace {
 
 using namespace umma;
 using namespace mixed;
+using namespace fixed;
 
 constexpr int UT = 256;                     // threads
 constexpr int MT = 128;                     // rows of the tile (2N <= 128)
@@ -64,16 +66,6 @@ struct __align__(1024) USmem {
   int to;
 };
 static_assert(sizeof(USmem) <= 232448, "shared memory above the 227 KB a CTA may use");
-
-// Exponent of the smallest power of two >= |x| from the binary64 bit pattern; INT_MIN for 0
-// (subnormals, far below every scale here, count as 2^-1022).
-__device__ __forceinline__ int ceil_exp(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  if (b == 0) return INT_MIN;
-  const int ex = (int)(b >> 52);
-  if (ex == 0) return -1022;
-  return ex - 1023 + ((b & 0xFFFFFFFFFFFFFull) != 0 ? 1 : 0);
-}
 
 // Row scale exponents of two N x N complex matrices X and Y (N <= 64): the exponent of the
 // smallest power of two >= the largest |Re|, |Im| of the row (0 for a zero row), clamped to the
@@ -112,45 +104,13 @@ __device__ __forceinline__ void row_exps(const double2* X, const double2* Y, int
   }
 }
 
-__device__ __forceinline__ float pow2f(int e) {  // 2^e, -126 <= e <= 127
-  return __int_as_float((e + 127) << 23);
-}
-
-// V = x 2^(31 - E) rounded to an integer (|x| <= 2^E, so |V| <= 2^31), from the bit pattern.
-__device__ __forceinline__ long long fixed31(double x, int E) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) return 0;
-  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));  // x = mant 2^(ex-1075)
-  const int k = 1044 + E - ex;   // right shift: x 2^(31-E) = mant 2^-k, k >= 21
-  const long long v = (k >= 60) ? 0 : (((mant >> (k - 1)) + 1) >> 1);
-  return (b >> 63) ? -v : v;
-}
-
-// BF16 bit pattern of an integer |d| <= 256 (exact), by the 1.5 * 2^23 float trick.
-__device__ __forceinline__ uint16_t bf16_of_int(int d) {
-  const float f = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
-  return (uint16_t)(__float_as_uint(f) >> 16);
-}
-
-// Balanced base-256 digits of V = d0 2^24 + d1 2^16 + d2 2^8 + d3 (|d_i| <= 128), as BF16.
-__device__ __forceinline__ void digits_fixed(long long V, uint16_t (&b)[NDIG]) {
-#pragma unroll
-  for (int i = NDIG - 1; i >= 1; --i) {
-    const int r = (int)((V + 128) & 255) - 128;
-    b[i] = bf16_of_int(r);
-    V = (V - r) >> 8;
-  }
-  b[0] = bf16_of_int((int)V);
-}
-
 // Eight consecutive K elements (16 B) of one digit plane from their fixed-point values: word w of
 // the chunk holds elements (2w, 2w + 1).
 __device__ __forceinline__ void store_chunk(unsigned char* dst, const long long (&v)[8],
                                             int plane_stride) {
   uint16_t d[8][NDIG];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) digits_fixed(v[e], d[e]);
+  for (int e = 0; e < 8; ++e) digits_of(v[e], d[e]);
 #pragma unroll
   for (int t = 0; t < NDIG; ++t)
     *reinterpret_cast<uint4*>(dst + t * plane_stride) =
